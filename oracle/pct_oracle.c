@@ -1,0 +1,563 @@
+/*
+ * pct_oracle.c -- plain, slow FP64 CPU oracle for the proton-CT hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY. Only the test-suite, the smoke check and the
+ * benchmark's CPU-baseline / reference leg load this file. The product path
+ * (the CUDA library) shares no code, header, table or constant generator with
+ * it, and neither includes nor links the other.
+ *
+ * What it computes (arXiv 1707.05014):
+ *   Sec. 2   : each proton's most-likely path (MLP) from its entry/exit
+ *              position and direction; the path lengths in the voxels it
+ *              touches form its row of A in A x = b (b = WEPL).
+ *   Sec. 2.1 : DROP -- block-sequential diagonally relaxed orthogonal
+ *              projections over a user-chosen number of blocks, a fixed
+ *              number of iterations (Fig. 1).
+ * The paper cites the MLP formalism (Schulte et al. 2008) without printing it;
+ * this file follows that published form directly:
+ *     y1 = (S1^-1 + R1^T S2^-1 R1)^-1 (S1^-1 R0 y0 + R1^T S2^-1 y2),
+ * with y = (lateral position, slope), S1/S2 the scattering matrices before and
+ * after the node, integrated here by 64-point Gauss-Legendre quadrature.
+ *
+ * Readings where the paper is silent (each listed in the design notes):
+ *   - 1/(beta^2 p^2)(w) is Schulte's 5th-order water polynomial for 200 MeV,
+ *     w = depth from the entry plane in cm; Highland factor
+ *     E0^2 (1 + 0.038 ln(L/X0))^2 / X0 with L the sub-path length.
+ *   - measurement planes at u = -R and +R, R the inscribed radius of the grid;
+ *     nodes every du = 2R/K, K = ceil(2R / step), step = min(h)/2 by default;
+ *     straight extensions before u0 / after u2 along the measured slopes.
+ *   - nodes are quantised to Q20 fixed point in grid units (round half even,
+ *     clamped to +-1000 voxels) and walked by an exact integer DDA: voxels
+ *     are half-open, tied face crossings step together, zero-length runs are
+ *     never emitted, a run is a maximal stretch in one voxel.
+ *   - DROP: x <- x + lambda S_b^-1 sum_{i in b} a_i (b_i - a_i.x)/|a_i|^2 with
+ *     S_b = diag(number of runs in voxel j over block b); block b holds
+ *     protons [b N / B, (b+1) N / B).
+ *
+ * Two node modes: OR_MODE_FP64 evaluates the nodes in double; OR_MODE_FP32
+ * evaluates them with a fixed single-precision operation order (fmaf, no
+ * contraction -- compile with -ffp-contract=off) so that the quantised nodes,
+ * and so the voxel index lists, are defined bit for bit. Chord lengths and the
+ * solver always run in double.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_QBITS 20
+#define OR_QONE ((int64_t)1 << OR_QBITS)
+#define OR_QCLAMP 1000.0
+
+#define OR_F_CONST_SCATTER 1 /* test only: 1/(beta^2 p^2) held at its entry value */
+#define OR_F_NO_LOG 2        /* test only: drop the logarithmic Highland term   */
+
+#define OR_MODE_FP64 0
+#define OR_MODE_FP32 1
+
+typedef struct {
+  int nx, ny, nz;
+  double hx, hy, hz;
+  double node_step; /* <= 0: min(h)/2 */
+} or_grid;
+
+typedef struct {
+  const float *t0, *v0, *st0, *sv0, *t2, *v2, *st2, *sv2, *wepl, *cphi, *sphi;
+} or_rec;
+
+typedef struct {
+  double R, du, u0;
+  int K; /* interior nodes k = 0..K, u_k = u0 + k du */
+  int E; /* straight extension nodes per side */
+} or_geom;
+
+/* ------------------------------------------------------------------ */
+/* Geometry                                                            */
+/* ------------------------------------------------------------------ */
+
+static void or_geometry(const or_grid *g, or_geom *o) {
+  double X = g->nx * g->hx, Y = g->ny * g->hy;
+  double hmin = fmin(g->hx, fmin(g->hy, g->hz));
+  double step = g->node_step > 0 ? g->node_step : 0.5 * hmin;
+  o->R = 0.5 * fmin(X, Y);
+  o->K = (int)ceil(2.0 * o->R / step - 1e-9);
+  o->du = 2.0 * o->R / o->K;
+  o->u0 = -o->R;
+  /* every point with |u| beyond the half diagonal of the xy box is outside */
+  o->E = (int)ceil((0.5 * sqrt(X * X + Y * Y) - o->R) / o->du) + 2;
+}
+
+int or_geom_info(const or_grid *g, double *R, double *du, int *K, int *E) {
+  or_geom o;
+  or_geometry(g, &o);
+  *R = o.R;
+  *du = o.du;
+  *K = o.K;
+  *E = o.E;
+  return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Scattering model (Schulte et al. 2008, cited in Sec. 2)             */
+/* ------------------------------------------------------------------ */
+
+static const double OR_A[6] = {7.457e-6, 4.548e-7, -5.777e-8, 1.301e-8, -9.228e-10, 2.687e-11};
+static const double OR_E0 = 13.6;  /* MeV  */
+static const double OR_X0 = 36.08; /* cm, radiation length of water */
+
+/* 1/(beta^2 p^2) at water depth w (cm), MeV^-2 */
+double or_inv_beta2p2(double w, int flags) {
+  if (flags & OR_F_CONST_SCATTER) return OR_A[0];
+  double s = 0.0, wp = 1.0;
+  for (int i = 0; i < 6; ++i) {
+    s += OR_A[i] * wp;
+    wp *= w;
+  }
+  return s;
+}
+
+/* E0^2 (1 + 0.038 ln(L/X0))^2 / X0 */
+static double or_highland(double L, int flags) {
+  double f = 1.0;
+  if (!(flags & OR_F_NO_LOG)) f = 1.0 + 0.038 * log(L / OR_X0);
+  return OR_E0 * OR_E0 * f * f / OR_X0;
+}
+
+/* n-point Gauss-Legendre nodes/weights on [-1, 1] by Newton on P_n */
+void or_gauss_legendre(int n, double *x, double *w) {
+  const double pi = 3.14159265358979323846;
+  for (int i = 0; i < (n + 1) / 2; ++i) {
+    double z = cos(pi * (i + 0.75) / (n + 0.5)), dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z; /* P_0, P_1 */
+      for (int j = 2; j <= n; ++j) {
+        double p2 = ((2.0 * j - 1.0) * z * p1 - (j - 1.0) * p0) / j;
+        p0 = p1;
+        p1 = p2;
+      }
+      /* p1 = P_n(z), p0 = P_{n-1}(z) */
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      double dz = p1 / dp;
+      z -= dz;
+      if (fabs(dz) < 1e-16) break;
+    }
+    x[i] = -z;
+    x[n - 1 - i] = z;
+    w[i] = w[n - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+#define OR_NGL 64
+static double or_glx[OR_NGL], or_glw[OR_NGL];
+static int or_gl_ready = 0;
+
+/* integral over w in [a, b] of (c - w)^m / (beta^2 p^2)(w) dw */
+double or_moment(double a, double b, double c, int m, int flags) {
+  if (!or_gl_ready) {
+    or_gauss_legendre(OR_NGL, or_glx, or_glw);
+    or_gl_ready = 1;
+  }
+  double half = 0.5 * (b - a), mid = 0.5 * (a + b), s = 0.0;
+  for (int i = 0; i < OR_NGL; ++i) {
+    double w = mid + half * or_glx[i];
+    s += or_glw[i] * pow(c - w, m) * or_inv_beta2p2(w, flags);
+  }
+  return s * half;
+}
+
+static void inv2(const double a[2][2], double o[2][2]) {
+  double det = a[0][0] * a[1][1] - a[0][1] * a[1][0];
+  o[0][0] = a[1][1] / det;
+  o[0][1] = -a[0][1] / det;
+  o[1][0] = -a[1][0] / det;
+  o[1][1] = a[0][0] / det;
+}
+
+static void mul2(const double a[2][2], const double b[2][2], double o[2][2]) {
+  double t[2][2];
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 2; ++j) t[i][j] = a[i][0] * b[0][j] + a[i][1] * b[1][j];
+  memcpy(o, t, sizeof t);
+}
+
+/*
+ * MLP coefficient table: for each interior node k = 0..K (depth u_k) the
+ * first rows of H^-1 S1^-1 R0 -> (c1, c2) and of H^-1 R1^T S2^-1 -> (c3, c4),
+ * so that t_k = c1 t0 + c2 st0 + c3 t2 + c4 st2 (positions in mm, c2/c4 in
+ * mm). Nodes k = 0 and k = K take the measured values exactly. out: (K+1)*4.
+ */
+int or_mlp_table(const or_grid *g, int flags, double *out) {
+  or_geom o;
+  or_geometry(g, &o);
+  const double W = 2.0 * o.R / 10.0; /* slab thickness, cm */
+  for (int k = 0; k <= o.K; ++k) {
+    double *c = out + 4 * k;
+    if (k == 0 || k == o.K) {
+      c[0] = (k == 0);
+      c[1] = 0.0;
+      c[2] = (k == o.K);
+      c[3] = 0.0;
+      continue;
+    }
+    double w1 = k * o.du / 10.0; /* node depth, cm */
+    double k1 = or_highland(w1, flags), k2 = or_highland(W - w1, flags);
+    double S1[2][2] = {{k1 * or_moment(0, w1, w1, 2, flags), k1 * or_moment(0, w1, w1, 1, flags)},
+                       {k1 * or_moment(0, w1, w1, 1, flags), k1 * or_moment(0, w1, w1, 0, flags)}};
+    double S2[2][2] = {{k2 * or_moment(w1, W, W, 2, flags), k2 * or_moment(w1, W, W, 1, flags)},
+                       {k2 * or_moment(w1, W, W, 1, flags), k2 * or_moment(w1, W, W, 0, flags)}};
+    double R0[2][2] = {{1.0, w1}, {0.0, 1.0}};
+    double R1[2][2] = {{1.0, W - w1}, {0.0, 1.0}};
+    double R1T[2][2] = {{1.0, 0.0}, {W - w1, 1.0}};
+    double S1i[2][2], S2i[2][2], H[2][2], Hi[2][2], T[2][2], Ma[2][2], Mb[2][2];
+    inv2(S1, S1i);
+    inv2(S2, S2i);
+    mul2(R1T, S2i, T); /* R1^T S2^-1 */
+    mul2(T, R1, H);    /* R1^T S2^-1 R1 */
+    for (int i = 0; i < 2; ++i)
+      for (int j = 0; j < 2; ++j) H[i][j] += S1i[i][j];
+    inv2(H, Hi);
+    mul2(Hi, S1i, Ma);
+    mul2(Ma, R0, Ma); /* H^-1 S1^-1 R0 */
+    mul2(Hi, T, Mb);  /* H^-1 R1^T S2^-1 */
+    c[0] = Ma[0][0];
+    c[1] = 10.0 * Ma[0][1];
+    c[2] = Mb[0][0];
+    c[3] = 10.0 * Mb[0][1];
+  }
+  return o.K;
+}
+
+/* ------------------------------------------------------------------ */
+/* Nodes                                                               */
+/* ------------------------------------------------------------------ */
+
+static int32_t or_quant_d(double q) {
+  if (q < -OR_QCLAMP) q = -OR_QCLAMP;
+  if (q > OR_QCLAMP) q = OR_QCLAMP;
+  return (int32_t)lrint(q * (double)OR_QONE); /* default mode: half to even */
+}
+
+static int32_t or_quant_f(float q) {
+  if (q < (float)-OR_QCLAMP) q = (float)-OR_QCLAMP;
+  if (q > (float)OR_QCLAMP) q = (float)OR_QCLAMP;
+  return (int32_t)lrintf(q * 1048576.0f);
+}
+
+/* Quantised node k of proton i in grid units (Q20). */
+static void or_node(const or_grid *g, const or_geom *o, const double *tab, const or_rec *r, int64_t i, int mode,
+                    int k, int32_t Q[3]) {
+  if (mode == OR_MODE_FP64) {
+    double t0 = r->t0[i], v0 = r->v0[i], st0 = r->st0[i], sv0 = r->sv0[i];
+    double t2 = r->t2[i], v2 = r->v2[i], st2 = r->st2[i], sv2 = r->sv2[i];
+    double cp = r->cphi[i], sp = r->sphi[i];
+    double u = o->u0 + k * o->du, t, v;
+    if (k < 0) {
+      t = t0 + st0 * (k * o->du);
+      v = v0 + sv0 * (k * o->du);
+    } else if (k > o->K) {
+      t = t2 + st2 * ((k - o->K) * o->du);
+      v = v2 + sv2 * ((k - o->K) * o->du);
+    } else {
+      const double *c = tab + 4 * k;
+      t = c[0] * t0 + c[1] * st0 + c[2] * t2 + c[3] * st2;
+      v = c[0] * v0 + c[1] * sv0 + c[2] * v2 + c[3] * sv2;
+    }
+    double x = u * cp - t * sp, y = u * sp + t * cp, z = v;
+    Q[0] = or_quant_d(x / g->hx + 0.5 * g->nx);
+    Q[1] = or_quant_d(y / g->hy + 0.5 * g->ny);
+    Q[2] = or_quant_d(z / g->hz + 0.5 * g->nz);
+  } else {
+    /* fixed single-precision order (the bit-exact contract) */
+    float t0 = r->t0[i], v0 = r->v0[i], st0 = r->st0[i], sv0 = r->sv0[i];
+    float t2 = r->t2[i], v2 = r->v2[i], st2 = r->st2[i], sv2 = r->sv2[i];
+    float cp = r->cphi[i], sp = r->sphi[i];
+    float du = (float)o->du, u0 = (float)o->u0;
+    float u = fmaf((float)k, du, u0), t, v;
+    if (k < 0) {
+      float dk = (float)k * du;
+      t = fmaf(st0, dk, t0);
+      v = fmaf(sv0, dk, v0);
+    } else if (k > o->K) {
+      float dk = (float)(k - o->K) * du;
+      t = fmaf(st2, dk, t2);
+      v = fmaf(sv2, dk, v2);
+    } else {
+      const double *c = tab + 4 * k;
+      float c1 = (float)c[0], c2 = (float)c[1], c3 = (float)c[2], c4 = (float)c[3];
+      float a = c1 * t0;
+      t = fmaf(c4, st2, fmaf(c3, t2, fmaf(c2, st0, a)));
+      float b = c1 * v0;
+      v = fmaf(c4, sv2, fmaf(c3, v2, fmaf(c2, sv0, b)));
+    }
+    float ts = t * sp, tc = t * cp;
+    float x = fmaf(u, cp, -ts);
+    float y = fmaf(u, sp, tc);
+    float ihx = (float)(1.0 / g->hx), ihy = (float)(1.0 / g->hy), ihz = (float)(1.0 / g->hz);
+    Q[0] = or_quant_f(fmaf(x, ihx, 0.5f * (float)g->nx));
+    Q[1] = or_quant_f(fmaf(y, ihy, 0.5f * (float)g->ny));
+    Q[2] = or_quant_f(fmaf(v, ihz, 0.5f * (float)g->nz));
+  }
+}
+
+/* Interior nodes k = 0..K of protons [first, first+count): out (count, K+1, 3) */
+int or_nodes(const or_grid *g, const double *tab, const or_rec *r, int64_t first, int64_t count, int mode,
+             int32_t *out) {
+  or_geom o;
+  or_geometry(g, &o);
+  for (int64_t p = 0; p < count; ++p)
+    for (int k = 0; k <= o.K; ++k) or_node(g, &o, tab, r, first + p, mode, k, out + 3 * ((int64_t)p * (o.K + 1) + k));
+  return 0;
+}
+
+/* All polyline nodes k = -E..K+E of proton i: out (K + 2E + 1, 3) */
+int or_polyline(const or_grid *g, const double *tab, const or_rec *r, int64_t i, int mode, int32_t *out) {
+  or_geom o;
+  or_geometry(g, &o);
+  for (int k = -o.E; k <= o.K + o.E; ++k) or_node(g, &o, tab, r, i, mode, k, out + 3 * (int64_t)(k + o.E));
+  return o.K + 2 * o.E + 1;
+}
+
+/* ------------------------------------------------------------------ */
+/* Voxel walk (row of A)                                               */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+  int32_t *j;
+  double *l;
+  int64_t n, cap;
+} or_row;
+
+static void or_row_push(or_row *w, int32_t j, double l) {
+  if (w->n == w->cap) {
+    w->cap = w->cap ? 2 * w->cap : 256;
+    w->j = (int32_t *)realloc(w->j, w->cap * sizeof(int32_t));
+    w->l = (double *)realloc(w->l, w->cap * sizeof(double));
+  }
+  w->j[w->n] = j;
+  w->l[w->n] = l;
+  w->n++;
+}
+
+static int64_t or_floor_div(int64_t a) { /* floor(a / 2^20) */
+  return a >= 0 ? a / OR_QONE : -((-a + OR_QONE - 1) / OR_QONE);
+}
+
+typedef struct {
+  int64_t cur[3];   /* current voxel */
+  double len;       /* run length so far, mm */
+  int pos;          /* run has strictly positive extent */
+  int started;
+} or_walk;
+
+static void or_emit(const or_grid *g, or_walk *s, or_row *row) {
+  if (s->pos && s->cur[0] >= 0 && s->cur[0] < g->nx && s->cur[1] >= 0 && s->cur[1] < g->ny && s->cur[2] >= 0 &&
+      s->cur[2] < g->nz)
+    or_row_push(row, (int32_t)(s->cur[0] + (int64_t)g->nx * (s->cur[1] + (int64_t)g->ny * s->cur[2])), s->len);
+  s->len = 0.0;
+  s->pos = 0;
+}
+
+/* Walk the straight segment P -> E (Q20 grid units), appending finished runs. */
+static void or_segment(const or_grid *g, const int32_t P[3], const int32_t E[3], or_walk *s, or_row *row) {
+  const double h[3] = {g->hx, g->hy, g->hz};
+  int64_t D[3], dist[3], step[3];
+  int a;
+  if (P[0] == E[0] && P[1] == E[1] && P[2] == E[2]) return;
+  for (a = 0; a < 3; ++a) {
+    int64_t c = or_floor_div(P[a]);
+    if (!s->started) s->cur[a] = c;
+    D[a] = (int64_t)E[a] - P[a];
+    step[a] = D[a] > 0 ? 1 : (D[a] < 0 ? -1 : 0);
+    /* distance from P to the next face in the direction of travel */
+    dist[a] = D[a] > 0 ? (c + 1) * OR_QONE - P[a] : (D[a] < 0 ? P[a] - c * OR_QONE : 0);
+  }
+  s->started = 1;
+  double L = 0.0;
+  for (a = 0; a < 3; ++a) {
+    double d = (double)D[a] * h[a] / (double)OR_QONE;
+    L += d * d;
+  }
+  L = sqrt(L);
+  /* previous crossing parameter as an exact fraction pn/pd (starts at 0) */
+  int64_t pn = 0, pd = 1;
+  double tprev = 0.0;
+  for (;;) {
+    /* axes whose next face lies within the segment: tau = dist/|D| <= 1 when
+       moving up (a point on a face belongs to the higher voxel), < 1 down */
+    int cand[3], any = 0;
+    for (a = 0; a < 3; ++a) {
+      int64_t ad = D[a] < 0 ? -D[a] : D[a];
+      cand[a] = D[a] > 0 ? dist[a] <= ad : (D[a] < 0 ? dist[a] < ad : 0);
+      any |= cand[a];
+    }
+    if (!any) break;
+    /* smallest tau among candidates, compared exactly */
+    int best = -1;
+    for (a = 0; a < 3; ++a) {
+      if (!cand[a]) continue;
+      if (best < 0) {
+        best = a;
+        continue;
+      }
+      __int128 lhs = (__int128)dist[a] * (D[best] < 0 ? -D[best] : D[best]);
+      __int128 rhs = (__int128)dist[best] * (D[a] < 0 ? -D[a] : D[a]);
+      if (lhs < rhs) best = a;
+    }
+    int64_t bn = dist[best], bd = D[best] < 0 ? -D[best] : D[best];
+    double tc = (double)bn / (double)bd;
+    s->len += (tc - tprev) * L;
+    if ((__int128)bn * pd > (__int128)pn * bd) s->pos = 1;
+    or_emit(g, s, row);
+    /* every axis tied with the minimum steps now */
+    for (a = 0; a < 3; ++a) {
+      if (!cand[a]) continue;
+      int64_t ad = D[a] < 0 ? -D[a] : D[a];
+      if ((__int128)dist[a] * bd == (__int128)bn * ad) {
+        s->cur[a] += step[a];
+        dist[a] += OR_QONE;
+      }
+    }
+    pn = bn;
+    pd = bd;
+    tprev = tc;
+  }
+  s->len += (1.0 - tprev) * L;
+  if (pn < pd) s->pos = 1;
+}
+
+/* Row of proton i: runs (voxel, chord mm) in path order. */
+static void or_walk_row(const or_grid *g, const or_geom *o, const double *tab, const or_rec *r, int64_t i, int mode,
+                        or_row *row) {
+  or_walk s;
+  memset(&s, 0, sizeof s);
+  row->n = 0;
+  int32_t P[3], E[3];
+  or_node(g, o, tab, r, i, mode, -o->E, P);
+  for (int k = -o->E + 1; k <= o->K + o->E; ++k) {
+    or_node(g, o, tab, r, i, mode, k, E);
+    or_segment(g, P, E, &s, row);
+    P[0] = E[0];
+    P[1] = E[1];
+    P[2] = E[2];
+  }
+  or_emit(g, &s, row);
+}
+
+/*
+ * Rows of protons [first, first+count) in CSR form. row_ptr has count+1
+ * entries. Writes at most cap runs; returns the number needed (>= 0).
+ */
+int64_t or_rows(const or_grid *g, const double *tab, const or_rec *r, int64_t first, int64_t count, int mode,
+                int64_t *row_ptr, int32_t *vox, double *len, int64_t cap) {
+  or_geom o;
+  or_geometry(g, &o);
+  or_row row = {0};
+  int64_t tot = 0;
+  row_ptr[0] = 0;
+  for (int64_t p = 0; p < count; ++p) {
+    or_walk_row(g, &o, tab, r, first + p, mode, &row);
+    for (int64_t q = 0; q < row.n; ++q, ++tot)
+      if (tot < cap) {
+        vox[tot] = row.j[q];
+        len[tot] = row.l[q];
+      }
+    row_ptr[p + 1] = tot;
+  }
+  free(row.j);
+  free(row.l);
+  return tot;
+}
+
+/* y_i = a_i . x for protons [first, first+count) (forward projection). */
+int or_project(const or_grid *g, const double *tab, const or_rec *r, int64_t first, int64_t count, int mode,
+               const double *x, double *y) {
+  or_geom o;
+  or_geometry(g, &o);
+  or_row row = {0};
+  for (int64_t p = 0; p < count; ++p) {
+    or_walk_row(g, &o, tab, r, first + p, mode, &row);
+    double s = 0.0;
+    for (int64_t q = 0; q < row.n; ++q) s += row.l[q] * x[row.j[q]];
+    y[p] = s;
+  }
+  free(row.j);
+  free(row.l);
+  return 0;
+}
+
+/* Run counts s_j of block b (rows of protons [b N/B, (b+1) N/B)). out: M */
+int or_block_counts(const or_grid *g, const double *tab, const or_rec *r, int64_t n, int n_blocks, int b, int mode,
+                    double *out) {
+  or_geom o;
+  or_geometry(g, &o);
+  int64_t M = (int64_t)g->nx * g->ny * g->nz;
+  memset(out, 0, M * sizeof(double));
+  or_row row = {0};
+  int64_t lo = (int64_t)b * n / n_blocks, hi = (int64_t)(b + 1) * n / n_blocks;
+  for (int64_t i = lo; i < hi; ++i) {
+    or_walk_row(g, &o, tab, r, i, mode, &row);
+    for (int64_t q = 0; q < row.n; ++q) out[row.j[q]] += 1.0;
+  }
+  free(row.j);
+  free(row.l);
+  return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* DROP (Sec. 2.1, Fig. 1)                                             */
+/* ------------------------------------------------------------------ */
+
+/*
+ * x (M, in/out: the initial guess on entry, the result on exit).
+ * For sweep = 1..n_sweeps, for block b = 0..B-1:
+ *   delta = 0, s = 0
+ *   for i in block b: a_i = row i; r_i = lambda (b_i - a_i.x)/|a_i|^2
+ *                     delta_j += a_ij r_i, s_j += 1 per run
+ *   x_j += delta_j / s_j (s_j > 0); optionally x_j = max(x_j, clamp_min)
+ * The next block starts from the updated x (Fig. 1). resid (n_sweeps, may be
+ * NULL) receives sum_i (b_i - a_i.x)^2 accumulated while sweeping.
+ */
+int or_drop(const or_grid *g, const double *tab, const or_rec *r, int64_t n, int n_blocks, double lambda,
+            int n_sweeps, int mode, int use_clamp, double clamp_min, double *x, double *resid) {
+  or_geom o;
+  or_geometry(g, &o);
+  int64_t M = (int64_t)g->nx * g->ny * g->nz;
+  double *delta = (double *)calloc(M, sizeof(double));
+  double *cnt = (double *)calloc(M, sizeof(double));
+  or_row row = {0};
+  if (!delta || !cnt) return -1;
+  for (int sw = 0; sw < n_sweeps; ++sw) {
+    double rr = 0.0;
+    for (int b = 0; b < n_blocks; ++b) {
+      int64_t lo = (int64_t)b * n / n_blocks, hi = (int64_t)(b + 1) * n / n_blocks;
+      memset(delta, 0, M * sizeof(double));
+      memset(cnt, 0, M * sizeof(double));
+      for (int64_t i = lo; i < hi; ++i) {
+        or_walk_row(g, &o, tab, r, i, mode, &row);
+        double ax = 0.0, nn = 0.0;
+        for (int64_t q = 0; q < row.n; ++q) {
+          ax += row.l[q] * x[row.j[q]];
+          nn += row.l[q] * row.l[q];
+        }
+        if (nn <= 0.0) continue;
+        double res = (double)r->wepl[i] - ax;
+        rr += res * res;
+        double ri = lambda * res / nn;
+        for (int64_t q = 0; q < row.n; ++q) {
+          delta[row.j[q]] += row.l[q] * ri;
+          cnt[row.j[q]] += 1.0;
+        }
+      }
+      for (int64_t j = 0; j < M; ++j) {
+        if (cnt[j] > 0.0) x[j] += delta[j] / cnt[j];
+        if (use_clamp && x[j] < clamp_min) x[j] = clamp_min;
+      }
+    }
+    if (resid) resid[sw] = rr;
+  }
+  free(delta);
+  free(cnt);
+  free(row.j);
+  free(row.l);
+  return 0;
+}

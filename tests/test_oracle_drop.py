@@ -1,0 +1,99 @@
+"""Pins for the oracle's DROP solver (Sec. 2.1, Fig. 1).
+
+* B = 1: the fixed point of x <- x + lam S^-1 A^T W (b - A x) satisfies
+  A^T W (b - A x) = 0, so DROP converges to the weighted least-squares
+  solution, which a dense Cholesky/lstsq solve gives independently.
+* One proton per block with lam = 1 is a Kaczmarz (ART) projection: right
+  after its block a proton's residual is exactly zero.
+* Consistent data (b = A x_true): the residual falls towards zero and the
+  image approaches x_true.
+"""
+import numpy as np
+import pytest
+
+from paper_1707_05014_gb300 import synthetic as S
+
+
+def _tiny():
+    g = S.Grid(4, 4, 2, 2.0, 2.0, 2.0)
+    wl = S.Workload("tiny442", g, 200, 21, 0, 4.0, 2.0, 1, 1, "water")
+    rec = S.make_histories(wl)
+    rec["wepl"] = (np.random.Generator(np.random.Philox(5)).random(200) * 8.0).astype(np.float32)
+    return g, rec
+
+
+def _dense(oracle, g, rec):
+    rp, vox, ln = oracle.rows(g, rec)
+    n = len(rp) - 1
+    A = np.zeros((n, g.m))
+    nn = np.zeros(n)
+    for i in range(n):
+        for j, l in zip(vox[rp[i]:rp[i + 1]], ln[rp[i]:rp[i + 1]]):
+            A[i, j] += l
+        nn[i] = (ln[rp[i]:rp[i + 1]] ** 2).sum()
+    return A, nn
+
+
+def test_single_block_converges_to_weighted_least_squares(oracle):
+    g, rec = _tiny()
+    A, nn = _dense(oracle, g, rec)
+    keep = nn > 0
+    assert np.linalg.matrix_rank(A[keep]) == g.m
+    # rows without repeated voxels: |a_i|^2 (sum over runs) is the textbook norm
+    assert np.allclose(nn, (A**2).sum(1))
+    b = rec["wepl"].astype(np.float64)
+    Wh = 1.0 / np.sqrt(nn[keep])
+    xs = np.linalg.lstsq(A[keep] * Wh[:, None], b[keep] * Wh, rcond=None)[0]
+    x = oracle.drop(g, rec, n_blocks=1, n_sweeps=4000, lam=1.5)
+    assert np.abs(x - xs).max() <= 1e-9 * np.abs(xs).max()
+
+
+def test_one_proton_block_is_an_exact_projection(oracle):
+    g, rec = _tiny()
+    for n in (1, 2, 7):
+        r = S.subset(rec, slice(0, n))
+        x = oracle.drop(g, r, n_blocks=n, n_sweeps=1, lam=1.0)
+        y = oracle.project(g, r, x)
+        assert abs(y[n - 1] - float(r["wepl"][n - 1])) < 1e-12 * max(1.0, float(r["wepl"][n - 1]))
+    # lam scales the step: the residual of the last proton becomes (1 - lam) r
+    r = S.subset(rec, slice(0, 1))
+    x = oracle.drop(g, r, n_blocks=1, n_sweeps=1, lam=0.25)
+    y = oracle.project(g, r, x)
+    assert abs((float(r["wepl"][0]) - y[0]) - 0.75 * float(r["wepl"][0])) < 1e-12
+
+
+def test_block_counts_are_run_counts(oracle):
+    g, rec = _tiny()
+    rp, vox, _ = oracle.rows(g, rec)
+    for B, b in ((1, 0), (4, 2)):
+        lo, hi = b * 200 // B, (b + 1) * 200 // B
+        ref = np.bincount(vox[rp[lo]:rp[hi]], minlength=g.m).astype(np.float64)
+        assert np.array_equal(oracle.block_counts(g, rec, B, b), ref)
+
+
+@pytest.mark.parametrize("B", [1, 5])
+def test_consistent_data_residual_vanishes(oracle, B):
+    wl = S.tiny_workload(4000, seed=3)
+    g = wl.grid
+    rec = S.make_histories(wl)
+    xt = S.voxelize(wl.phantom(), g)
+    rec["wepl"] = oracle.project(g, rec, xt).astype(np.float32)
+    x, res = oracle.drop(g, rec, B, 30, lam=1.0, return_resid=True)
+    assert np.all(np.diff(res[1:]) < 0)
+    assert res[-1] < 2e-3 * res[0]
+
+
+@pytest.mark.slow
+def test_noise_free_tiny_workload_converges(oracle):
+    # Noise-free consistent data on the 32^3 water cylinder: the mean RSP error
+    # over partial-volume-free voxels falls below 1% within 10 sweeps of 100
+    # blocks and keeps falling.
+    wl = S.tiny_workload(100_000)
+    g = wl.grid
+    rec = S.make_histories(wl)
+    xt = S.voxelize(wl.phantom(), g)
+    rec["wepl"] = oracle.project(g, rec, xt).astype(np.float32)
+    e5 = S.mean_rsp_error(oracle.drop(g, rec, 100, 5), xt, g)
+    e10 = S.mean_rsp_error(oracle.drop(g, rec, 100, 10), xt, g)
+    assert e10 < e5
+    assert e10 < 0.01

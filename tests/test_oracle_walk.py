@@ -1,0 +1,194 @@
+"""Pins for the oracle's voxel walk (Sec. 2: a row of A holds the path length
+in each voxel the proton touches).
+
+Checks against things fixed by geometry alone: axis-aligned and exactly
+diagonal straight paths (chords known in closed form, tie rule on faces and
+edges), the total chord of a row equals the clipped polyline length, and a
+brute-force supersampling of every segment reproduces the per-voxel chords.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1707_05014_gb300 import synthetic as S
+
+G32 = S.Grid(32, 32, 32, 2.0, 2.0, 2.0)
+GHEAD = S.Grid(160, 160, 64, 1.25, 1.25, 1.25)
+
+
+def _rec(g, t, v, c, s, st=0.0, sv=0.0):
+    r = S.straight_records(g, [t], [v], [st], [sv], [0.0])
+    r["cphi"][:] = np.float32(c)
+    r["sphi"][:] = np.float32(s)
+    return r
+
+
+def _split(g, vox):
+    ix = vox % g.nx
+    iy = (vox // g.nx) % g.ny
+    iz = vox // (g.nx * g.ny)
+    return ix, iy, iz
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_axis_aligned_straight_paths(oracle, mode):
+    g = G32
+    for (c, s), t, v in [((1.0, 0.0), 3.3, -7.1), ((0.0, 1.0), -11.9, 20.2), ((-1.0, 0.0), 0.7, 0.9),
+                         ((0.0, -1.0), 29.0, -29.0)]:
+        rp, vox, ln = oracle.rows(g, _rec(g, t, v, c, s), mode=mode)
+        ix, iy, iz = _split(g, vox)
+        assert len(vox) == g.nx
+        assert np.allclose(ln, g.hx, rtol=0, atol=1e-9)  # FP32 nodes wiggle by 1 Q20 unit
+        x_line = -t * s  # x = u c - t s, y = u s + t c
+        y_line = t * c
+        if c != 0:
+            assert np.all(iy == math.floor(y_line / g.hy + g.ny / 2))
+            assert list(ix) == (list(range(g.nx)) if c > 0 else list(range(g.nx - 1, -1, -1)))
+        else:
+            assert np.all(ix == math.floor(x_line / g.hx + g.nx / 2))
+            assert list(iy) == (list(range(g.ny)) if s > 0 else list(range(g.ny - 1, -1, -1)))
+        assert np.all(iz == math.floor(v / g.hz + g.nz / 2))
+
+
+def test_point_on_face_belongs_to_higher_voxel(oracle):
+    # t = 0 and v = 0 put the path exactly on the faces y = 0 and z = 0; voxels
+    # are half-open [i, i+1) so it lies in iy = ny/2 and iz = nz/2.
+    g = G32
+    for c in (1.0, -1.0):
+        rp, vox, ln = oracle.rows(g, _rec(g, 0.0, 0.0, c, 0.0))
+        ix, iy, iz = _split(g, vox)
+        assert len(vox) == g.nx
+        assert np.all(iy == g.ny // 2) and np.all(iz == g.nz // 2)
+        assert np.allclose(ln, g.hx, atol=1e-12)
+
+
+def test_diagonal_through_edges_steps_tied_axes_together(oracle):
+    # phi = 45 deg with identical float cos/sin: x == y bit for bit, so every
+    # crossing is an edge crossing; tied axes step at once, so the row holds
+    # the diagonal voxels only, each with chord h*sqrt(2), and no zero runs.
+    g = G32
+    c = np.float32(math.sqrt(0.5))
+    for sign in (1.0, -1.0):
+        rp, vox, ln = oracle.rows(g, _rec(g, 0.0, 5.5, sign * c, sign * c))
+        ix, iy, iz = _split(g, vox)
+        assert np.all(ix == iy)
+        assert len(vox) == g.nx
+        assert np.allclose(ln, g.hx * math.sqrt(2.0), rtol=1e-12)
+        assert np.all(ln > 0)
+
+
+def _clip_len(p0, p1, lo, hi):
+    """Length of segment p0->p1 inside the box [lo, hi] (Liang-Barsky)."""
+    d = p1 - p0
+    t0, t1 = 0.0, 1.0
+    for a in range(3):
+        if d[a] == 0:
+            if p0[a] < lo[a] or p0[a] > hi[a]:
+                return 0.0
+            continue
+        ta = (lo[a] - p0[a]) / d[a]
+        tb = (hi[a] - p0[a]) / d[a]
+        t0 = max(t0, min(ta, tb))
+        t1 = min(t1, max(ta, tb))
+    return max(t1 - t0, 0.0) * float(np.linalg.norm(d))
+
+
+def _poly_mm(g, Q):
+    h = np.array([g.hx, g.hy, g.hz])
+    return Q.astype(np.float64) / 2.0**20 * h  # grid-anchored mm
+
+
+@pytest.mark.parametrize("gname", ["g32", "head"])
+def test_row_total_equals_clipped_polyline_length(oracle, gname):
+    if gname == "g32":
+        wl = S.tiny_workload(300, seed=11)
+    else:
+        wl = S.head_workload(120, seed=12)
+    g = wl.grid
+    rec = S.make_histories(wl)
+    rp, vox, ln = oracle.rows(g, rec)
+    hi = np.array([g.nx * g.hx, g.ny * g.hy, g.nz * g.hz])
+    for i in range(len(rec["t0"])):
+        P = _poly_mm(g, oracle.polyline(g, rec, i))
+        ref = sum(_clip_len(P[k], P[k + 1], np.zeros(3), hi) for k in range(len(P) - 1))
+        got = ln[rp[i]:rp[i + 1]].sum()
+        assert abs(got - ref) <= 1e-12 * max(ref, 1.0)
+
+
+def test_rows_are_maximal_positive_runs(oracle):
+    wl = S.head_workload(400, seed=13)
+    g = wl.grid
+    rec = S.make_histories(wl)
+    rp, vox, ln = oracle.rows(g, rec)
+    assert np.all(ln > 0)
+    for i in range(400):
+        v = vox[rp[i]:rp[i + 1]]
+        assert np.all(v[1:] != v[:-1])  # a run ends only when the voxel changes
+        ix, iy, iz = _split(g, v)
+        # consecutive runs are face/edge/corner neighbours
+        step = np.maximum(np.abs(np.diff(ix)), np.maximum(np.abs(np.diff(iy)), np.abs(np.diff(iz))))
+        assert np.all(step <= 1)
+    # typical head rows: a few hundred non-zeros out of 1.6M voxels (Sec. 2)
+    nnz = np.diff(rp)
+    assert 100 < np.median(nnz) < 400
+
+
+def test_brute_force_supersampling(oracle):
+    wl = S.head_workload(12, seed=14)
+    g = wl.grid
+    rec = S.make_histories(wl)
+    rp, vox, ln = oracle.rows(g, rec)
+    h = np.array([g.hx, g.hy, g.hz])
+    nsub = 2048
+    for i in range(12):
+        Q = oracle.polyline(g, rec, i).astype(np.float64) / 2.0**20  # grid units
+        acc = {}
+        ds_max = 0.0
+        for k in range(len(Q) - 1):
+            a, b = Q[k], Q[k + 1]
+            seg = (b - a) * h
+            L = float(np.linalg.norm(seg))
+            if L == 0:
+                continue
+            tm = (np.arange(nsub) + 0.5) / nsub
+            pts = a[None, :] + tm[:, None] * (b - a)[None, :]
+            idx = np.floor(pts).astype(np.int64)
+            inside = np.all((idx >= 0) & (idx < np.array([g.nx, g.ny, g.nz])), axis=1)
+            j = idx[:, 0] + g.nx * (idx[:, 1] + g.ny * idx[:, 2])
+            for jj in j[inside]:
+                acc[jj] = acc.get(jj, 0.0) + L / nsub
+            ds_max = max(ds_max, L / nsub)
+        row = {}
+        for jj, ll in zip(vox[rp[i]:rp[i + 1]], ln[rp[i]:rp[i + 1]]):
+            row[int(jj)] = row.get(int(jj), 0.0) + ll
+        assert set(acc) <= set(row)
+        for jj, ll in row.items():
+            if ll > 4 * ds_max:
+                assert jj in acc
+            assert abs(acc.get(jj, 0.0) - ll) <= 6 * ds_max
+
+
+def test_fp64_and_fp32_rows_agree_except_near_ties(oracle):
+    # The FP32-order nodes move by < 1e-4 voxel, so index lists agree for all
+    # but a small fraction of protons. A chord moves by (node shift)/sin(angle
+    # between path and face), so grazing crossings (slopes of a few mrad) can
+    # move by ~1e-3 voxel while the typical chord moves by ~1e-6 voxel.
+    wl = S.head_workload(1000, seed=15)
+    g = wl.grid
+    rec = S.make_histories(wl)
+    a = oracle.rows(g, rec, mode=oracle.MODE_FP32)
+    b = oracle.rows(g, rec, mode=oracle.MODE_FP64)
+    same = 0
+    diffs = []
+    for i in range(1000):
+        va, vb = a[1][a[0][i]:a[0][i + 1]], b[1][b[0][i]:b[0][i + 1]]
+        if len(va) == len(vb) and np.all(va == vb):
+            same += 1
+            la, lb = a[2][a[0][i]:a[0][i + 1]], b[2][b[0][i]:b[0][i + 1]]
+            diffs.append(np.abs(la - lb) / g.hx)
+    d = np.concatenate(diffs)
+    assert same >= 990
+    assert np.median(d) < 1e-5
+    assert np.percentile(d, 99) < 1e-4
+    assert d.max() < 1e-2
