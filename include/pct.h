@@ -1,0 +1,179 @@
+/*
+ * pct.h -- C ABI of the GB300 proton-CT reconstruction library (libpct.so).
+ *
+ * The library computes the hot path of arXiv 1707.05014: for every proton
+ * history it estimates the most-likely path (MLP) from the measured entry and
+ * exit position and direction (Sec. 2), turns it into the sparse row a_i of
+ * A x = b (voxel indices and chord lengths, Sec. 2), and runs the DROP
+ * block-iterative row-projection solve over the relative stopping power x
+ * (Sec. 2.1, Fig. 1). Rows are recomputed on the GPU in every sweep and never
+ * stored.
+ *
+ * Conventions (all calls):
+ *   - Every function returns a pct_status (PCT_OK = 0, errors < 0); no C++
+ *     exception crosses the ABI. pct_last_error() returns a thread-local text
+ *     for the last failing call of the calling thread.
+ *   - Geometry: the grid is centred at the origin, voxel j = ix + nx*(iy +
+ *     ny*iz). The gantry angle phi rotates about z: beam direction
+ *     d = (cos phi, sin phi, 0), lateral axis e_t = (-sin phi, cos phi, 0),
+ *     vertical e_v = (0, 0, 1). Measurement planes at depth u = -R and +R,
+ *     R = min(nx*hx, ny*hy)/2. Lengths in mm, slopes dimensionless.
+ *   - Device work is queued on the context's stream (pct_set_stream); calls
+ *     return before it finishes unless stated. Errors raised by a kernel
+ *     surface on the next synchronising call (pct_sync, pct_get_rsp to host).
+ *   - The context owns every device buffer it allocates (cudaMalloc on the
+ *     context's device); pct_destroy frees them.
+ */
+#ifndef PCT_H
+#define PCT_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define PCT_API __attribute__((visibility("default")))
+#else
+#define PCT_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int pct_status;
+#define PCT_OK 0
+#define PCT_ERR_INVALID_ARG (-1)  /* bad pointer, size or option                 */
+#define PCT_ERR_INVALID_DATA (-2) /* a history record failed validation          */
+#define PCT_ERR_NO_MEMORY (-3)    /* device or host allocation failed            */
+#define PCT_ERR_CUDA (-4)         /* a CUDA runtime call or kernel failed        */
+#define PCT_ERR_CAPACITY (-5)     /* caller buffer too small (see *needed)      */
+#define PCT_ERR_TIMEOUT (-6)      /* a bounded device-side wait ran out          */
+#define PCT_ERR_STATE (-7)        /* call out of order (e.g. iterate before load) */
+
+/* Voxel grid: nx*ny*nz voxels of hx*hy*hz mm (Sec. 2: "a discrete rectangular
+ * grid of M voxels"). Each of nx, ny, nz must lie in [1, 512]. */
+typedef struct pct_grid {
+  int32_t nx, ny, nz;
+  double hx, hy, hz;
+} pct_grid;
+
+/* Solver options (Sec. 2.1: user-determined number of blocks; the number of
+ * iterations is passed to pct_iterate). */
+typedef struct pct_config {
+  int32_t n_blocks;         /* DROP blocks B >= 1; block b holds histories
+                               [b*N/B, (b+1)*N/B) in load order               */
+  float lambda;             /* relaxation, 0 < lambda < 2 (default 1)         */
+  double node_step_mm;      /* MLP node spacing request; <= 0: min(h)/2        */
+  int32_t flags;            /* PCT_FLAG_*                                      */
+  float clamp_min;          /* lower clamp of x after each block (with flag)   */
+  int32_t threads_per_proton; /* 1 (reserved for 2, 4, 8)                      */
+  int32_t cta_threads;      /* threads per CTA of the fused kernel; 0 = 128    */
+} pct_config;
+
+#define PCT_FLAG_CLAMP 1    /* x_j = max(x_j, clamp_min) after each block      */
+#define PCT_FLAG_NO_KAHAN 2 /* plain instead of compensated a_i.x (precision study) */
+#define PCT_FLAG_PROFILE 4  /* record CUDA events around every fused launch
+                               (read with pct_last_sweep_times)               */
+
+/* One history per index: entry state at u = -R, exit state at u = +R, the
+ * WEPL b_i (mm) and the gantry angle as cos/sin (Sec. 2: "entry position and
+ * direction", "exit position and direction", WEPL). Eleven float arrays of n
+ * elements each (structure of arrays). */
+typedef struct pct_histories {
+  int64_t n;
+  const float *t0, *v0, *st0, *sv0; /* lateral / vertical position and slope at u = -R */
+  const float *t2, *v2, *st2, *sv2; /* the same at u = +R                            */
+  const float *wepl;                /* water-equivalent path length, mm              */
+  const float *cphi, *sphi;         /* cos and sin of the gantry angle               */
+} pct_histories;
+
+/* pct_load_histories flags */
+#define PCT_LOAD_HOST 0          /* arrays are host memory; copied to the device   */
+#define PCT_LOAD_DEVICE_COPY 1   /* device arrays; copied into context storage     */
+#define PCT_LOAD_DEVICE_BORROW 2 /* device arrays used in place; the caller keeps
+                                    them alive and unchanged until pct_destroy or
+                                    the next load                                 */
+
+typedef struct pct_ctx pct_ctx;
+
+/* Create a context for one grid on CUDA device `device`. Builds the FP64 MLP
+ * coefficient table on the GPU (Sec. 2, MLP of Schulte et al. 2008: first rows
+ * of (S1^-1 + R1^T S2^-1 R1)^-1 S1^-1 R0 and ... R1^T S2^-1 per node).
+ * *out receives the context; on error *out is NULL. */
+PCT_API pct_status pct_create(pct_ctx **out, const pct_grid *grid, const pct_config *cfg, int device);
+
+/* Free all device buffers, graphs and the stream owned by ctx. NULL is a no-op. */
+PCT_API pct_status pct_destroy(pct_ctx *ctx);
+
+/* Use `stream` (a cudaStream_t, or the special handles cudaStreamLegacy /
+ * cudaStreamPerThread; NULL = the context's own non-blocking stream) for all
+ * later device work of ctx. The caller keeps the stream alive. */
+PCT_API pct_status pct_set_stream(pct_ctx *ctx, void *stream);
+
+/* Derived geometry: plane half-distance R (mm), node spacing du (mm),
+ * interior node count K+1 (nodes k = 0..K at u = -R + k du), extension nodes
+ * per side E, voxel count M. Any pointer may be NULL. */
+PCT_API pct_status pct_geometry(const pct_ctx *ctx, double *R, double *du, int32_t *K, int32_t *E, int64_t *M);
+
+/* Copy the FP64 MLP table, (K+1) x 4 doubles (c1, c2 [mm], c3, c4 [mm]; node
+ * k lateral position t_k = c1 t0 + c2 st0 + c3 t2 + c4 st2), to `out` (host
+ * memory if to_device == 0, else device memory). Synchronises on host copies. */
+PCT_API pct_status pct_mlp_table(pct_ctx *ctx, double *out, int to_device);
+
+/* Load N histories (Sec. 2). Validates every record on the GPU: finite
+ * values, |slope| < 0.5, |t|,|v| within the position limit, wepl >= 0,
+ * |cos^2 + sin^2 - 1| < 1e-3. On failure returns PCT_ERR_INVALID_DATA and
+ * the first bad index in *first_bad (may be NULL; -1 when all are valid).
+ * Then computes each block's run counts s_j (DROP's diagonal weights) and
+ * resets x to 0. Synchronises. */
+PCT_API pct_status pct_load_histories(pct_ctx *ctx, const pct_histories *h, int flags, int64_t *first_bad);
+
+/* Rows a_i of histories [first, first+count) of the loaded set, in CSR form,
+ * all DEVICE pointers: row_ptr (count+1 int64), vox (cap int32 voxel
+ * indices), len (cap float chord lengths in mm, in path order; a run is a
+ * maximal stretch in one voxel, zero-length runs never appear). `nodes`
+ * (optional, may be NULL) receives count x (K+1) x 3 int32: the interior MLP
+ * nodes in Q20 fixed point grid units. *needed receives the total number of
+ * runs; if it exceeds cap, returns PCT_ERR_CAPACITY and writes no runs.
+ * Synchronises. */
+PCT_API pct_status pct_mlp_rows(pct_ctx *ctx, int64_t first, int64_t count, int64_t *row_ptr, int32_t *vox, float *len,
+                        int64_t cap, int32_t *nodes, int64_t *needed);
+
+/* Run counts s_j of DROP block `block` as float (exact integers), M values,
+ * written to DEVICE memory `out`. */
+PCT_API pct_status pct_block_counts(pct_ctx *ctx, int32_t block, float *out);
+
+/* Set the initial image x0 (M floats; device memory if on_device, else host). */
+PCT_API pct_status pct_set_x0(pct_ctx *ctx, const float *x0, int on_device);
+
+/* Run n_sweeps DROP iterations (Sec. 2.1, Fig. 1): for each block b in
+ * order, every history i of b contributes lambda (b_i - a_i.x)/|a_i|^2 a_i
+ * (a_i recomputed from the MLP, a_i.x compensated), then
+ * x_j += delta_j / s_j. Asynchronous on the context stream; one CUDA graph
+ * per sweep. */
+PCT_API pct_status pct_iterate(pct_ctx *ctx, int32_t n_sweeps);
+
+/* With PCT_FLAG_PROFILE: wait for the queued work, then write the device
+ * time (ms) of each block's fused MLP + projection kernel and of each block's
+ * apply kernel in the most recent sweep to fused_ms[b] and apply_ms[b]
+ * (n_blocks entries each, host memory; either may be NULL). Returns
+ * PCT_ERR_STATE without the flag or before the first sweep. */
+PCT_API pct_status pct_last_sweep_times(pct_ctx *ctx, float *fused_ms, float *apply_ms);
+
+/* Copy x (M floats) to `out` (host memory if to_device == 0, else device).
+ * Synchronises for host copies and reports device-side errors. */
+PCT_API pct_status pct_get_rsp(pct_ctx *ctx, float *out, int to_device);
+
+/* Wait for all queued work of ctx; report device-side errors. */
+PCT_API pct_status pct_sync(pct_ctx *ctx);
+
+/* Kernel launches queued by this context since creation (for accounting). */
+PCT_API int64_t pct_launch_count(const pct_ctx *ctx);
+
+/* Text for the last error of the calling thread ("" if none). */
+PCT_API const char *pct_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PCT_H */

@@ -1,0 +1,453 @@
+// C ABI of libpct (declared in include/pct.h): context, buffers, loading,
+// row export and the DROP iteration loop under a captured CUDA graph.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+
+#include "../../include/pct.h"
+#include "pct_internal.h"
+
+using pct::Geo;
+using pct::Rec;
+
+struct pct_ctx {
+  int device = 0;
+  pct_grid grid{};
+  pct_config cfg{};
+  Geo geo{};
+  double R = 0, du = 0;
+  int K = 0, E = 0;
+  int64_t M = 0;
+  float pos_limit = 0;
+  cudaStream_t own_stream = nullptr;  // created by the context; also the capture stream
+  cudaStream_t stream = nullptr;      // where work is queued
+  double* tab64 = nullptr;
+  float4* tab32 = nullptr;
+  int64_t n = 0;
+  float* rec_store = nullptr;  // owned copy of the 11 record arrays (null when borrowed)
+  Rec rec{};
+  float* x = nullptr;
+  float* delta = nullptr;
+  float* inv_s = nullptr;  // B x M
+  unsigned int* cnt = nullptr;
+  unsigned long long* first_bad = nullptr;
+  cudaGraphExec_t sweep = nullptr;
+  cudaEvent_t* ev = nullptr;  // 3 per block (profiling): fused start, fused end, apply end
+  bool swept = false;
+  int64_t launches = 0;
+  bool loaded = false;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+pct_status fail(pct_status code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+#define PCT_CK(call)                                                                          \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess) return fail(PCT_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+#define PCT_ALLOC(ptr, bytes)                                                                         \
+  do {                                                                                                \
+    cudaError_t e_ = cudaMalloc((void**)&(ptr), (bytes));                                             \
+    if (e_ != cudaSuccess) {                                                                          \
+      (void)cudaGetLastError();                                                                       \
+      return fail(PCT_ERR_NO_MEMORY, "cudaMalloc(%lld bytes): %s", (long long)(bytes), cudaGetErrorString(e_)); \
+    }                                                                                                 \
+  } while (0)
+
+void free_records(pct_ctx* c) {
+  if (c->sweep) cudaGraphExecDestroy(c->sweep);
+  c->sweep = nullptr;
+  c->swept = false;
+  if (c->rec_store) cudaFree(c->rec_store);
+  c->rec_store = nullptr;
+  if (c->inv_s) cudaFree(c->inv_s);
+  c->inv_s = nullptr;
+  c->rec = Rec{};
+  c->n = 0;
+  c->loaded = false;
+}
+
+int64_t block_lo(const pct_ctx* c, int b) { return (int64_t)b * c->n / c->cfg.n_blocks; }
+
+pct_status sync_and_check(pct_ctx* c) {
+  PCT_CK(cudaStreamSynchronize(c->stream));
+  PCT_CK(cudaGetLastError());
+  return PCT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* pct_last_error(void) { return g_err.c_str(); }
+
+pct_status pct_create(pct_ctx** out, const pct_grid* grid, const pct_config* cfg, int device) {
+  if (!out) return fail(PCT_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!grid || !cfg) return fail(PCT_ERR_INVALID_ARG, "grid or cfg is NULL");
+  const pct_grid& g = *grid;
+  if (g.nx < 1 || g.ny < 1 || g.nz < 1 || g.nx > pct::kMaxDim || g.ny > pct::kMaxDim || g.nz > pct::kMaxDim)
+    return fail(PCT_ERR_INVALID_ARG, "grid dims must be in [1, %d]", pct::kMaxDim);
+  if (!(g.hx > 0 && g.hy > 0 && g.hz > 0) || !isfinite(g.hx) || !isfinite(g.hy) || !isfinite(g.hz))
+    return fail(PCT_ERR_INVALID_ARG, "voxel sizes must be finite and > 0");
+  if (cfg->n_blocks < 1) return fail(PCT_ERR_INVALID_ARG, "n_blocks must be >= 1");
+  if (!(cfg->lambda > 0.f && cfg->lambda < 2.f)) return fail(PCT_ERR_INVALID_ARG, "lambda must be in (0, 2)");
+  if (cfg->threads_per_proton != 0 && cfg->threads_per_proton != 1)
+    return fail(PCT_ERR_INVALID_ARG, "threads_per_proton must be 1");
+
+  pct_ctx* c = new pct_ctx();
+  c->device = device;
+  c->grid = g;
+  c->cfg = *cfg;
+  if (c->cfg.cta_threads <= 0) c->cfg.cta_threads = 128;
+
+  // Geometry in FP64, then rounded once to FP32 for the kernels.
+  const double X = g.nx * g.hx, Y = g.ny * g.hy, Z = g.nz * g.hz;
+  const double hmin = fmin(g.hx, fmin(g.hy, g.hz));
+  const double step = cfg->node_step_mm > 0 ? cfg->node_step_mm : 0.5 * hmin;
+  c->R = 0.5 * fmin(X, Y);
+  c->K = (int)ceil(2.0 * c->R / step - 1e-9);
+  if (c->K < 2 || c->K + 1 > pct::kMaxNodes) {
+    delete c;
+    return fail(PCT_ERR_INVALID_ARG, "node count K+1 = %d outside [3, %d]", c->K + 1, pct::kMaxNodes);
+  }
+  c->du = 2.0 * c->R / c->K;
+  const double hd_xy = 0.5 * sqrt(X * X + Y * Y);
+  c->E = (int)ceil((hd_xy - c->R) / c->du) + 2;
+  c->M = (int64_t)g.nx * g.ny * g.nz;
+  c->pos_limit = (float)(0.5 * sqrt(X * X + Y * Y + Z * Z) + c->R);
+  {
+    // worst-case node distance from the grid centre, in voxels: must stay
+    // inside the +-1000 voxel quantisation range for every valid record
+    const double umax = c->R + (c->E + 1) * c->du;
+    const double tmax = c->pos_limit + 0.5 * (2.0 * c->R + c->E * c->du);
+    const double qmax = (umax + tmax) / hmin + 0.5 * fmax((double)g.nx, fmax((double)g.ny, (double)g.nz));
+    if (qmax >= pct::kQClamp) {
+      delete c;
+      return fail(PCT_ERR_INVALID_ARG, "grid too large for the fixed-point node range (%.0f voxels)", qmax);
+    }
+  }
+  Geo& G = c->geo;
+  G.nx = g.nx;
+  G.ny = g.ny;
+  G.nz = g.nz;
+  G.K = c->K;
+  G.E = c->E;
+  G.du = (float)c->du;
+  G.u0 = (float)(-c->R);
+  G.ihx = (float)(1.0 / g.hx);
+  G.ihy = (float)(1.0 / g.hy);
+  G.ihz = (float)(1.0 / g.hz);
+  G.hnx = 0.5f * (float)g.nx;
+  G.hny = 0.5f * (float)g.ny;
+  G.hnz = 0.5f * (float)g.nz;
+  G.lx = (float)(g.hx / (double)pct::kQOne);
+  G.ly = (float)(g.hy / (double)pct::kQOne);
+  G.lz = (float)(g.hz / (double)pct::kQOne);
+  G.bx = (float)(0.5 * X);
+  G.by = (float)(0.5 * Y);
+  G.bz = (float)(0.5 * Z);
+  G.R = (float)c->R;
+
+  pct_status st = PCT_OK;
+  do {
+    cudaError_t e = cudaSetDevice(device);
+    if (e != cudaSuccess) {
+      st = fail(PCT_ERR_CUDA, "cudaSetDevice(%d): %s", device, cudaGetErrorString(e));
+      break;
+    }
+    e = cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      st = fail(PCT_ERR_CUDA, "cudaStreamCreate: %s", cudaGetErrorString(e));
+      break;
+    }
+    c->stream = c->own_stream;
+    size_t M = (size_t)c->M;
+    if (cudaMalloc((void**)&c->tab64, (c->K + 1) * 4 * sizeof(double)) != cudaSuccess ||
+        cudaMalloc((void**)&c->tab32, (c->K + 1) * sizeof(float4)) != cudaSuccess ||
+        cudaMalloc((void**)&c->x, M * sizeof(float)) != cudaSuccess ||
+        cudaMalloc((void**)&c->delta, M * sizeof(float)) != cudaSuccess ||
+        cudaMalloc((void**)&c->cnt, M * sizeof(unsigned int)) != cudaSuccess ||
+        cudaMalloc((void**)&c->first_bad, sizeof(unsigned long long)) != cudaSuccess) {
+      (void)cudaGetLastError();
+      st = fail(PCT_ERR_NO_MEMORY, "device allocation failed for a %lld-voxel grid", (long long)c->M);
+      break;
+    }
+    if ((e = cudaMemsetAsync(c->x, 0, M * sizeof(float), c->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(c->delta, 0, M * sizeof(float), c->stream)) != cudaSuccess ||
+        (e = pct::launch_mlp_table(c->R, c->du, c->K, c->tab64, c->tab32, c->stream)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(c->stream)) != cudaSuccess) {
+      st = fail(PCT_ERR_CUDA, "context set-up: %s", cudaGetErrorString(e));
+      break;
+    }
+    c->launches += 1;
+    if (c->cfg.flags & PCT_FLAG_PROFILE) {
+      c->ev = new cudaEvent_t[3 * c->cfg.n_blocks]();
+      for (int i = 0; i < 3 * c->cfg.n_blocks && e == cudaSuccess; ++i) e = cudaEventCreate(&c->ev[i]);
+      if (e != cudaSuccess) {
+        st = fail(PCT_ERR_CUDA, "cudaEventCreate: %s", cudaGetErrorString(e));
+        break;
+      }
+    }
+  } while (0);
+  if (st != PCT_OK) {
+    pct_destroy(c);
+    return st;
+  }
+  *out = c;
+  return PCT_OK;
+}
+
+pct_status pct_destroy(pct_ctx* c) {
+  if (!c) return PCT_OK;
+  cudaSetDevice(c->device);
+  if (c->own_stream) cudaStreamSynchronize(c->own_stream);
+  if (c->stream && c->stream != c->own_stream) cudaStreamSynchronize(c->stream);
+  free_records(c);
+  cudaFree(c->tab64);
+  cudaFree(c->tab32);
+  cudaFree(c->x);
+  cudaFree(c->delta);
+  cudaFree(c->cnt);
+  cudaFree(c->first_bad);
+  if (c->ev) {
+    for (int i = 0; i < 3 * c->cfg.n_blocks; ++i) cudaEventDestroy(c->ev[i]);
+    delete[] c->ev;
+  }
+  if (c->own_stream) cudaStreamDestroy(c->own_stream);
+  delete c;
+  return PCT_OK;
+}
+
+pct_status pct_set_stream(pct_ctx* c, void* stream) {
+  if (!c) return fail(PCT_ERR_INVALID_ARG, "ctx is NULL");
+  c->stream = stream ? (cudaStream_t)stream : c->own_stream;
+  return PCT_OK;
+}
+
+pct_status pct_geometry(const pct_ctx* c, double* R, double* du, int32_t* K, int32_t* E, int64_t* M) {
+  if (!c) return fail(PCT_ERR_INVALID_ARG, "ctx is NULL");
+  if (R) *R = c->R;
+  if (du) *du = c->du;
+  if (K) *K = c->K;
+  if (E) *E = c->E;
+  if (M) *M = c->M;
+  return PCT_OK;
+}
+
+pct_status pct_mlp_table(pct_ctx* c, double* out, int to_device) {
+  if (!c || !out) return fail(PCT_ERR_INVALID_ARG, "ctx or out is NULL");
+  PCT_CK(cudaSetDevice(c->device));
+  size_t bytes = (size_t)(c->K + 1) * 4 * sizeof(double);
+  PCT_CK(cudaMemcpyAsync(out, c->tab64, bytes, to_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                         c->stream));
+  if (!to_device) return sync_and_check(c);
+  return PCT_OK;
+}
+
+pct_status pct_load_histories(pct_ctx* c, const pct_histories* h, int flags, int64_t* first_bad) {
+  if (first_bad) *first_bad = -1;
+  if (!c || !h) return fail(PCT_ERR_INVALID_ARG, "ctx or histories is NULL");
+  if (h->n < 1) return fail(PCT_ERR_INVALID_ARG, "n must be >= 1");
+  if (h->n < c->cfg.n_blocks) return fail(PCT_ERR_INVALID_ARG, "n (%lld) < n_blocks (%d)", (long long)h->n,
+                                          c->cfg.n_blocks);
+  const float* src[11] = {h->t0, h->v0, h->st0, h->sv0, h->t2, h->v2, h->st2, h->sv2, h->wepl, h->cphi, h->sphi};
+  for (int f = 0; f < 11; ++f)
+    if (!src[f]) return fail(PCT_ERR_INVALID_ARG, "history array %d is NULL", f);
+  if (flags != PCT_LOAD_HOST && flags != PCT_LOAD_DEVICE_COPY && flags != PCT_LOAD_DEVICE_BORROW)
+    return fail(PCT_ERR_INVALID_ARG, "unknown load flags %d", flags);
+  PCT_CK(cudaSetDevice(c->device));
+  PCT_CK(cudaStreamSynchronize(c->stream));
+  free_records(c);
+  const int64_t n = h->n;
+  const float* dst[11];
+  if (flags == PCT_LOAD_DEVICE_BORROW) {
+    for (int f = 0; f < 11; ++f) dst[f] = src[f];
+  } else {
+    PCT_ALLOC(c->rec_store, (size_t)n * 11 * sizeof(float));
+    for (int f = 0; f < 11; ++f) {
+      float* d = c->rec_store + (size_t)f * n;
+      PCT_CK(cudaMemcpyAsync(d, src[f], (size_t)n * sizeof(float),
+                             flags == PCT_LOAD_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, c->stream));
+      dst[f] = d;
+    }
+  }
+  c->rec = Rec{dst[0], dst[1], dst[2], dst[3], dst[4], dst[5], dst[6], dst[7], dst[8], dst[9], dst[10]};
+  c->n = n;
+
+  // validation
+  PCT_CK(cudaMemsetAsync(c->first_bad, 0xff, sizeof(unsigned long long), c->stream));
+  PCT_CK(pct::launch_validate(c->rec, n, c->pos_limit, c->first_bad, c->stream));
+  c->launches += 1;
+  unsigned long long fb = 0;
+  PCT_CK(cudaMemcpyAsync(&fb, c->first_bad, sizeof fb, cudaMemcpyDeviceToHost, c->stream));
+  PCT_CK(cudaStreamSynchronize(c->stream));
+  if (fb != ~0ull) {
+    if (first_bad) *first_bad = (int64_t)fb;
+    free_records(c);
+    return fail(PCT_ERR_INVALID_DATA, "history %lld failed validation", (long long)fb);
+  }
+
+  // DROP block weights: s_j = runs of block b in voxel j; store 1/s_j
+  const int B = c->cfg.n_blocks;
+  PCT_ALLOC(c->inv_s, (size_t)B * c->M * sizeof(float));
+  for (int b = 0; b < B; ++b) {
+    const int64_t lo = block_lo(c, b), hi = block_lo(c, b + 1);
+    PCT_CK(cudaMemsetAsync(c->cnt, 0, (size_t)c->M * sizeof(unsigned int), c->stream));
+    PCT_CK(pct::launch_count(c->geo, c->rec, c->tab32, lo, hi - lo, c->cnt, c->cfg.cta_threads, c->stream));
+    PCT_CK(pct::launch_inv_counts(c->cnt, c->inv_s + (size_t)b * c->M, c->M, c->stream));
+    c->launches += 2;
+  }
+  PCT_CK(cudaMemsetAsync(c->x, 0, (size_t)c->M * sizeof(float), c->stream));
+  PCT_CK(cudaMemsetAsync(c->delta, 0, (size_t)c->M * sizeof(float), c->stream));
+  pct_status st = sync_and_check(c);
+  if (st != PCT_OK) return st;
+  c->loaded = true;
+  return PCT_OK;
+}
+
+pct_status pct_mlp_rows(pct_ctx* c, int64_t first, int64_t count, int64_t* row_ptr, int32_t* vox, float* len,
+                        int64_t cap, int32_t* nodes, int64_t* needed) {
+  if (needed) *needed = 0;
+  if (!c || !row_ptr) return fail(PCT_ERR_INVALID_ARG, "ctx or row_ptr is NULL");
+  if (!c->loaded) return fail(PCT_ERR_STATE, "no histories loaded");
+  if (first < 0 || count < 0 || first + count > c->n) return fail(PCT_ERR_INVALID_ARG, "range outside [0, n)");
+  if (cap < 0 || (cap > 0 && (!vox || !len))) return fail(PCT_ERR_INVALID_ARG, "bad row buffers");
+  PCT_CK(cudaSetDevice(c->device));
+  PCT_CK(pct::launch_row_counts(c->geo, c->rec, c->tab32, first, count, row_ptr, c->stream));
+  PCT_CK(pct::launch_scan_rows(row_ptr, count, c->stream));
+  c->launches += 2;
+  int64_t total = 0;
+  PCT_CK(cudaMemcpyAsync(&total, row_ptr + count, sizeof total, cudaMemcpyDeviceToHost, c->stream));
+  PCT_CK(cudaStreamSynchronize(c->stream));
+  if (needed) *needed = total;
+  if (total > cap) return fail(PCT_ERR_CAPACITY, "rows need %lld runs, capacity %lld", (long long)total,
+                               (long long)cap);
+  PCT_CK(pct::launch_row_fill(c->geo, c->rec, c->tab32, first, count, row_ptr, vox, len, nodes, c->stream));
+  c->launches += 1;
+  return sync_and_check(c);
+}
+
+pct_status pct_block_counts(pct_ctx* c, int32_t block, float* out) {
+  if (!c || !out) return fail(PCT_ERR_INVALID_ARG, "ctx or out is NULL");
+  if (!c->loaded) return fail(PCT_ERR_STATE, "no histories loaded");
+  if (block < 0 || block >= c->cfg.n_blocks) return fail(PCT_ERR_INVALID_ARG, "block out of range");
+  PCT_CK(cudaSetDevice(c->device));
+  const int64_t lo = block_lo(c, block), hi = block_lo(c, block + 1);
+  PCT_CK(cudaMemsetAsync(c->cnt, 0, (size_t)c->M * sizeof(unsigned int), c->stream));
+  PCT_CK(pct::launch_count(c->geo, c->rec, c->tab32, lo, hi - lo, c->cnt, c->cfg.cta_threads, c->stream));
+  PCT_CK(pct::launch_counts_to_float(c->cnt, out, c->M, c->stream));
+  c->launches += 2;
+  return PCT_OK;
+}
+
+pct_status pct_set_x0(pct_ctx* c, const float* x0, int on_device) {
+  if (!c || !x0) return fail(PCT_ERR_INVALID_ARG, "ctx or x0 is NULL");
+  PCT_CK(cudaSetDevice(c->device));
+  PCT_CK(cudaMemcpyAsync(c->x, x0, (size_t)c->M * sizeof(float),
+                         on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+  if (!on_device) return sync_and_check(c);
+  return PCT_OK;
+}
+
+static pct_status build_sweep_graph(pct_ctx* c) {
+  cudaGraph_t graph = nullptr;
+  cudaStream_t s = c->own_stream;
+  PCT_CK(cudaStreamSynchronize(s));
+  PCT_CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  cudaError_t err = cudaSuccess;
+  const int B = c->cfg.n_blocks;
+  const int clamp = (c->cfg.flags & PCT_FLAG_CLAMP) != 0;
+  for (int b = 0; b < B && err == cudaSuccess; ++b) {
+    const int64_t lo = block_lo(c, b), hi = block_lo(c, b + 1);
+    if (c->ev) err = cudaEventRecordWithFlags(c->ev[3 * b], s, cudaEventRecordExternal);
+    if (err == cudaSuccess)
+      err = pct::launch_drop_fused(c->geo, c->rec, c->tab32, lo, hi - lo, c->x, c->delta, c->cfg.lambda,
+                                   c->cfg.flags, c->cfg.cta_threads, s);
+    if (err == cudaSuccess && c->ev) err = cudaEventRecordWithFlags(c->ev[3 * b + 1], s, cudaEventRecordExternal);
+    if (err == cudaSuccess)
+      err = pct::launch_drop_apply(c->x, c->delta, c->inv_s + (size_t)b * c->M, c->M, clamp, c->cfg.clamp_min, s);
+    if (err == cudaSuccess && c->ev) err = cudaEventRecordWithFlags(c->ev[3 * b + 2], s, cudaEventRecordExternal);
+  }
+  cudaError_t e2 = cudaStreamEndCapture(s, &graph);
+  if (err != cudaSuccess || e2 != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    (void)cudaGetLastError();
+    return fail(PCT_ERR_CUDA, "sweep capture: %s", cudaGetErrorString(err != cudaSuccess ? err : e2));
+  }
+  cudaError_t e3 = cudaGraphInstantiate(&c->sweep, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e3 != cudaSuccess) {
+    c->sweep = nullptr;
+    return fail(PCT_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e3));
+  }
+  return PCT_OK;
+}
+
+pct_status pct_iterate(pct_ctx* c, int32_t n_sweeps) {
+  if (!c) return fail(PCT_ERR_INVALID_ARG, "ctx is NULL");
+  if (!c->loaded) return fail(PCT_ERR_STATE, "no histories loaded");
+  if (n_sweeps < 0) return fail(PCT_ERR_INVALID_ARG, "n_sweeps < 0");
+  PCT_CK(cudaSetDevice(c->device));
+  if (!c->sweep) {
+    // the capture stream must not have pending work from another stream
+    if (c->stream != c->own_stream) PCT_CK(cudaStreamSynchronize(c->stream));
+    pct_status st = build_sweep_graph(c);
+    if (st != PCT_OK) return st;
+  }
+  for (int s = 0; s < n_sweeps; ++s) PCT_CK(cudaGraphLaunch(c->sweep, c->stream));
+  c->launches += (int64_t)n_sweeps * 2 * c->cfg.n_blocks;
+  if (n_sweeps > 0) c->swept = true;
+  return PCT_OK;
+}
+
+pct_status pct_last_sweep_times(pct_ctx* c, float* fused_ms, float* apply_ms) {
+  if (!c) return fail(PCT_ERR_INVALID_ARG, "ctx is NULL");
+  if (!c->ev || !c->swept) return fail(PCT_ERR_STATE, "profiling off or no sweep run yet");
+  PCT_CK(cudaSetDevice(c->device));
+  pct_status st = sync_and_check(c);
+  if (st != PCT_OK) return st;
+  for (int b = 0; b < c->cfg.n_blocks; ++b) {
+    float f = 0.f, a = 0.f;
+    PCT_CK(cudaEventElapsedTime(&f, c->ev[3 * b], c->ev[3 * b + 1]));
+    PCT_CK(cudaEventElapsedTime(&a, c->ev[3 * b + 1], c->ev[3 * b + 2]));
+    if (fused_ms) fused_ms[b] = f;
+    if (apply_ms) apply_ms[b] = a;
+  }
+  return PCT_OK;
+}
+
+pct_status pct_get_rsp(pct_ctx* c, float* out, int to_device) {
+  if (!c || !out) return fail(PCT_ERR_INVALID_ARG, "ctx or out is NULL");
+  PCT_CK(cudaSetDevice(c->device));
+  PCT_CK(cudaMemcpyAsync(out, c->x, (size_t)c->M * sizeof(float),
+                         to_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+  if (!to_device) return sync_and_check(c);
+  return PCT_OK;
+}
+
+pct_status pct_sync(pct_ctx* c) {
+  if (!c) return fail(PCT_ERR_INVALID_ARG, "ctx is NULL");
+  PCT_CK(cudaSetDevice(c->device));
+  return sync_and_check(c);
+}
+
+int64_t pct_launch_count(const pct_ctx* c) { return c ? c->launches : 0; }
+
+}  // extern "C"

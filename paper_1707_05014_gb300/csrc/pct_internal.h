@@ -1,0 +1,54 @@
+// Internal declarations shared by the library's translation units (not part
+// of the C ABI). Device-side structs are passed to kernels by value.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pct {
+
+constexpr int kQBits = 20;               // Q20 fixed-point grid coordinates
+constexpr int32_t kQOne = 1 << kQBits;   // one voxel
+constexpr float kQClamp = 1000.0f;       // |q| clamp in voxels (never reached for valid records)
+constexpr int kMaxNodes = 2048;          // K + 1 limit (shared-memory MLP table)
+constexpr int kMaxDim = 512;             // per-axis voxel limit
+
+// Grid and node geometry in the single-precision form the kernels use.
+struct Geo {
+  int nx, ny, nz;
+  int K;          // interior nodes k = 0..K
+  int E;          // straight extension nodes per side (k = -E..-1, K+1..K+E)
+  float du;       // node spacing (mm), rounded from FP64
+  float u0;       // first measurement plane (-R), rounded from FP64
+  float ihx, ihy, ihz;  // 1/h rounded from FP64
+  float hnx, hny, hnz;  // n/2
+  float lx, ly, lz;     // h * 2^-20: mm per Q20 unit
+  float bx, by, bz;     // half box extents (mm)
+  float R;              // plane half distance (mm)
+};
+
+// Structure-of-arrays history records (device pointers).
+struct Rec {
+  const float *t0, *v0, *st0, *sv0, *t2, *v2, *st2, *sv2, *wepl, *cphi, *sphi;
+};
+
+// Launchers (pct_kernels.cu / pct_table.cu). All enqueue on `s` and return
+// the launch error (cudaSuccess when queued).
+cudaError_t launch_mlp_table(double R, double du, int K, double* tab64, float4* tab32, cudaStream_t s);
+cudaError_t launch_validate(const Rec& r, int64_t n, float pos_limit, unsigned long long* first_bad,
+                            cudaStream_t s);
+cudaError_t launch_count(const Geo& g, const Rec& r, const float4* tab, int64_t first, int64_t count,
+                         unsigned int* cnt, int threads, cudaStream_t s);
+cudaError_t launch_inv_counts(const unsigned int* cnt, float* inv_s, int64_t M, cudaStream_t s);
+cudaError_t launch_counts_to_float(const unsigned int* cnt, float* out, int64_t M, cudaStream_t s);
+cudaError_t launch_drop_fused(const Geo& g, const Rec& r, const float4* tab, int64_t first, int64_t count,
+                              const float* x, float* delta, float lambda, int flags, int threads, cudaStream_t s);
+cudaError_t launch_drop_apply(float* x, float* delta, const float* inv_s, int64_t M, int clamp, float clamp_min,
+                              cudaStream_t s);
+cudaError_t launch_row_counts(const Geo& g, const Rec& r, const float4* tab, int64_t first, int64_t count,
+                              int64_t* row_ptr, cudaStream_t s);
+cudaError_t launch_scan_rows(int64_t* row_ptr, int64_t count, cudaStream_t s);
+cudaError_t launch_row_fill(const Geo& g, const Rec& r, const float4* tab, int64_t first, int64_t count,
+                            const int64_t* row_ptr, int32_t* vox, float* len, int32_t* nodes, cudaStream_t s);
+
+}  // namespace pct

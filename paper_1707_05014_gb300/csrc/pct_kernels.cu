@@ -1,0 +1,228 @@
+// Hot-path kernels: record validation, per-block run counts, the fused
+// MLP + DROP projection kernel, the block apply, and the CSR row export.
+//
+// DROP (arXiv 1707.05014 Sec. 2.1, Fig. 1), block b:
+//   for i in b:  r_i = lambda (b_i - a_i.x) / |a_i|^2,  delta += r_i a_i
+//   x_j += delta_j / s_j     (s_j = number of runs of block b in voxel j)
+// The fused kernel computes a_i twice from the MLP (once for a_i.x and
+// |a_i|^2, once for the scatter) instead of storing it.
+#include "pct_walk.cuh"
+
+namespace pct {
+namespace {
+
+__device__ __forceinline__ void load_table(const float4* __restrict__ src, float4* dst, int n) {
+  for (int k = threadIdx.x; k < n; k += blockDim.x) dst[k] = src[k];
+  __syncthreads();
+}
+
+__device__ __forceinline__ bool bad_float(float v) { return !isfinite(v); }
+
+__global__ void validate_kernel(Rec r, int64_t n, float pos_limit, unsigned long long* first_bad) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const RecV v = load_rec(r, i);
+  bool bad = bad_float(v.t0) || bad_float(v.v0) || bad_float(v.st0) || bad_float(v.sv0) || bad_float(v.t2) ||
+             bad_float(v.v2) || bad_float(v.st2) || bad_float(v.sv2) || bad_float(v.wepl) || bad_float(v.cp) ||
+             bad_float(v.sp);
+  bad = bad || fabsf(v.st0) >= 0.5f || fabsf(v.sv0) >= 0.5f || fabsf(v.st2) >= 0.5f || fabsf(v.sv2) >= 0.5f;
+  bad = bad || fabsf(v.t0) > pos_limit || fabsf(v.v0) > pos_limit || fabsf(v.t2) > pos_limit ||
+        fabsf(v.v2) > pos_limit;
+  bad = bad || v.wepl < 0.f || fabsf(v.cp * v.cp + v.sp * v.sp - 1.f) > 1e-3f;
+  if (bad) atomicMin(first_bad, (unsigned long long)i);
+}
+
+__global__ void count_kernel(Geo g, Rec r, const float4* __restrict__ tab_g, int64_t first, int64_t count,
+                             unsigned int* __restrict__ cnt) {
+  extern __shared__ float4 tab[];
+  load_table(tab_g, tab, g.K + 1);
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= count) return;
+  const RecV v = load_rec(r, first + p);
+  walk_proton(g, tab, v, [&](int j, float) { atomicAdd(cnt + j, 1u); });
+}
+
+__global__ void inv_counts_kernel(const unsigned int* __restrict__ cnt, float* __restrict__ inv_s, int64_t M) {
+  int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= M) return;
+  unsigned c = cnt[j];
+  inv_s[j] = c ? 1.0f / (float)c : 0.0f;
+}
+
+__global__ void counts_to_float_kernel(const unsigned int* __restrict__ cnt, float* __restrict__ out, int64_t M) {
+  int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= M) return;
+  out[j] = (float)cnt[j];
+}
+
+// One thread per proton: MLP nodes -> walk -> compensated a_i.x and |a_i|^2
+// -> relaxed residual -> walk again -> scatter-add into delta.
+__global__ void __launch_bounds__(128) drop_fused_kernel(Geo g, Rec r, const float4* __restrict__ tab_g,
+                                                          int64_t first, int64_t count, const float* __restrict__ x,
+                                                          float* __restrict__ delta, float lambda, int flags) {
+  extern __shared__ float4 tab[];
+  load_table(tab_g, tab, g.K + 1);
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= count) return;
+  const RecV v = load_rec(r, first + p);
+  float y = 0.f, c = 0.f, nn = 0.f;
+  if (flags & 2) {
+    walk_proton(g, tab, v, [&](int j, float l) {
+      y = __fmaf_rn(l, __ldg(x + j), y);
+      nn = __fmaf_rn(l, l, nn);
+    });
+  } else {
+    // Kahan-compensated sum of l * x_j: the true sum is y - c
+    walk_proton(g, tab, v, [&](int j, float l) {
+      const float term = __fsub_rn(__fmul_rn(l, __ldg(x + j)), c);
+      const float t = __fadd_rn(y, term);
+      c = __fsub_rn(__fsub_rn(t, y), term);
+      y = t;
+      nn = __fmaf_rn(l, l, nn);
+    });
+  }
+  if (!(nn > 0.f)) return;
+  const float res = __fadd_rn(__fsub_rn(v.wepl, y), c);
+  const float ri = lambda * res / nn;
+  walk_proton(g, tab, v, [&](int j, float l) { atomicAdd(delta + j, l * ri); });
+}
+
+__global__ void drop_apply_kernel(float* __restrict__ x, float* __restrict__ delta, const float* __restrict__ inv_s,
+                                  int64_t M, int clamp, float clamp_min) {
+  int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= M) return;
+  float xv = __fmaf_rn(delta[j], inv_s[j], x[j]);
+  if (clamp) xv = fmaxf(xv, clamp_min);
+  x[j] = xv;
+  delta[j] = 0.f;
+}
+
+__global__ void row_count_kernel(Geo g, Rec r, const float4* __restrict__ tab_g, int64_t first, int64_t count,
+                                 int64_t* __restrict__ row_ptr) {
+  extern __shared__ float4 tab[];
+  load_table(tab_g, tab, g.K + 1);
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= count) return;
+  const RecV v = load_rec(r, first + p);
+  int64_t n = 0;
+  walk_proton(g, tab, v, [&](int, float) { ++n; });
+  row_ptr[p + 1] = n;
+}
+
+// In-place inclusive scan of row_ptr[1..count]; row_ptr[0] = 0. One CTA of
+// 1024 threads, each owning a contiguous chunk (sized for the row export).
+__global__ void __launch_bounds__(1024) scan_rows_kernel(int64_t* __restrict__ rp, int64_t count) {
+  __shared__ long long sums[1024];
+  const int t = threadIdx.x;
+  const int64_t per = (count + 1023) / 1024;
+  const int64_t lo = min((int64_t)t * per, count), hi = min(lo + per, count);
+  long long s = 0;
+  for (int64_t i = lo; i < hi; ++i) s += rp[1 + i];
+  sums[t] = s;
+  __syncthreads();
+  if (t == 0) {
+    long long acc = 0;
+    for (int q = 0; q < 1024; ++q) {
+      long long w = sums[q];
+      sums[q] = acc;
+      acc += w;
+    }
+    rp[0] = 0;
+  }
+  __syncthreads();
+  long long acc = sums[t];
+  for (int64_t i = lo; i < hi; ++i) {
+    acc += rp[1 + i];
+    rp[1 + i] = acc;
+  }
+}
+
+__global__ void row_fill_kernel(Geo g, Rec r, const float4* __restrict__ tab_g, int64_t first, int64_t count,
+                                const int64_t* __restrict__ row_ptr, int32_t* __restrict__ vox,
+                                float* __restrict__ len, int32_t* __restrict__ nodes) {
+  extern __shared__ float4 tab[];
+  load_table(tab_g, tab, g.K + 1);
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= count) return;
+  const RecV v = load_rec(r, first + p);
+  int64_t o = row_ptr[p];
+  walk_proton(g, tab, v, [&](int j, float l) {
+    vox[o] = j;
+    len[o] = l;
+    ++o;
+  });
+  if (nodes) {
+    int32_t* out = nodes + (int64_t)p * (g.K + 1) * 3;
+    for (int k = 0; k <= g.K; ++k) {
+      const int3 Q = node_q(g, tab, v, k);
+      out[3 * k + 0] = Q.x;
+      out[3 * k + 1] = Q.y;
+      out[3 * k + 2] = Q.z;
+    }
+  }
+}
+
+inline unsigned grid_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
+
+}  // namespace
+
+cudaError_t launch_validate(const Rec& r, int64_t n, float pos_limit, unsigned long long* first_bad,
+                            cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  validate_kernel<<<grid_for(n, 256), 256, 0, s>>>(r, n, pos_limit, first_bad);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_count(const Geo& g, const Rec& r, const float4* tab, int64_t first, int64_t count,
+                         unsigned int* cnt, int threads, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  count_kernel<<<grid_for(count, threads), threads, (g.K + 1) * sizeof(float4), s>>>(g, r, tab, first, count, cnt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_inv_counts(const unsigned int* cnt, float* inv_s, int64_t M, cudaStream_t s) {
+  inv_counts_kernel<<<grid_for(M, 256), 256, 0, s>>>(cnt, inv_s, M);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_counts_to_float(const unsigned int* cnt, float* out, int64_t M, cudaStream_t s) {
+  counts_to_float_kernel<<<grid_for(M, 256), 256, 0, s>>>(cnt, out, M);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_drop_fused(const Geo& g, const Rec& r, const float4* tab, int64_t first, int64_t count,
+                              const float* x, float* delta, float lambda, int flags, int threads, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  threads = 128;
+  drop_fused_kernel<<<grid_for(count, threads), threads, (g.K + 1) * sizeof(float4), s>>>(g, r, tab, first, count, x,
+                                                                                           delta, lambda, flags);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_drop_apply(float* x, float* delta, const float* inv_s, int64_t M, int clamp, float clamp_min,
+                              cudaStream_t s) {
+  drop_apply_kernel<<<grid_for(M, 256), 256, 0, s>>>(x, delta, inv_s, M, clamp, clamp_min);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_row_counts(const Geo& g, const Rec& r, const float4* tab, int64_t first, int64_t count,
+                              int64_t* row_ptr, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  row_count_kernel<<<grid_for(count, 128), 128, (g.K + 1) * sizeof(float4), s>>>(g, r, tab, first, count, row_ptr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scan_rows(int64_t* row_ptr, int64_t count, cudaStream_t s) {
+  scan_rows_kernel<<<1, 1024, 0, s>>>(row_ptr, count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_row_fill(const Geo& g, const Rec& r, const float4* tab, int64_t first, int64_t count,
+                            const int64_t* row_ptr, int32_t* vox, float* len, int32_t* nodes, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  row_fill_kernel<<<grid_for(count, 128), 128, (g.K + 1) * sizeof(float4), s>>>(g, r, tab, first, count, row_ptr, vox,
+                                                                                 len, nodes);
+  return cudaGetLastError();
+}
+
+}  // namespace pct

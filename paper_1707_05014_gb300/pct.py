@@ -1,0 +1,287 @@
+"""Thin Python binding of libpct (include/pct.h): argument marshalling only.
+
+Every step of the reconstruction runs in the library's CUDA kernels; this
+module only converts numpy arrays / torch tensors to pointers and status codes
+to exceptions. PyTorch supplies device memory for caller-side buffers and the
+current CUDA stream. If the compiled library is missing this module raises --
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Dict, Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libpct.so")
+
+FIELDS = ("t0", "v0", "st0", "sv0", "t2", "v2", "st2", "sv2", "wepl", "cphi", "sphi")
+
+PCT_OK = 0
+STATUS = {
+    -1: "INVALID_ARG", -2: "INVALID_DATA", -3: "NO_MEMORY", -4: "CUDA", -5: "CAPACITY", -6: "TIMEOUT", -7: "STATE",
+}
+FLAG_CLAMP = 1
+FLAG_NO_KAHAN = 2
+FLAG_PROFILE = 4
+LOAD_HOST = 0
+LOAD_DEVICE_COPY = 1
+LOAD_DEVICE_BORROW = 2
+
+
+class PctError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"pct {STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class _Grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32), ("hx", ctypes.c_double),
+                ("hy", ctypes.c_double), ("hz", ctypes.c_double)]
+
+
+class _Config(ctypes.Structure):
+    _fields_ = [("n_blocks", ctypes.c_int32), ("lam", ctypes.c_float), ("node_step_mm", ctypes.c_double),
+                ("flags", ctypes.c_int32), ("clamp_min", ctypes.c_float), ("threads_per_proton", ctypes.c_int32),
+                ("cta_threads", ctypes.c_int32)]
+
+
+class _Hist(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64)] + [(f, ctypes.c_void_p) for f in FIELDS]
+
+
+_lib = None
+
+_SIGS = {
+    "pct_create": [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(_Grid), ctypes.POINTER(_Config), ctypes.c_int],
+    "pct_destroy": [ctypes.c_void_p],
+    "pct_set_stream": [ctypes.c_void_p, ctypes.c_void_p],
+    "pct_geometry": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                     ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64)],
+    "pct_mlp_table": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int],
+    "pct_load_histories": [ctypes.c_void_p, ctypes.POINTER(_Hist), ctypes.c_int, ctypes.POINTER(ctypes.c_int64)],
+    "pct_mlp_rows": [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                     ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)],
+    "pct_block_counts": [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p],
+    "pct_set_x0": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int],
+    "pct_iterate": [ctypes.c_void_p, ctypes.c_int32],
+    "pct_get_rsp": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int],
+    "pct_sync": [ctypes.c_void_p],
+    "pct_last_sweep_times": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
+}
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libpct.so; raises if it has not been built (no fallback)."""
+    global _lib
+    if _lib is not None and path == LIB_PATH:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libpct.so not built at {path}: run paper_1707_05014_gb300.build.build()")
+    L = ctypes.CDLL(path)
+    for name, args in _SIGS.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    L.pct_last_error.argtypes = []
+    L.pct_last_error.restype = ctypes.c_char_p
+    L.pct_launch_count.argtypes = [ctypes.c_void_p]
+    L.pct_launch_count.restype = ctypes.c_int64
+    if path == LIB_PATH:
+        _lib = L
+    return L
+
+
+def _check(code: int):
+    if code != PCT_OK:
+        raise PctError(code, load_library().pct_last_error().decode())
+
+
+def _torch():
+    import torch
+
+    return torch
+
+
+def _is_tensor(a) -> bool:
+    try:
+        import torch
+
+        return isinstance(a, torch.Tensor)
+    except ImportError:  # pragma: no cover
+        return False
+
+
+CUDA_STREAM_LEGACY = 1  # cudaStreamLegacy: the handle of the legacy default stream
+
+
+def _stream_ptr():
+    """torch's current stream as a cudaStream_t; torch reports the legacy
+    default stream as 0, which the C ABI reads as "the context's own stream",
+    so it is passed as cudaStreamLegacy instead."""
+    torch = _torch()
+    h = torch.cuda.current_stream().cuda_stream
+    return ctypes.c_void_p(h if h else CUDA_STREAM_LEGACY)
+
+
+class Context:
+    """One reconstruction: a grid, its MLP table, loaded histories and x.
+
+    Mirrors pct_create / pct_load_histories / pct_mlp_rows / pct_iterate /
+    pct_get_rsp. Device work runs on torch's current CUDA stream at the time of
+    each call (pct_set_stream is refreshed before every call).
+    """
+
+    def __init__(self, grid, n_blocks: int = 10, lam: float = 1.0, node_step: float = 0.0, flags: int = 0,
+                 clamp_min: float = 0.0, device: int = 0, cta_threads: int = 128):
+        L = load_library()
+        self._L = L
+        self.grid = grid
+        g = _Grid(int(grid.nx), int(grid.ny), int(grid.nz), float(grid.hx), float(grid.hy), float(grid.hz))
+        c = _Config(int(n_blocks), float(lam), float(node_step), int(flags), float(clamp_min), 1, int(cta_threads))
+        h = ctypes.c_void_p()
+        _check(L.pct_create(ctypes.byref(h), ctypes.byref(g), ctypes.byref(c), int(device)))
+        self._h = h
+        self.device = device
+        self.n_blocks = n_blocks
+        self._keep = None
+        R, du, K, E, M = ctypes.c_double(), ctypes.c_double(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+        _check(L.pct_geometry(h, ctypes.byref(R), ctypes.byref(du), ctypes.byref(K), ctypes.byref(E), ctypes.byref(M)))
+        self.R, self.du, self.K, self.E, self.M = R.value, du.value, K.value, E.value, M.value
+        self.n = 0
+
+    # -- lifetime ---------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._L.pct_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):  # pragma: no cover - best effort
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _bind_stream(self):
+        _check(self._L.pct_set_stream(self._h, _stream_ptr()))
+
+    # -- calls -------------------------------------------------------------
+    def mlp_table(self) -> np.ndarray:
+        out = np.zeros((self.K + 1, 4), dtype=np.float64)
+        self._bind_stream()
+        _check(self._L.pct_mlp_table(self._h, out.ctypes.data_as(ctypes.c_void_p), 0))
+        return out
+
+    def load(self, rec: Dict, borrow: bool = False) -> None:
+        """Load histories: numpy arrays (host copy) or CUDA tensors (device copy,
+        or used in place with ``borrow=True``; the caller keeps them alive)."""
+        arrs = [rec[f] for f in FIELDS]
+        n = len(arrs[0])
+        if _is_tensor(arrs[0]) and arrs[0].is_cuda:
+            torch = _torch()
+            arrs = [a.to(torch.float32).contiguous() for a in arrs]
+            if not all(a.is_cuda for a in arrs):
+                raise ValueError("tensors must all be on the same device")
+            ptrs = [a.data_ptr() for a in arrs]
+            flags = LOAD_DEVICE_BORROW if borrow else LOAD_DEVICE_COPY
+        elif _is_tensor(arrs[0]):  # host tensors (e.g. pinned): copied by the library
+            torch = _torch()
+            arrs = [a.to(torch.float32).contiguous() for a in arrs]
+            ptrs = [a.data_ptr() for a in arrs]
+            flags = LOAD_HOST
+        else:
+            arrs = [np.ascontiguousarray(a, dtype=np.float32) for a in arrs]
+            ptrs = [a.ctypes.data for a in arrs]
+            flags = LOAD_HOST
+        h = _Hist(n, *ptrs)
+        fb = ctypes.c_int64(-1)
+        self._bind_stream()
+        code = self._L.pct_load_histories(self._h, ctypes.byref(h), flags, ctypes.byref(fb))
+        self.first_bad = fb.value
+        _check(code)
+        self._keep = arrs if flags == LOAD_DEVICE_BORROW else None
+        self.n = n
+
+    def rows(self, first: int = 0, count: Optional[int] = None, with_nodes: bool = False):
+        """CSR rows of histories [first, first+count) as CUDA tensors:
+        (row_ptr int64, vox int32, len float32[, nodes int32 (count, K+1, 3)])."""
+        torch = _torch()
+        count = self.n - first if count is None else count
+        dev = torch.device("cuda", self.device)
+        rp = torch.zeros(count + 1, dtype=torch.int64, device=dev)
+        need = ctypes.c_int64(0)
+        self._bind_stream()
+        code = self._L.pct_mlp_rows(self._h, first, count, ctypes.c_void_p(rp.data_ptr()), None, None, 0, None,
+                                    ctypes.byref(need))
+        if code not in (PCT_OK, -5):
+            _check(code)
+        cap = max(int(need.value), 1)
+        vox = torch.empty(cap, dtype=torch.int32, device=dev)
+        ln = torch.empty(cap, dtype=torch.float32, device=dev)
+        nodes = torch.empty((count, self.K + 1, 3), dtype=torch.int32, device=dev) if with_nodes else None
+        _check(self._L.pct_mlp_rows(self._h, first, count, ctypes.c_void_p(rp.data_ptr()),
+                                    ctypes.c_void_p(vox.data_ptr()), ctypes.c_void_p(ln.data_ptr()), cap,
+                                    ctypes.c_void_p(nodes.data_ptr()) if nodes is not None else None,
+                                    ctypes.byref(need)))
+        n = int(need.value)
+        out = (rp, vox[:n], ln[:n])
+        return out + (nodes,) if with_nodes else out
+
+    def block_counts(self, block: int):
+        torch = _torch()
+        out = torch.empty(self.M, dtype=torch.float32, device=torch.device("cuda", self.device))
+        self._bind_stream()
+        _check(self._L.pct_block_counts(self._h, int(block), ctypes.c_void_p(out.data_ptr())))
+        return out
+
+    def set_x0(self, x0) -> None:
+        self._bind_stream()
+        if _is_tensor(x0):
+            x0 = x0.to(_torch().float32).contiguous()
+            _check(self._L.pct_set_x0(self._h, ctypes.c_void_p(x0.data_ptr()), 1))
+            self._x0_keep = x0
+        else:
+            a = np.ascontiguousarray(x0, dtype=np.float32)
+            _check(self._L.pct_set_x0(self._h, a.ctypes.data_as(ctypes.c_void_p), 0))
+
+    def iterate(self, n_sweeps: int) -> None:
+        self._bind_stream()
+        _check(self._L.pct_iterate(self._h, int(n_sweeps)))
+
+    def get_rsp(self, device: bool = False):
+        """x as a numpy array (synchronising) or a CUDA tensor (asynchronous)."""
+        self._bind_stream()
+        if device:
+            torch = _torch()
+            out = torch.empty(self.M, dtype=torch.float32, device=torch.device("cuda", self.device))
+            _check(self._L.pct_get_rsp(self._h, ctypes.c_void_p(out.data_ptr()), 1))
+            return out
+        out = np.empty(self.M, dtype=np.float32)
+        _check(self._L.pct_get_rsp(self._h, out.ctypes.data_as(ctypes.c_void_p), 0))
+        return out
+
+    def last_sweep_times(self):
+        """(fused_ms, apply_ms) per block of the most recent sweep (needs
+        FLAG_PROFILE); synchronises."""
+        f = np.zeros(self.n_blocks, dtype=np.float32)
+        a = np.zeros(self.n_blocks, dtype=np.float32)
+        self._bind_stream()
+        _check(self._L.pct_last_sweep_times(self._h, f.ctypes.data_as(ctypes.c_void_p),
+                                            a.ctypes.data_as(ctypes.c_void_p)))
+        return f, a
+
+    def sync(self) -> None:
+        self._bind_stream()
+        _check(self._L.pct_sync(self._h))
+
+    @property
+    def launches(self) -> int:
+        return int(self._L.pct_launch_count(self._h))

@@ -350,3 +350,101 @@ def concat(recs: Sequence[Dict[str, np.ndarray]]) -> Dict[str, np.ndarray]:
 
 def subset(rec: Dict[str, np.ndarray], idx) -> Dict[str, np.ndarray]:
     return {k: np.ascontiguousarray(rec[k][idx]) for k in RECORD_FIELDS}
+
+
+# ---------------------------------------------------------------------------
+# Device-side generator (same recipe, torch RNG on the GPU) for large N.
+# ---------------------------------------------------------------------------
+
+def _chord_quadric_t(torch, q: Quadric, p0, dv, ta, tb):
+    c = torch.tensor(q.centre, dtype=p0.dtype, device=p0.device)
+    a = torch.tensor(q.axes, dtype=p0.dtype, device=p0.device)
+    o = (p0 - c) / a
+    d = dv / a
+    if q.kind == "cylz":
+        o = o[:, :2]
+        d = d[:, :2]
+    A = (d * d).sum(dim=1)
+    Bq = 2.0 * (o * d).sum(dim=1)
+    Cq = (o * o).sum(dim=1) - 1.0
+    disc = Bq * Bq - 4.0 * A * Cq
+    ok = (disc > 0) & (A > 0)
+    sq = torch.sqrt(torch.where(ok, disc, torch.zeros_like(disc)))
+    Asafe = torch.where(A > 0, A, torch.ones_like(A))
+    t1 = (-Bq - sq) / (2.0 * Asafe)
+    t2 = (-Bq + sq) / (2.0 * Asafe)
+    lo = torch.maximum(t1, ta)
+    hi = torch.minimum(t2, tb)
+    L = torch.linalg.norm(dv, dim=1)
+    return torch.where(ok & (hi > lo), (hi - lo) * L, torch.zeros_like(L))
+
+
+def _box_clip_t(torch, grid: Grid, p0, dv):
+    n = p0.shape[0]
+    inf = torch.full((n,), float("inf"), dtype=p0.dtype, device=p0.device)
+    lo, hi = -inf, inf.clone()
+    bmin, bmax = grid.box_min, grid.box_max
+    for a in range(3):
+        d = dv[:, a]
+        nz = d != 0
+        dsafe = torch.where(nz, d, torch.ones_like(d))
+        t1 = (float(bmin[a]) - p0[:, a]) / dsafe
+        t2 = (float(bmax[a]) - p0[:, a]) / dsafe
+        inside = (p0[:, a] >= float(bmin[a])) & (p0[:, a] <= float(bmax[a]))
+        tmin = torch.where(nz, torch.minimum(t1, t2), torch.where(inside, -inf, inf))
+        tmax = torch.where(nz, torch.maximum(t1, t2), torch.where(inside, inf, -inf))
+        lo = torch.maximum(lo, tmin)
+        hi = torch.minimum(hi, tmax)
+    return lo, hi
+
+
+def make_histories_device(wl: Workload, n: int | None = None, device: str = "cuda", seed_offset: int = 0,
+                          noise: float = 0.01, slope_sigma: float = 0.003, chunk: int = 8_000_000):
+    """Same recipe as :func:`make_histories`, drawn with torch's generator on
+    ``device`` (a different random stream). Returns float32 tensors."""
+    import torch
+
+    n = wl.n if n is None else n
+    g = wl.grid
+    R = g.radius
+    gen = torch.Generator(device=device)
+    gen.manual_seed(wl.seed * 1_000_003 + seed_offset)
+    ph = wl.phantom()
+    sig, L = slab_sigma(2.0 * R)
+    out = {f: torch.empty(n, dtype=torch.float32, device=device) for f in RECORD_FIELDS}
+    f64 = torch.float64
+    for s in range(0, n, chunk):
+        m = min(chunk, n - s)
+        rnd = lambda: torch.rand(m, generator=gen, device=device, dtype=f64)  # noqa: E731
+        nrm = lambda: torch.randn(m, generator=gen, device=device, dtype=f64)  # noqa: E731
+        if wl.n_angles == 0:
+            phi = rnd() * (2.0 * math.pi)
+        else:
+            phi = torch.randint(0, wl.n_angles, (m,), generator=gen, device=device).to(f64) * (2.0 * math.pi / wl.n_angles)
+        t0 = (2.0 * rnd() - 1.0) * wl.t_range
+        v0 = (2.0 * rnd() - 1.0) * wl.v_range
+        st0 = nrm() * slope_sigma
+        sv0 = nrm() * slope_sigma
+        part = {"t0": t0, "v0": v0, "st0": st0, "sv0": sv0}
+        for lat, pos, slope in (("t", t0, st0), ("v", v0, sv0)):
+            z1 = nrm()
+            z2 = nrm()
+            part[lat + "2"] = pos + L * slope + sig * L * (0.5 * z1 + z2 / (2.0 * math.sqrt(3.0)))
+            part["s" + lat + "2"] = slope + sig * z1
+        part["cphi"] = torch.cos(phi)
+        part["sphi"] = torch.sin(phi)
+        r32 = {k: v.to(torch.float32) for k, v in part.items()}
+        c = r32["cphi"].to(f64)
+        sn = r32["sphi"].to(f64)
+        p0 = torch.stack([-R * c - r32["t0"].to(f64) * sn, -R * sn + r32["t0"].to(f64) * c, r32["v0"].to(f64)], 1)
+        p2 = torch.stack([R * c - r32["t2"].to(f64) * sn, R * sn + r32["t2"].to(f64) * c, r32["v2"].to(f64)], 1)
+        dv = p2 - p0
+        ta, tb = _box_clip_t(torch, g, p0, dv)
+        w = ph.base * torch.clamp(tb - ta, min=0.0) * torch.linalg.norm(dv, dim=1)
+        for q in ph.parts:
+            w = w + q.delta * _chord_quadric_t(torch, q, p0, dv, ta, tb)
+        w = w * (1.0 + noise * nrm())
+        r32["wepl"] = torch.clamp(w, min=0.0).to(torch.float32)
+        for k in RECORD_FIELDS:
+            out[k][s:s + m] = r32[k]
+    return out

@@ -1,0 +1,175 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Bars (stated in the design notes):
+* MLP table: FP64 on both sides, |diff| <= 1e-12 (c2, c4 scaled by 2R).
+* Interior MLP nodes (Q20) and voxel index lists: bit-exact against the
+  oracle's FP32-order node mode; run counts s_j bit-exact.
+* Chords: |l_gpu - l_oracle| <= 1e-5 * max(l, h_min).
+* DROP image after the fixed sweeps: |x_gpu - x_oracle| <= 1e-3 * max(|x|, 1).
+"""
+import numpy as np
+import pytest
+
+from paper_1707_05014_gb300 import synthetic as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pct():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA GPU required for -m gpu tests")
+    from paper_1707_05014_gb300 import build, pct as P
+
+    build.build()
+    return P
+
+
+def _cmp_rows(oracle, g, rec, ctx, first, count, hmin):
+    rp, vox, ln, nodes = ctx.rows(first, count, with_nodes=True)
+    rp, vox, ln, nodes = rp.cpu().numpy(), vox.cpu().numpy(), ln.cpu().numpy(), nodes.cpu().numpy()
+    orp, ovox, oln = oracle.rows(g, rec, first, count, mode=oracle.MODE_FP32)
+    onodes = oracle.nodes(g, rec, first, count, mode=oracle.MODE_FP32)
+    assert np.array_equal(nodes, onodes)
+    assert np.array_equal(rp, orp)
+    assert np.array_equal(vox, ovox)
+    err = np.abs(ln.astype(np.float64) - oln)
+    assert np.all(err <= 1e-5 * np.maximum(oln, hmin)), err.max()
+    return rp, vox, ln
+
+
+@pytest.mark.parametrize("gi", [0, 1, 2])
+def test_mlp_table_matches_oracle(pct, oracle, gi):
+    g = [S.Grid(32, 32, 32, 2.0, 2.0, 2.0), S.Grid(160, 160, 64, 1.25, 1.25, 1.25),
+         S.Grid(200, 200, 48, 1.0, 1.0, 2.0)][gi]
+    with pct.Context(g, n_blocks=1) as ctx:
+        tab = ctx.mlp_table()
+    ref = oracle.mlp_table(g)
+    scale = np.array([1.0, 2 * g.radius, 1.0, 2 * g.radius])
+    assert tab.shape == ref.shape
+    assert np.abs((tab - ref) / scale).max() <= 1e-12
+    R, du, K, E = oracle.geom_info(g)
+    with pct.Context(g, n_blocks=1) as ctx:
+        assert (ctx.K, ctx.E) == (K, E) and abs(ctx.du - du) < 1e-15 and abs(ctx.R - R) < 1e-15
+
+
+@pytest.mark.parametrize("n", [1, 127, 129, 3001])
+def test_rows_bit_exact_tiny(pct, oracle, n):
+    wl = S.tiny_workload(n, seed=7)
+    rec = S.make_histories(wl)
+    with pct.Context(wl.grid, n_blocks=1) as ctx:
+        ctx.load(rec)
+        _cmp_rows(oracle, wl.grid, rec, ctx, 0, n, 2.0)
+
+
+def test_rows_bit_exact_head(pct, oracle):
+    wl = S.head_workload(4000, seed=8)
+    rec = S.make_histories(wl)
+    with pct.Context(wl.grid, n_blocks=4) as ctx:
+        ctx.load(rec)
+        _cmp_rows(oracle, wl.grid, rec, ctx, 0, 4000, 1.25)
+        # a ragged interior range
+        _cmp_rows(oracle, wl.grid, rec, ctx, 1237, 333, 1.25)
+
+
+def test_rows_special_paths(pct, oracle):
+    # axis-aligned, face-aligned, edge-diagonal and grid-missing protons
+    g = S.Grid(32, 32, 32, 2.0, 2.0, 2.0)
+    c45 = np.float32(np.sqrt(0.5))
+    recs = []
+    for (c, s), t, v in [((1, 0), 3.3, -7.1), ((0, 1), 0.0, 0.0), ((-1, 0), 0.0, 20.0), ((c45, c45), 0.0, 5.5),
+                         ((-c45, -c45), 0.0, -5.5), ((1, 0), 10.0, 40.0)]:
+        r = S.straight_records(g, [t], [v], [0.0], [0.0], [0.0])
+        r["cphi"][:] = np.float32(c)
+        r["sphi"][:] = np.float32(s)
+        recs.append(r)
+    rec = S.concat(recs)
+    with pct.Context(g, n_blocks=1) as ctx:
+        ctx.load(rec)
+        rp, vox, ln = _cmp_rows(oracle, g, rec, ctx, 0, len(recs), 2.0)
+    assert rp[-1] - rp[-2] == 0  # v = 40 mm passes above the 64 mm tall grid
+
+
+def test_block_counts_bit_exact(pct, oracle):
+    wl = S.tiny_workload(20_000, seed=9)
+    rec = S.make_histories(wl)
+    with pct.Context(wl.grid, n_blocks=3) as ctx:
+        ctx.load(rec)
+        for b in range(3):
+            got = ctx.block_counts(b).cpu().numpy().astype(np.float64)
+            assert np.array_equal(got, oracle.block_counts(wl.grid, rec, 3, b, mode=oracle.MODE_FP32))
+
+
+def _drop_parity(pct, oracle, wl, n_blocks, n_sweeps, lam=1.0, x0=None):
+    rec = S.make_histories(wl)
+    with pct.Context(wl.grid, n_blocks=n_blocks, lam=lam) as ctx:
+        ctx.load(rec)
+        if x0 is not None:
+            ctx.set_x0(x0)
+        ctx.iterate(n_sweeps)
+        x = ctx.get_rsp().astype(np.float64)
+    xo = oracle.drop(wl.grid, rec, n_blocks, n_sweeps, lam=lam, x0=x0, mode=oracle.MODE_FP32)
+    err = np.abs(x - xo) / np.maximum(np.abs(xo), 1.0)
+    assert err.max() <= 1e-3, (err.max(), int(err.argmax()))
+    return x, xo
+
+
+def test_drop_parity_tiny_workload(pct, oracle):
+    # 32^3 water cylinder, 100k protons, 10 blocks, 10 sweeps
+    _drop_parity(pct, oracle, S.tiny_workload(100_000), 10, 10)
+
+
+@pytest.mark.parametrize("lam,B,n", [(0.5, 7, 10_007), (1.9, 1, 5_000)])
+def test_drop_parity_ragged_blocks(pct, oracle, lam, B, n):
+    _drop_parity(pct, oracle, S.tiny_workload(n, seed=31), B, 3, lam=lam)
+
+
+def test_drop_parity_with_x0(pct, oracle):
+    wl = S.tiny_workload(20_000, seed=32)
+    x0 = S.voxelize(wl.phantom(), wl.grid).astype(np.float32) * 0.9
+    _drop_parity(pct, oracle, wl, 5, 2, x0=x0)
+
+
+def test_drop_parity_head_subset(pct, oracle):
+    wl = S.head_workload(200_000, seed=33)
+    _drop_parity(pct, oracle, wl, 10, 2)
+
+
+def test_invalid_records_are_rejected(pct):
+    wl = S.tiny_workload(1000, seed=10)
+    rec = S.make_histories(wl)
+    bad = {k: v.copy() for k, v in rec.items()}
+    bad["st0"][17] = 0.7
+    bad["wepl"][400] = np.nan
+    with pct.Context(wl.grid, n_blocks=2) as ctx:
+        with pytest.raises(pct.PctError) as ei:
+            ctx.load(bad)
+        assert ei.value.code == -2 and ctx.first_bad == 17
+        with pytest.raises(pct.PctError) as ei:
+            ctx.iterate(1)
+        assert ei.value.code == -7
+        ctx.load(rec)  # a valid load afterwards works
+        ctx.iterate(1)
+        ctx.sync()
+    with pct.Context(wl.grid, n_blocks=2000) as ctx:
+        with pytest.raises(pct.PctError):
+            ctx.load(rec)  # fewer histories than blocks
+
+
+def test_device_borrow_equals_host_copy(pct):
+    import torch
+
+    wl = S.tiny_workload(5000, seed=11)
+    rec = S.make_histories(wl)
+    trec = {k: torch.from_numpy(v).cuda() for k, v in rec.items()}
+    out = []
+    for r, borrow in ((rec, False), (trec, True), (trec, False)):
+        with pct.Context(wl.grid, n_blocks=5) as ctx:
+            ctx.load(r, borrow=borrow)
+            ctx.iterate(2)
+            out.append(ctx.get_rsp())
+    # same inputs, same launch order: only atomic ordering differs
+    assert np.abs(out[0] - out[1]).max() <= 1e-4 * max(1.0, np.abs(out[0]).max())
+    assert np.abs(out[0] - out[2]).max() <= 1e-4 * max(1.0, np.abs(out[0]).max())
