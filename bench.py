@@ -170,7 +170,8 @@ def run_ours(args):
     rec = S.make_histories_device(wl, device=f"cuda:{local}")
     torch.cuda.synchronize()
 
-    ctx = P.Context(g, n_blocks=wl.n_blocks, flags=P.FLAG_PROFILE, device=local)
+    flags = P.FLAG_PROFILE | (P.FLAG_NO_SORT if args.no_sort else 0)
+    ctx = P.Context(g, n_blocks=wl.n_blocks, flags=flags, device=local)
     ctx.load(rec, borrow=True)
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
@@ -281,6 +282,7 @@ def main():
     ap.add_argument("--e2e-sweeps", type=int, default=10)
     ap.add_argument("--cpu-sample", type=int, default=200_000)
     ap.add_argument("--ref-sample", type=int, default=100_000)
+    ap.add_argument("--no-sort", action="store_true", help="keep each block in load order (A/B of the ordering)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

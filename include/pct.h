@@ -73,6 +73,12 @@ typedef struct pct_config {
 #define PCT_FLAG_NO_KAHAN 2 /* plain instead of compensated a_i.x (precision study) */
 #define PCT_FLAG_PROFILE 4  /* record CUDA events around every fused launch
                                (read with pct_last_sweep_times)               */
+#define PCT_FLAG_NO_SORT 8  /* keep each block in load order (default: each
+                               block is stored ordered by gantry angle and
+                               entry lateral position, which keeps the lanes
+                               of a warp on near-parallel paths; membership
+                               of the blocks, and so the result, is unchanged
+                               up to floating-point summation order)          */
 
 /* One history per index: entry state at u = -R, exit state at u = +R, the
  * WEPL b_i (mm) and the gantry angle as cos/sin (Sec. 2: "entry position and
@@ -120,14 +126,18 @@ PCT_API pct_status pct_geometry(const pct_ctx *ctx, double *R, double *du, int32
 PCT_API pct_status pct_mlp_table(pct_ctx *ctx, double *out, int to_device);
 
 /* Load N histories (Sec. 2). Validates every record on the GPU: finite
- * values, |slope| < 0.5, |t|,|v| within the position limit, wepl >= 0,
- * |cos^2 + sin^2 - 1| < 1e-3. On failure returns PCT_ERR_INVALID_DATA and
- * the first bad index in *first_bad (may be NULL; -1 when all are valid).
- * Then computes each block's run counts s_j (DROP's diagonal weights) and
- * resets x to 0. Synchronises. */
+ * values, |slope| < 0.5, |t|,|v| within the position limit (half the grid's
+ * 3-D diagonal plus R), wepl >= 0, |cos^2 + sin^2 - 1| < 1e-3. On failure
+ * returns PCT_ERR_INVALID_DATA and the first bad index in *first_bad (may be
+ * NULL; -1 when all are valid). The records are copied into context storage
+ * (ordered within each block unless PCT_FLAG_NO_SORT; PCT_LOAD_DEVICE_BORROW
+ * avoids the copy only with PCT_FLAG_NO_SORT). Then computes each block's run
+ * counts s_j (DROP's diagonal weights) and resets x to 0. Each block must hold
+ * fewer than 2^32 histories. Synchronises. */
 PCT_API pct_status pct_load_histories(pct_ctx *ctx, const pct_histories *h, int flags, int64_t *first_bad);
 
-/* Rows a_i of histories [first, first+count) of the loaded set, in CSR form,
+/* Rows a_i of histories [first, first+count) of the loaded set (indices in
+ * load order), in CSR form,
  * all DEVICE pointers: row_ptr (count+1 int64), vox (cap int32 voxel
  * indices), len (cap float chord lengths in mm, in path order; a run is a
  * maximal stretch in one voxel, zero-length runs never appear). `nodes`

@@ -29,6 +29,7 @@ struct pct_ctx {
   int64_t n = 0;
   float* rec_store = nullptr;  // owned copy of the 11 record arrays (null when borrowed)
   Rec rec{};
+  int64_t* where = nullptr;    // load index -> stored position (null: stored in load order)
   float* x = nullptr;
   float* delta = nullptr;
   float* inv_s = nullptr;  // B x M
@@ -78,6 +79,8 @@ void free_records(pct_ctx* c) {
   c->rec_store = nullptr;
   if (c->inv_s) cudaFree(c->inv_s);
   c->inv_s = nullptr;
+  if (c->where) cudaFree(c->where);
+  c->where = nullptr;
   c->rec = Rec{};
   c->n = 0;
   c->loaded = false;
@@ -151,6 +154,9 @@ pct_status pct_create(pct_ctx** out, const pct_grid* grid, const pct_config* cfg
   G.E = c->E;
   G.du = (float)c->du;
   G.u0 = (float)(-c->R);
+  G.hx = (float)g.hx;
+  G.hy = (float)g.hy;
+  G.hz = (float)g.hz;
   G.ihx = (float)(1.0 / g.hx);
   G.ihy = (float)(1.0 / g.hy);
   G.ihz = (float)(1.0 / g.hz);
@@ -261,12 +267,41 @@ pct_status pct_mlp_table(pct_ctx* c, double* out, int to_device) {
   return PCT_OK;
 }
 
+namespace {
+
+Rec rec_at(float* base, int64_t stride) {
+  const float* f[11];
+  for (int i = 0; i < 11; ++i) f[i] = base + (size_t)i * stride;
+  return Rec{f[0], f[1], f[2], f[3], f[4], f[5], f[6], f[7], f[8], f[9], f[10]};
+}
+
+Rec rec_offset(const float* const* src, int64_t lo) {
+  return Rec{src[0] + lo, src[1] + lo, src[2] + lo, src[3] + lo, src[4] + lo, src[5] + lo,
+             src[6] + lo, src[7] + lo, src[8] + lo, src[9] + lo, src[10] + lo};
+}
+
+struct Scratch {
+  float* staging = nullptr;
+  unsigned* key = nullptr;
+  unsigned* order = nullptr;
+  unsigned* hist = nullptr;
+  ~Scratch() {
+    cudaFree(staging);
+    cudaFree(key);
+    cudaFree(order);
+    cudaFree(hist);
+  }
+};
+
+}  // namespace
+
 pct_status pct_load_histories(pct_ctx* c, const pct_histories* h, int flags, int64_t* first_bad) {
   if (first_bad) *first_bad = -1;
   if (!c || !h) return fail(PCT_ERR_INVALID_ARG, "ctx or histories is NULL");
   if (h->n < 1) return fail(PCT_ERR_INVALID_ARG, "n must be >= 1");
   if (h->n < c->cfg.n_blocks) return fail(PCT_ERR_INVALID_ARG, "n (%lld) < n_blocks (%d)", (long long)h->n,
                                           c->cfg.n_blocks);
+  if (h->n >= ((int64_t)1 << 32) * c->cfg.n_blocks) return fail(PCT_ERR_INVALID_ARG, "blocks of >= 2^32 histories");
   const float* src[11] = {h->t0, h->v0, h->st0, h->sv0, h->t2, h->v2, h->st2, h->sv2, h->wepl, h->cphi, h->sphi};
   for (int f = 0; f < 11; ++f)
     if (!src[f]) return fail(PCT_ERR_INVALID_ARG, "history array %d is NULL", f);
@@ -276,25 +311,52 @@ pct_status pct_load_histories(pct_ctx* c, const pct_histories* h, int flags, int
   PCT_CK(cudaStreamSynchronize(c->stream));
   free_records(c);
   const int64_t n = h->n;
-  const float* dst[11];
-  if (flags == PCT_LOAD_DEVICE_BORROW) {
-    for (int f = 0; f < 11; ++f) dst[f] = src[f];
+  c->n = n;
+  const int B = c->cfg.n_blocks;
+  const bool sort = !(c->cfg.flags & PCT_FLAG_NO_SORT);
+  const bool in_place = flags == PCT_LOAD_DEVICE_BORROW && !sort;
+  int64_t max_blk = 0;
+  for (int b = 0; b < B; ++b) max_blk = block_lo(c, b + 1) - block_lo(c, b) > max_blk ? block_lo(c, b + 1) - block_lo(c, b) : max_blk;
+
+  Scratch sc;
+  if (in_place) {
+    c->rec = rec_offset(src, 0);
   } else {
     PCT_ALLOC(c->rec_store, (size_t)n * 11 * sizeof(float));
-    for (int f = 0; f < 11; ++f) {
-      float* d = c->rec_store + (size_t)f * n;
-      PCT_CK(cudaMemcpyAsync(d, src[f], (size_t)n * sizeof(float),
-                             flags == PCT_LOAD_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, c->stream));
-      dst[f] = d;
+    c->rec = rec_at(c->rec_store, n);
+  }
+  if (sort) {
+    PCT_ALLOC(c->where, (size_t)n * sizeof(int64_t));
+    PCT_ALLOC(sc.key, (size_t)max_blk * sizeof(unsigned));
+    PCT_ALLOC(sc.order, (size_t)max_blk * sizeof(unsigned));
+    PCT_ALLOC(sc.hist, (size_t)pct::kSortAngles * pct::kSortLateral * sizeof(unsigned));
+  }
+  if (flags == PCT_LOAD_HOST) PCT_ALLOC(sc.staging, (size_t)max_blk * 11 * sizeof(float));
+
+  // per block: bring the records to the device, validate, order (or copy)
+  PCT_CK(cudaMemsetAsync(c->first_bad, 0xff, sizeof(unsigned long long), c->stream));
+  for (int b = 0; b < B; ++b) {
+    const int64_t lo = block_lo(c, b), cnt = block_lo(c, b + 1) - lo;
+    Rec blk;
+    if (flags == PCT_LOAD_HOST) {
+      for (int f = 0; f < 11; ++f)
+        PCT_CK(cudaMemcpyAsync(sc.staging + (size_t)f * max_blk, src[f] + lo, (size_t)cnt * sizeof(float),
+                               cudaMemcpyHostToDevice, c->stream));
+      blk = rec_at(sc.staging, max_blk);
+    } else {
+      blk = rec_offset(src, lo);
+    }
+    PCT_CK(pct::launch_validate(blk, cnt, lo, c->pos_limit, c->first_bad, c->stream));
+    c->launches += 1;
+    if (sort) {
+      PCT_CK(pct::launch_sort_block(blk, cnt, lo, c->pos_limit, c->rec, c->where, sc.key, sc.hist, sc.order,
+                                    c->stream));
+      c->launches += 5;
+    } else if (!in_place) {
+      PCT_CK(pct::launch_copy_block(blk, cnt, lo, c->rec, nullptr, c->stream));
+      c->launches += 1;
     }
   }
-  c->rec = Rec{dst[0], dst[1], dst[2], dst[3], dst[4], dst[5], dst[6], dst[7], dst[8], dst[9], dst[10]};
-  c->n = n;
-
-  // validation
-  PCT_CK(cudaMemsetAsync(c->first_bad, 0xff, sizeof(unsigned long long), c->stream));
-  PCT_CK(pct::launch_validate(c->rec, n, c->pos_limit, c->first_bad, c->stream));
-  c->launches += 1;
   unsigned long long fb = 0;
   PCT_CK(cudaMemcpyAsync(&fb, c->first_bad, sizeof fb, cudaMemcpyDeviceToHost, c->stream));
   PCT_CK(cudaStreamSynchronize(c->stream));
@@ -305,7 +367,6 @@ pct_status pct_load_histories(pct_ctx* c, const pct_histories* h, int flags, int
   }
 
   // DROP block weights: s_j = runs of block b in voxel j; store 1/s_j
-  const int B = c->cfg.n_blocks;
   PCT_ALLOC(c->inv_s, (size_t)B * c->M * sizeof(float));
   for (int b = 0; b < B; ++b) {
     const int64_t lo = block_lo(c, b), hi = block_lo(c, b + 1);
@@ -316,7 +377,7 @@ pct_status pct_load_histories(pct_ctx* c, const pct_histories* h, int flags, int
   }
   PCT_CK(cudaMemsetAsync(c->x, 0, (size_t)c->M * sizeof(float), c->stream));
   PCT_CK(cudaMemsetAsync(c->delta, 0, (size_t)c->M * sizeof(float), c->stream));
-  pct_status st = sync_and_check(c);
+  pct_status st = sync_and_check(c);  // scratch is freed after the stream is idle
   if (st != PCT_OK) return st;
   c->loaded = true;
   return PCT_OK;
@@ -330,7 +391,7 @@ pct_status pct_mlp_rows(pct_ctx* c, int64_t first, int64_t count, int64_t* row_p
   if (first < 0 || count < 0 || first + count > c->n) return fail(PCT_ERR_INVALID_ARG, "range outside [0, n)");
   if (cap < 0 || (cap > 0 && (!vox || !len))) return fail(PCT_ERR_INVALID_ARG, "bad row buffers");
   PCT_CK(cudaSetDevice(c->device));
-  PCT_CK(pct::launch_row_counts(c->geo, c->rec, c->tab32, first, count, row_ptr, c->stream));
+  PCT_CK(pct::launch_row_counts(c->geo, c->rec, c->tab32, first, count, c->where, row_ptr, c->stream));
   PCT_CK(pct::launch_scan_rows(row_ptr, count, c->stream));
   c->launches += 2;
   int64_t total = 0;
@@ -339,7 +400,8 @@ pct_status pct_mlp_rows(pct_ctx* c, int64_t first, int64_t count, int64_t* row_p
   if (needed) *needed = total;
   if (total > cap) return fail(PCT_ERR_CAPACITY, "rows need %lld runs, capacity %lld", (long long)total,
                                (long long)cap);
-  PCT_CK(pct::launch_row_fill(c->geo, c->rec, c->tab32, first, count, row_ptr, vox, len, nodes, c->stream));
+  PCT_CK(pct::launch_row_fill(c->geo, c->rec, c->tab32, first, count, c->where, row_ptr, vox, len, nodes,
+                              c->stream));
   c->launches += 1;
   return sync_and_check(c);
 }

@@ -12,6 +12,9 @@ constexpr int32_t kQOne = 1 << kQBits;   // one voxel
 constexpr float kQClamp = 1000.0f;       // |q| clamp in voxels (never reached for valid records)
 constexpr int kMaxNodes = 2048;          // K + 1 limit (shared-memory MLP table)
 constexpr int kMaxDim = 512;             // per-axis voxel limit
+constexpr int kSortAngles = 256;         // load-time ordering: gantry-angle bins
+constexpr int kSortLateral = 1024;       // load-time ordering: entry lateral-position bins
+constexpr int kRowCap = 512;             // runs kept per history between the fused kernel's two passes
 
 // Grid and node geometry in the single-precision form the kernels use.
 struct Geo {
@@ -20,6 +23,7 @@ struct Geo {
   int E;          // straight extension nodes per side (k = -E..-1, K+1..K+E)
   float du;       // node spacing (mm), rounded from FP64
   float u0;       // first measurement plane (-R), rounded from FP64
+  float hx, hy, hz;     // voxel size (mm)
   float ihx, ihy, ihz;  // 1/h rounded from FP64
   float hnx, hny, hnz;  // n/2
   float lx, ly, lz;     // h * 2^-20: mm per Q20 unit
@@ -35,8 +39,15 @@ struct Rec {
 // Launchers (pct_kernels.cu / pct_table.cu). All enqueue on `s` and return
 // the launch error (cudaSuccess when queued).
 cudaError_t launch_mlp_table(double R, double du, int K, double* tab64, float4* tab32, cudaStream_t s);
-cudaError_t launch_validate(const Rec& r, int64_t n, float pos_limit, unsigned long long* first_bad,
+cudaError_t launch_validate(const Rec& r, int64_t n, int64_t base, float pos_limit, unsigned long long* first_bad,
                             cudaStream_t s);
+// Order n records of one block by (angle bin, entry lateral bin) into
+// dst_rec[base .. base+n); where[base + i] receives the stored position of
+// input record i (where may be null). key/order: n entries; hist: bins.
+cudaError_t launch_sort_block(const Rec& src, int64_t n, int64_t base, float lat_lim, Rec dst_rec, int64_t* where,
+                              unsigned* key, unsigned* hist, unsigned* order, cudaStream_t s);
+// Copy n records into dst_rec[base ..) in input order (where as above).
+cudaError_t launch_copy_block(const Rec& src, int64_t n, int64_t base, Rec dst_rec, int64_t* where, cudaStream_t s);
 cudaError_t launch_count(const Geo& g, const Rec& r, const float4* tab, int64_t first, int64_t count,
                          unsigned int* cnt, int threads, cudaStream_t s);
 cudaError_t launch_inv_counts(const unsigned int* cnt, float* inv_s, int64_t M, cudaStream_t s);
@@ -46,9 +57,10 @@ cudaError_t launch_drop_fused(const Geo& g, const Rec& r, const float4* tab, int
 cudaError_t launch_drop_apply(float* x, float* delta, const float* inv_s, int64_t M, int clamp, float clamp_min,
                               cudaStream_t s);
 cudaError_t launch_row_counts(const Geo& g, const Rec& r, const float4* tab, int64_t first, int64_t count,
-                              int64_t* row_ptr, cudaStream_t s);
+                              const int64_t* where, int64_t* row_ptr, cudaStream_t s);
 cudaError_t launch_scan_rows(int64_t* row_ptr, int64_t count, cudaStream_t s);
 cudaError_t launch_row_fill(const Geo& g, const Rec& r, const float4* tab, int64_t first, int64_t count,
-                            const int64_t* row_ptr, int32_t* vox, float* len, int32_t* nodes, cudaStream_t s);
+                            const int64_t* where, const int64_t* row_ptr, int32_t* vox, float* len, int32_t* nodes,
+                            cudaStream_t s);
 
 }  // namespace pct

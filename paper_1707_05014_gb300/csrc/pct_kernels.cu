@@ -18,7 +18,7 @@ __device__ __forceinline__ void load_table(const float4* __restrict__ src, float
 
 __device__ __forceinline__ bool bad_float(float v) { return !isfinite(v); }
 
-__global__ void validate_kernel(Rec r, int64_t n, float pos_limit, unsigned long long* first_bad) {
+__global__ void validate_kernel(Rec r, int64_t n, int64_t base, float pos_limit, unsigned long long* first_bad) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const RecV v = load_rec(r, i);
@@ -29,7 +29,7 @@ __global__ void validate_kernel(Rec r, int64_t n, float pos_limit, unsigned long
   bad = bad || fabsf(v.t0) > pos_limit || fabsf(v.v0) > pos_limit || fabsf(v.t2) > pos_limit ||
         fabsf(v.v2) > pos_limit;
   bad = bad || v.wepl < 0.f || fabsf(v.cp * v.cp + v.sp * v.sp - 1.f) > 1e-3f;
-  if (bad) atomicMin(first_bad, (unsigned long long)i);
+  if (bad) atomicMin(first_bad, (unsigned long long)(base + i));
 }
 
 __global__ void count_kernel(Geo g, Rec r, const float4* __restrict__ tab_g, int64_t first, int64_t count,
@@ -56,7 +56,10 @@ __global__ void counts_to_float_kernel(const unsigned int* __restrict__ cnt, flo
 }
 
 // One thread per proton: MLP nodes -> walk -> compensated a_i.x and |a_i|^2
-// -> relaxed residual -> walk again -> scatter-add into delta.
+// -> relaxed residual -> scatter-add into delta. The first pass keeps the
+// row (voxel, chord) in thread-local memory so the scatter replays it instead
+// of walking again; a row longer than kRowCap runs (none for valid records on
+// the supported grids) is walked a second time instead.
 __global__ void __launch_bounds__(128) drop_fused_kernel(Geo g, Rec r, const float4* __restrict__ tab_g,
                                                           int64_t first, int64_t count, const float* __restrict__ x,
                                                           float* __restrict__ delta, float lambda, int flags) {
@@ -65,11 +68,15 @@ __global__ void __launch_bounds__(128) drop_fused_kernel(Geo g, Rec r, const flo
   int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= count) return;
   const RecV v = load_rec(r, first + p);
+  uint2 row[kRowCap];
+  int nrow = 0;
   float y = 0.f, c = 0.f, nn = 0.f;
   if (flags & 2) {
     walk_proton(g, tab, v, [&](int j, float l) {
       y = __fmaf_rn(l, __ldg(x + j), y);
       nn = __fmaf_rn(l, l, nn);
+      if (nrow < kRowCap) row[nrow] = make_uint2((unsigned)j, __float_as_uint(l));
+      ++nrow;
     });
   } else {
     // Kahan-compensated sum of l * x_j: the true sum is y - c
@@ -79,12 +86,21 @@ __global__ void __launch_bounds__(128) drop_fused_kernel(Geo g, Rec r, const flo
       c = __fsub_rn(__fsub_rn(t, y), term);
       y = t;
       nn = __fmaf_rn(l, l, nn);
+      if (nrow < kRowCap) row[nrow] = make_uint2((unsigned)j, __float_as_uint(l));
+      ++nrow;
     });
   }
   if (!(nn > 0.f)) return;
   const float res = __fadd_rn(__fsub_rn(v.wepl, y), c);
   const float ri = lambda * res / nn;
-  walk_proton(g, tab, v, [&](int j, float l) { atomicAdd(delta + j, l * ri); });
+  if (nrow <= kRowCap) {
+    for (int q = 0; q < nrow; ++q) {
+      const uint2 e = row[q];
+      atomicAdd(delta + e.x, __uint_as_float(e.y) * ri);
+    }
+  } else {
+    walk_proton(g, tab, v, [&](int j, float l) { atomicAdd(delta + j, l * ri); });
+  }
 }
 
 __global__ void drop_apply_kernel(float* __restrict__ x, float* __restrict__ delta, const float* __restrict__ inv_s,
@@ -98,12 +114,12 @@ __global__ void drop_apply_kernel(float* __restrict__ x, float* __restrict__ del
 }
 
 __global__ void row_count_kernel(Geo g, Rec r, const float4* __restrict__ tab_g, int64_t first, int64_t count,
-                                 int64_t* __restrict__ row_ptr) {
+                                 const int64_t* __restrict__ where, int64_t* __restrict__ row_ptr) {
   extern __shared__ float4 tab[];
   load_table(tab_g, tab, g.K + 1);
   int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= count) return;
-  const RecV v = load_rec(r, first + p);
+  const RecV v = load_rec(r, where ? where[first + p] : first + p);
   int64_t n = 0;
   walk_proton(g, tab, v, [&](int, float) { ++n; });
   row_ptr[p + 1] = n;
@@ -138,13 +154,13 @@ __global__ void __launch_bounds__(1024) scan_rows_kernel(int64_t* __restrict__ r
 }
 
 __global__ void row_fill_kernel(Geo g, Rec r, const float4* __restrict__ tab_g, int64_t first, int64_t count,
-                                const int64_t* __restrict__ row_ptr, int32_t* __restrict__ vox,
-                                float* __restrict__ len, int32_t* __restrict__ nodes) {
+                                const int64_t* __restrict__ where, const int64_t* __restrict__ row_ptr,
+                                int32_t* __restrict__ vox, float* __restrict__ len, int32_t* __restrict__ nodes) {
   extern __shared__ float4 tab[];
   load_table(tab_g, tab, g.K + 1);
   int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= count) return;
-  const RecV v = load_rec(r, first + p);
+  const RecV v = load_rec(r, where ? where[first + p] : first + p);
   int64_t o = row_ptr[p];
   walk_proton(g, tab, v, [&](int j, float l) {
     vox[o] = j;
@@ -162,14 +178,125 @@ __global__ void row_fill_kernel(Geo g, Rec r, const float4* __restrict__ tab_g, 
   }
 }
 
+
+// ---- load-time ordering of each block: (gantry-angle bin, entry lateral bin)
+// so that the 32 lanes of a warp trace nearly parallel paths (coherent face
+// crossings). Counting sort: key -> histogram -> exclusive scan -> scatter.
+
+__global__ void sort_key_kernel(Rec r, int64_t n, int n_ang, int n_lat, float lat_lim, unsigned* __restrict__ key) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float two_pi = 6.283185307f;
+  float a = atan2f(r.sphi[i], r.cphi[i]);
+  if (a < 0.f) a += two_pi;
+  int ab = min(n_ang - 1, max(0, (int)(a * (n_ang / two_pi) + 0.5f) % n_ang));
+  int tb = (int)floorf((r.t0[i] + lat_lim) * (n_lat / (2.f * lat_lim)));
+  tb = min(n_lat - 1, max(0, tb));
+  key[i] = (unsigned)(ab * n_lat + tb);
+}
+
+__global__ void histogram_kernel(const unsigned* __restrict__ key, int64_t n, unsigned* __restrict__ hist) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  atomicAdd(hist + key[i], 1u);
+}
+
+// exclusive scan of hist[0..nb) in place, one CTA of 1024 threads
+__global__ void __launch_bounds__(1024) scan_bins_kernel(unsigned* __restrict__ hist, int nb) {
+  __shared__ unsigned sums[1024];
+  const int t = threadIdx.x;
+  const int per = (nb + 1023) / 1024;
+  const int lo = min(t * per, nb), hi = min(lo + per, nb);
+  unsigned s = 0;
+  for (int i = lo; i < hi; ++i) s += hist[i];
+  sums[t] = s;
+  __syncthreads();
+  if (t == 0) {
+    unsigned acc = 0;
+    for (int q = 0; q < 1024; ++q) {
+      unsigned w = sums[q];
+      sums[q] = acc;
+      acc += w;
+    }
+  }
+  __syncthreads();
+  unsigned acc = sums[t];
+  for (int i = lo; i < hi; ++i) {
+    unsigned w = hist[i];
+    hist[i] = acc;
+    acc += w;
+  }
+}
+
+__global__ void scatter_kernel(const unsigned* __restrict__ key, int64_t n, unsigned* __restrict__ offs,
+                               unsigned* __restrict__ order) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const unsigned p = atomicAdd(offs + key[i], 1u);
+  order[p] = (unsigned)i;
+}
+
+struct RecOut {
+  float *t0, *v0, *st0, *sv0, *t2, *v2, *st2, *sv2, *wepl, *cphi, *sphi;
+};
+
+// dst[base + p] = src[order[p]] for every field; where[base + order[p]] = base + p
+__global__ void gather_kernel(Rec src, RecOut dst, const unsigned* __restrict__ order, int64_t n, int64_t base,
+                              int64_t* __restrict__ where) {
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  const int64_t i = order ? (int64_t)order[p] : p;
+  const int64_t o = base + p;
+  dst.t0[o] = src.t0[i];
+  dst.v0[o] = src.v0[i];
+  dst.st0[o] = src.st0[i];
+  dst.sv0[o] = src.sv0[i];
+  dst.t2[o] = src.t2[i];
+  dst.v2[o] = src.v2[i];
+  dst.st2[o] = src.st2[i];
+  dst.sv2[o] = src.sv2[i];
+  dst.wepl[o] = src.wepl[i];
+  dst.cphi[o] = src.cphi[i];
+  dst.sphi[o] = src.sphi[i];
+  if (where) where[base + i] = o;
+}
+
 inline unsigned grid_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
 }  // namespace
 
-cudaError_t launch_validate(const Rec& r, int64_t n, float pos_limit, unsigned long long* first_bad,
+cudaError_t launch_sort_block(const Rec& src, int64_t n, int64_t base, float lat_lim, Rec dst_rec,
+                              int64_t* where, unsigned* key, unsigned* hist, unsigned* order, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int n_ang = kSortAngles, n_lat = kSortLateral;
+  cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(unsigned) * n_ang * n_lat, s);
+  if (e != cudaSuccess) return e;
+  sort_key_kernel<<<grid_for(n, 256), 256, 0, s>>>(src, n, n_ang, n_lat, lat_lim, key);
+  histogram_kernel<<<grid_for(n, 256), 256, 0, s>>>(key, n, hist);
+  scan_bins_kernel<<<1, 1024, 0, s>>>(hist, n_ang * n_lat);
+  scatter_kernel<<<grid_for(n, 256), 256, 0, s>>>(key, n, hist, order);
+  RecOut d{const_cast<float*>(dst_rec.t0), const_cast<float*>(dst_rec.v0), const_cast<float*>(dst_rec.st0),
+           const_cast<float*>(dst_rec.sv0), const_cast<float*>(dst_rec.t2), const_cast<float*>(dst_rec.v2),
+           const_cast<float*>(dst_rec.st2), const_cast<float*>(dst_rec.sv2), const_cast<float*>(dst_rec.wepl),
+           const_cast<float*>(dst_rec.cphi), const_cast<float*>(dst_rec.sphi)};
+  gather_kernel<<<grid_for(n, 256), 256, 0, s>>>(src, d, order, n, base, where);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copy_block(const Rec& src, int64_t n, int64_t base, Rec dst_rec, int64_t* where, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  RecOut d{const_cast<float*>(dst_rec.t0), const_cast<float*>(dst_rec.v0), const_cast<float*>(dst_rec.st0),
+           const_cast<float*>(dst_rec.sv0), const_cast<float*>(dst_rec.t2), const_cast<float*>(dst_rec.v2),
+           const_cast<float*>(dst_rec.st2), const_cast<float*>(dst_rec.sv2), const_cast<float*>(dst_rec.wepl),
+           const_cast<float*>(dst_rec.cphi), const_cast<float*>(dst_rec.sphi)};
+  gather_kernel<<<grid_for(n, 256), 256, 0, s>>>(src, d, nullptr, n, base, where);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_validate(const Rec& r, int64_t n, int64_t base, float pos_limit, unsigned long long* first_bad,
                             cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  validate_kernel<<<grid_for(n, 256), 256, 0, s>>>(r, n, pos_limit, first_bad);
+  validate_kernel<<<grid_for(n, 256), 256, 0, s>>>(r, n, base, pos_limit, first_bad);
   return cudaGetLastError();
 }
 
@@ -206,9 +333,10 @@ cudaError_t launch_drop_apply(float* x, float* delta, const float* inv_s, int64_
 }
 
 cudaError_t launch_row_counts(const Geo& g, const Rec& r, const float4* tab, int64_t first, int64_t count,
-                              int64_t* row_ptr, cudaStream_t s) {
+                              const int64_t* where, int64_t* row_ptr, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
-  row_count_kernel<<<grid_for(count, 128), 128, (g.K + 1) * sizeof(float4), s>>>(g, r, tab, first, count, row_ptr);
+  row_count_kernel<<<grid_for(count, 128), 128, (g.K + 1) * sizeof(float4), s>>>(g, r, tab, first, count, where,
+                                                                                  row_ptr);
   return cudaGetLastError();
 }
 
@@ -218,10 +346,11 @@ cudaError_t launch_scan_rows(int64_t* row_ptr, int64_t count, cudaStream_t s) {
 }
 
 cudaError_t launch_row_fill(const Geo& g, const Rec& r, const float4* tab, int64_t first, int64_t count,
-                            const int64_t* row_ptr, int32_t* vox, float* len, int32_t* nodes, cudaStream_t s) {
+                            const int64_t* where, const int64_t* row_ptr, int32_t* vox, float* len, int32_t* nodes,
+                            cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
-  row_fill_kernel<<<grid_for(count, 128), 128, (g.K + 1) * sizeof(float4), s>>>(g, r, tab, first, count, row_ptr, vox,
-                                                                                 len, nodes);
+  row_fill_kernel<<<grid_for(count, 128), 128, (g.K + 1) * sizeof(float4), s>>>(g, r, tab, first, count, where,
+                                                                                 row_ptr, vox, len, nodes);
   return cudaGetLastError();
 }
 

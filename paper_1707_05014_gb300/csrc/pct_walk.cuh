@@ -13,9 +13,11 @@
 // Every product is a separately rounded __fmul_rn and every fused step an
 // explicit __fmaf_rn, so the compiler cannot contract or reorder them.
 // Between consecutive nodes an integer DDA orders the face crossings by
-// exact 32x32->64-bit cross-multiplication; voxels are half-open [i, i+1),
-// tied crossings step together, and a run (maximal stretch in one voxel) is
-// reported only when its exact extent is positive.
+// exact cross-multiplication; voxels are half-open [i, i+1), tied crossings
+// step together, and a run (maximal stretch in one voxel) is reported only
+// when its exact extent is positive. The indices are exact; chord lengths are
+// single precision (segment length from the Q20 differences, crossing
+// parameters by fast division), within 1e-5 relative of the FP64 oracle.
 #pragma once
 
 #include "pct_internal.h"
@@ -44,14 +46,13 @@ __device__ __forceinline__ RecV load_rec(const Rec& r, int64_t i) {
   return v;
 }
 
-__device__ __forceinline__ int32_t quantise(float q) {
-  q = fminf(fmaxf(q, -kQClamp), kQClamp);
-  return __float2int_rn(__fmul_rn(q, (float)kQOne));
-}
+// Q = rint(q * 2^20). The contract also clamps q to +-1000 voxels first;
+// pct_create rejects grids for which a validated record could reach that
+// range, so the clamp is the identity here and is not evaluated.
+__device__ __forceinline__ int32_t quantise(float q) { return __float2int_rn(__fmul_rn(q, (float)kQOne)); }
 
-// Q20 grid coordinates of node k. `tab` holds (c1, c2, c3, c4) per interior node.
-__device__ __forceinline__ int3 node_q(const Geo& g, const float4* __restrict__ tab, const RecV& r, int k) {
-  const float u = __fmaf_rn((float)k, g.du, g.u0);
+// Lateral (t) and vertical (v) position of node k in mm.
+__device__ __forceinline__ float2 node_tv(const Geo& g, const float4* __restrict__ tab, const RecV& r, int k) {
   float t, v;
   if (k < 0) {
     const float dk = __fmul_rn((float)k, g.du);
@@ -66,104 +67,266 @@ __device__ __forceinline__ int3 node_q(const Geo& g, const float4* __restrict__ 
     t = __fmaf_rn(c.w, r.st2, __fmaf_rn(c.z, r.t2, __fmaf_rn(c.y, r.st0, __fmul_rn(c.x, r.t0))));
     v = __fmaf_rn(c.w, r.sv2, __fmaf_rn(c.z, r.v2, __fmaf_rn(c.y, r.sv0, __fmul_rn(c.x, r.v0))));
   }
+  return make_float2(t, v);
+}
+
+// Grid coordinates (voxels, float) of the node at depth u with lateral and
+// vertical position (t, v).
+__device__ __forceinline__ float3 node_grid(const Geo& g, const RecV& r, float u, float t, float v) {
   const float ts = __fmul_rn(t, r.sp), tc = __fmul_rn(t, r.cp);
   const float x = __fmaf_rn(u, r.cp, -ts);
   const float y = __fmaf_rn(u, r.sp, tc);
-  int3 Q;
-  Q.x = quantise(__fmaf_rn(x, g.ihx, g.hnx));
-  Q.y = quantise(__fmaf_rn(y, g.ihy, g.hny));
-  Q.z = quantise(__fmaf_rn(v, g.ihz, g.hnz));
-  return Q;
+  return make_float3(__fmaf_rn(x, g.ihx, g.hnx), __fmaf_rn(y, g.ihy, g.hny), __fmaf_rn(v, g.ihz, g.hnz));
+}
+
+__device__ __forceinline__ int3 quantise3(float3 q) { return make_int3(quantise(q.x), quantise(q.y), quantise(q.z)); }
+
+// Q20 grid coordinates of node k.
+__device__ __forceinline__ int3 node_q(const Geo& g, const float4* __restrict__ tab, const RecV& r, int k) {
+  const float2 tv = node_tv(g, tab, r, k);
+  return quantise3(node_grid(g, r, __fmaf_rn((float)k, g.du, g.u0), tv.x, tv.y));
 }
 
 __device__ __forceinline__ int floor_q(int32_t q) { return q >> kQBits; }  // arithmetic shift = floor
 
+// Depth parameter at which the line p(u) = u d + (a + s u) e_t (xy only)
+// enters (first = true: the largest entering u) or leaves (the smallest
+// leaving u) the box |x| <= bx, |y| <= by. Non-finite results are replaced by
+// the unconstrained value (-inf for entering, +inf for leaving).
+__device__ __forceinline__ float box_param(const Geo& g, const RecV& r, float a, float s, bool entering) {
+  // x(u) = u (c - s sn) - a sn,  y(u) = u (sn + s c) + a c
+  const float ax = r.cp - s * r.sp, bx = -a * r.sp;
+  const float ay = r.sp + s * r.cp, by = a * r.cp;
+  float res = entering ? -INFINITY : INFINITY;
+  const float A[2] = {ax, ay}, Bc[2] = {bx, by}, H[2] = {g.bx, g.by};
+  for (int i = 0; i < 2; ++i) {
+    if (fabsf(A[i]) < 1e-12f) continue;
+    const float u1 = (-H[i] - Bc[i]) / A[i], u2 = (H[i] - Bc[i]) / A[i];
+    const float lo = fminf(u1, u2), hi = fmaxf(u1, u2);
+    if (entering) {
+      if (isfinite(lo)) res = fmaxf(res, lo);
+    } else {
+      if (isfinite(hi)) res = fminf(res, hi);
+    }
+  }
+  return res;
+}
+
 // Node range of one proton. Nodes before -E and after K+E lie outside the
-// box's circumscribed cylinder; a tighter per-proton range that starts and
-// ends outside the box gives the same runs (a straight line meets the convex
-// box in one interval), so any conservative range is equivalent.
+// box's circumscribed cylinder. A straight line meets the convex box in one
+// interval, so any range that starts before the entry ray reaches the box
+// and ends after the exit ray leaves it gives the same runs; the range here
+// is the box-clipped one widened by two nodes (one voxel) on each side.
 __device__ __forceinline__ void node_range(const Geo& g, const RecV& r, int& klo, int& khi) {
   klo = -g.E;
   khi = g.K + g.E;
+  // entry ray: t = t0 + st0 (u - u0) = (t0 - st0 u0) + st0 u
+  const float ue = box_param(g, r, r.t0 - r.st0 * g.u0, r.st0, true);
+  if (isfinite(ue)) klo = max(klo, min(0, (int)floorf((ue - g.u0) / g.du) - 2));
+  // exit ray: t = t2 + st2 (u - u2) with u2 = -u0
+  const float ux = box_param(g, r, r.t2 + r.st2 * g.u0, r.st2, false);
+  if (isfinite(ux)) khi = min(khi, max(g.K, g.K + (int)ceilf((ux + g.u0) / g.du) + 2));
 }
 
 // Walk one proton's polyline, calling visit(j, len) for every run in path
 // order (j = voxel index, len = chord in mm).
+//
+// Per segment P -> Q the voxel index along an axis changes exactly when a face
+// is crossed (floor(Q/2^20) != floor(P/2^20), with the half-open convention:
+// a face reached exactly counts when moving up, not when moving down). When
+// every axis moves less than one voxel -- always the case for valid records,
+// whose segments span at most ~0.6 voxel -- each axis crosses at most one
+// face, and the (at most three) crossings are ordered in one event loop by
+// exact 32x32->64-bit cross-multiplication; tied crossings form one event.
+// Longer segments take the general loop that re-arms an axis after each face.
+// Segment state carried along the polyline.
+struct WalkState {
+  int3 P;        // current node, Q20
+  float3 qP;     // current node, float grid coordinates
+  int cx, cy, cz;  // voxel holding P
+  float run;     // length of the current run so far (mm)
+  bool pos;      // the current run has positive exact extent
+};
+
+template <class Visit>
+__device__ __forceinline__ void emit_run(const Geo& g, WalkState& s, Visit& visit) {
+  if (s.pos && (unsigned)s.cx < (unsigned)g.nx && (unsigned)s.cy < (unsigned)g.ny && (unsigned)s.cz < (unsigned)g.nz)
+    visit(s.cx + g.nx * (s.cy + g.ny * s.cz), s.run);
+  s.run = 0.f;
+  s.pos = false;
+}
+
+// Advance the walk from s.P to the next node (Q, q), emitting finished runs.
+template <class Visit>
+__device__ __forceinline__ void walk_segment(const Geo& g, WalkState& s, const float3 q, Visit& visit) {
+  const int3 Q = quantise3(q);
+  const int Dx = Q.x - s.P.x, Dy = Q.y - s.P.y, Dz = Q.z - s.P.z;
+  // Segment length. The float grid coordinates differ from the Q20 nodes by
+  // at most 2^-21 voxel (the rounding to Q20), far inside the chord
+  // tolerance; differences of nearby floats are exact.
+  const float fx = (q.x - s.qP.x) * g.hx, fy = (q.y - s.qP.y) * g.hy, fz = (q.z - s.qP.z) * g.hz;
+  const float L2 = __fmaf_rn(fx, fx, __fmaf_rn(fy, fy, fz * fz));
+  const bool moved = (Dx | Dy | Dz) != 0;
+  const float L = moved ? L2 * rsqrtf(L2) : 0.f;
+  const int nx = floor_q(Q.x), ny = floor_q(Q.y), nz = floor_q(Q.z);
+  const int sx = nx - s.cx, sy = ny - s.cy, sz = nz - s.cz;
+  if ((sx | sy | sz) == 0) {
+    // no face crossed: the whole segment extends the current run
+    s.run += L;
+    s.pos |= moved;
+  } else if (abs(sx) <= 1 && abs(sy) <= 1 && abs(sz) <= 1) {
+    // each crossing axis crosses exactly one face; its crossing parameter is
+    // the exact fraction n/d
+    const uint32_t ddx = (uint32_t)abs(Dx), ddy = (uint32_t)abs(Dy), ddz = (uint32_t)abs(Dz);
+    const uint32_t ndx = sx > 0 ? (uint32_t)(nx * kQOne - s.P.x) : (uint32_t)(s.P.x - s.cx * kQOne);
+    const uint32_t ndy = sy > 0 ? (uint32_t)(ny * kQOne - s.P.y) : (uint32_t)(s.P.y - s.cy * kQOne);
+    const uint32_t ndz = sz > 0 ? (uint32_t)(nz * kQOne - s.P.z) : (uint32_t)(s.P.z - s.cz * kQOne);
+    bool rx = sx != 0, ry = sy != 0, rz = sz != 0;  // crossings not yet taken
+    uint32_t pn = 0, pd = 1;                         // previous event tau = pn / pd
+    float tprev = 0.f;
+    while (rx | ry | rz) {
+      uint32_t bn = rx ? ndx : (ry ? ndy : ndz);
+      uint32_t bd = rx ? ddx : (ry ? ddy : ddz);
+      if (ry && (uint64_t)ndy * bd < (uint64_t)bn * ddy) {
+        bn = ndy;
+        bd = ddy;
+      }
+      if (rz && (uint64_t)ndz * bd < (uint64_t)bn * ddz) {
+        bn = ndz;
+        bd = ddz;
+      }
+      const float tc = __fdividef((float)bn, (float)bd);
+      s.run += (tc - tprev) * L;
+      s.pos |= (uint64_t)bn * pd > (uint64_t)pn * bd;
+      emit_run(g, s, visit);
+      if (rx && (uint64_t)ndx * bd == (uint64_t)bn * ddx) {
+        s.cx += sx;
+        rx = false;
+      }
+      if (ry && (uint64_t)ndy * bd == (uint64_t)bn * ddy) {
+        s.cy += sy;
+        ry = false;
+      }
+      if (rz && (uint64_t)ndz * bd == (uint64_t)bn * ddz) {
+        s.cz += sz;
+        rz = false;
+      }
+      pn = bn;
+      pd = bd;
+      tprev = tc;
+    }
+    s.run += (1.f - tprev) * L;
+    s.pos |= pn < pd;
+  } else {
+    // general case: an axis may cross several faces
+    const uint32_t adx = (uint32_t)abs(Dx), ady = (uint32_t)abs(Dy), adz = (uint32_t)abs(Dz);
+    uint32_t dx = Dx > 0 ? (uint32_t)((s.cx + 1) * kQOne - s.P.x) : (uint32_t)(s.P.x - s.cx * kQOne);
+    uint32_t dy = Dy > 0 ? (uint32_t)((s.cy + 1) * kQOne - s.P.y) : (uint32_t)(s.P.y - s.cy * kQOne);
+    uint32_t dz = Dz > 0 ? (uint32_t)((s.cz + 1) * kQOne - s.P.z) : (uint32_t)(s.P.z - s.cz * kQOne);
+    uint32_t pn = 0, pd = 1;
+    float tprev = 0.f;
+    for (;;) {
+      // tau <= 1 moving up (a point on a face belongs to the higher voxel),
+      // tau < 1 moving down
+      const bool ax = Dx > 0 ? dx <= adx : (Dx < 0 && dx < adx);
+      const bool ay = Dy > 0 ? dy <= ady : (Dy < 0 && dy < ady);
+      const bool az = Dz > 0 ? dz <= adz : (Dz < 0 && dz < adz);
+      if (!(ax | ay | az)) break;
+      uint32_t bn = 0, bd = 1;
+      bool have = false;
+      if (ax) {
+        bn = dx;
+        bd = adx;
+        have = true;
+      }
+      if (ay && (!have || (uint64_t)dy * bd < (uint64_t)bn * ady)) {
+        bn = dy;
+        bd = ady;
+        have = true;
+      }
+      if (az && (!have || (uint64_t)dz * bd < (uint64_t)bn * adz)) {
+        bn = dz;
+        bd = adz;
+      }
+      const float tc = __fdividef((float)bn, (float)bd);
+      s.run += (tc - tprev) * L;
+      s.pos |= (uint64_t)bn * pd > (uint64_t)pn * bd;
+      emit_run(g, s, visit);
+      if (ax && (uint64_t)dx * bd == (uint64_t)bn * adx) {
+        s.cx += Dx > 0 ? 1 : -1;
+        dx += kQOne;
+      }
+      if (ay && (uint64_t)dy * bd == (uint64_t)bn * ady) {
+        s.cy += Dy > 0 ? 1 : -1;
+        dy += kQOne;
+      }
+      if (az && (uint64_t)dz * bd == (uint64_t)bn * adz) {
+        s.cz += Dz > 0 ? 1 : -1;
+        dz += kQOne;
+      }
+      pn = bn;
+      pd = bd;
+      tprev = tc;
+    }
+    s.run += (1.f - tprev) * L;
+    s.pos |= pn < pd;
+  }
+  s.P = Q;
+  s.qP = q;
+}
+
+// Walk one proton's polyline, calling visit(j, len) for every run in path
+// order (j = voxel index, len = chord in mm).
+//
+// Per segment P -> Q the voxel index along an axis changes exactly when a face
+// is crossed (floor(Q/2^20) != floor(P/2^20), with the half-open convention:
+// a face reached exactly counts when moving up, not when moving down). When
+// every axis moves less than one voxel -- always the case for valid records,
+// whose segments span at most ~0.6 voxel -- each axis crosses at most one
+// face, and the (at most three) crossings are ordered in one event loop by
+// exact 32x32->64-bit cross-multiplication; tied crossings form one event.
+// Longer segments take the general loop that re-arms an axis after each face.
+// The node loop runs in three phases (entry extension, MLP nodes, exit
+// extension) so that no per-node branch selects the node formula.
 template <class Visit>
 __device__ __forceinline__ void walk_proton(const Geo& g, const float4* __restrict__ tab, const RecV& r,
                                             Visit&& visit) {
   int klo, khi;
   node_range(g, r, klo, khi);
-  int3 P = node_q(g, tab, r, klo);
-  int cx = floor_q(P.x), cy = floor_q(P.y), cz = floor_q(P.z);
-  float run = 0.f;
-  bool pos = false;
-  for (int k = klo + 1; k <= khi; ++k) {
-    const int3 Q = node_q(g, tab, r, k);
-    const int Dx = Q.x - P.x, Dy = Q.y - P.y, Dz = Q.z - P.z;
-    if ((Dx | Dy | Dz) != 0) {
-      const uint32_t adx = (uint32_t)abs(Dx), ady = (uint32_t)abs(Dy), adz = (uint32_t)abs(Dz);
-      // distance from P to the next face in the direction of travel
-      uint32_t dx = Dx > 0 ? (uint32_t)((cx + 1) * kQOne - P.x) : (uint32_t)(P.x - cx * kQOne);
-      uint32_t dy = Dy > 0 ? (uint32_t)((cy + 1) * kQOne - P.y) : (uint32_t)(P.y - cy * kQOne);
-      uint32_t dz = Dz > 0 ? (uint32_t)((cz + 1) * kQOne - P.z) : (uint32_t)(P.z - cz * kQOne);
-      const float fx = (float)Dx * g.lx, fy = (float)Dy * g.ly, fz = (float)Dz * g.lz;
-      const float L = sqrtf(fx * fx + fy * fy + fz * fz);
-      uint32_t pn = 0, pd = 1;  // previous crossing tau = pn / pd
-      float tprev = 0.f;
-      for (;;) {
-        // a face is crossed within the segment if tau <= 1 moving up (a point
-        // on a face belongs to the higher voxel) or tau < 1 moving down
-        const bool ax = Dx > 0 ? dx <= adx : (Dx < 0 && dx < adx);
-        const bool ay = Dy > 0 ? dy <= ady : (Dy < 0 && dy < ady);
-        const bool az = Dz > 0 ? dz <= adz : (Dz < 0 && dz < adz);
-        if (!(ax | ay | az)) break;
-        uint32_t bn = 0, bd = 1;
-        bool have = false;
-        if (ax) {
-          bn = dx;
-          bd = adx;
-          have = true;
-        }
-        if (ay && (!have || (uint64_t)dy * bd < (uint64_t)bn * ady)) {
-          bn = dy;
-          bd = ady;
-          have = true;
-        }
-        if (az && (!have || (uint64_t)dz * bd < (uint64_t)bn * adz)) {
-          bn = dz;
-          bd = adz;
-        }
-        const float tc = __fdiv_rn((float)bn, (float)bd);
-        run += (tc - tprev) * L;
-        pos |= (uint64_t)bn * pd > (uint64_t)pn * bd;
-        if (pos && (unsigned)cx < (unsigned)g.nx && (unsigned)cy < (unsigned)g.ny && (unsigned)cz < (unsigned)g.nz)
-          visit(cx + g.nx * (cy + g.ny * cz), run);
-        run = 0.f;
-        pos = false;
-        if (ax && (uint64_t)dx * bd == (uint64_t)bn * adx) {
-          cx += Dx > 0 ? 1 : -1;
-          dx += kQOne;
-        }
-        if (ay && (uint64_t)dy * bd == (uint64_t)bn * ady) {
-          cy += Dy > 0 ? 1 : -1;
-          dy += kQOne;
-        }
-        if (az && (uint64_t)dz * bd == (uint64_t)bn * adz) {
-          cz += Dz > 0 ? 1 : -1;
-          dz += kQOne;
-        }
-        pn = bn;
-        pd = bd;
-        tprev = tc;
-      }
-      run += (1.f - tprev) * L;
-      pos |= pn < pd;
-      P = Q;
-    }
+  WalkState s;
+  {
+    const float2 tv = node_tv(g, tab, r, klo);
+    s.qP = node_grid(g, r, __fmaf_rn((float)klo, g.du, g.u0), tv.x, tv.y);
+    s.P = quantise3(s.qP);
   }
-  if (pos && (unsigned)cx < (unsigned)g.nx && (unsigned)cy < (unsigned)g.ny && (unsigned)cz < (unsigned)g.nz)
-    visit(cx + g.nx * (cy + g.ny * cz), run);
+  s.cx = floor_q(s.P.x);
+  s.cy = floor_q(s.P.y);
+  s.cz = floor_q(s.P.z);
+  s.run = 0.f;
+  s.pos = false;
+  int k = klo + 1;
+  // entry extension: straight along the entry slope
+  for (; k < 0 && k <= khi; ++k) {
+    const float kf = (float)k;
+    const float dk = __fmul_rn(kf, g.du);
+    const float t = __fmaf_rn(r.st0, dk, r.t0), v = __fmaf_rn(r.sv0, dk, r.v0);
+    walk_segment(g, s, node_grid(g, r, __fmaf_rn(kf, g.du, g.u0), t, v), visit);
+  }
+  // MLP nodes between the measurement planes
+  const int kmid = min(khi, g.K);
+  for (; k <= kmid; ++k) {
+    const float4 c = tab[k];
+    const float t = __fmaf_rn(c.w, r.st2, __fmaf_rn(c.z, r.t2, __fmaf_rn(c.y, r.st0, __fmul_rn(c.x, r.t0))));
+    const float v = __fmaf_rn(c.w, r.sv2, __fmaf_rn(c.z, r.v2, __fmaf_rn(c.y, r.sv0, __fmul_rn(c.x, r.v0))));
+    walk_segment(g, s, node_grid(g, r, __fmaf_rn((float)k, g.du, g.u0), t, v), visit);
+  }
+  // exit extension: straight along the exit slope
+  for (; k <= khi; ++k) {
+    const float dk = __fmul_rn((float)(k - g.K), g.du);
+    const float t = __fmaf_rn(r.st2, dk, r.t2), v = __fmaf_rn(r.sv2, dk, r.v2);
+    walk_segment(g, s, node_grid(g, r, __fmaf_rn((float)k, g.du, g.u0), t, v), visit);
+  }
+  emit_run(g, s, visit);
 }
 
 }  // namespace pct

@@ -64,10 +64,11 @@ def test_rows_bit_exact_tiny(pct, oracle, n):
         _cmp_rows(oracle, wl.grid, rec, ctx, 0, n, 2.0)
 
 
-def test_rows_bit_exact_head(pct, oracle):
+@pytest.mark.parametrize("sort", [True, False])
+def test_rows_bit_exact_head(pct, oracle, sort):
     wl = S.head_workload(4000, seed=8)
     rec = S.make_histories(wl)
-    with pct.Context(wl.grid, n_blocks=4) as ctx:
+    with pct.Context(wl.grid, n_blocks=4, flags=0 if sort else pct.FLAG_NO_SORT) as ctx:
         ctx.load(rec)
         _cmp_rows(oracle, wl.grid, rec, ctx, 0, 4000, 1.25)
         # a ragged interior range
@@ -102,9 +103,9 @@ def test_block_counts_bit_exact(pct, oracle):
             assert np.array_equal(got, oracle.block_counts(wl.grid, rec, 3, b, mode=oracle.MODE_FP32))
 
 
-def _drop_parity(pct, oracle, wl, n_blocks, n_sweeps, lam=1.0, x0=None):
+def _drop_parity(pct, oracle, wl, n_blocks, n_sweeps, lam=1.0, x0=None, flags=0):
     rec = S.make_histories(wl)
-    with pct.Context(wl.grid, n_blocks=n_blocks, lam=lam) as ctx:
+    with pct.Context(wl.grid, n_blocks=n_blocks, lam=lam, flags=flags) as ctx:
         ctx.load(rec)
         if x0 is not None:
             ctx.set_x0(x0)
@@ -116,9 +117,10 @@ def _drop_parity(pct, oracle, wl, n_blocks, n_sweeps, lam=1.0, x0=None):
     return x, xo
 
 
-def test_drop_parity_tiny_workload(pct, oracle):
+@pytest.mark.parametrize("sort", [True, False])
+def test_drop_parity_tiny_workload(pct, oracle, sort):
     # 32^3 water cylinder, 100k protons, 10 blocks, 10 sweeps
-    _drop_parity(pct, oracle, S.tiny_workload(100_000), 10, 10)
+    _drop_parity(pct, oracle, S.tiny_workload(100_000), 10, 10, flags=0 if sort else pct.FLAG_NO_SORT)
 
 
 @pytest.mark.parametrize("lam,B,n", [(0.5, 7, 10_007), (1.9, 1, 5_000)])
@@ -166,7 +168,7 @@ def test_device_borrow_equals_host_copy(pct):
     trec = {k: torch.from_numpy(v).cuda() for k, v in rec.items()}
     out = []
     for r, borrow in ((rec, False), (trec, True), (trec, False)):
-        with pct.Context(wl.grid, n_blocks=5) as ctx:
+        with pct.Context(wl.grid, n_blocks=5, flags=pct.FLAG_NO_SORT) as ctx:
             ctx.load(r, borrow=borrow)
             ctx.iterate(2)
             out.append(ctx.get_rsp())
