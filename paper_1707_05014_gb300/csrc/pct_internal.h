@@ -13,7 +13,7 @@ constexpr float kQClamp = 1000.0f;       // |q| clamp in voxels (never reached f
 constexpr int kMaxNodes = 2048;          // K + 1 limit (shared-memory MLP table)
 constexpr int kMaxDim = 512;             // per-axis voxel limit
 constexpr int kSortAngles = 256;         // load-time ordering: gantry-angle bins
-constexpr int kSortLateral = 1024;       // load-time ordering: entry lateral-position bins
+constexpr int kSortLateral = 4096;       // load-time ordering: mid-path lateral-position bins
 constexpr int kRowCap = 512;             // runs kept per history between the fused kernel's two passes
 
 // Grid and node geometry in the single-precision form the kernels use.

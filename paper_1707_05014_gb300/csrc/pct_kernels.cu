@@ -190,7 +190,10 @@ __global__ void sort_key_kernel(Rec r, int64_t n, int n_ang, int n_lat, float la
   float a = atan2f(r.sphi[i], r.cphi[i]);
   if (a < 0.f) a += two_pi;
   int ab = min(n_ang - 1, max(0, (int)(a * (n_ang / two_pi) + 0.5f) % n_ang));
-  int tb = (int)floorf((r.t0[i] + lat_lim) * (n_lat / (2.f * lat_lim)));
+  // lateral position halfway between the planes: neighbouring lanes then stay
+  // within a fraction of a voxel of each other along the whole path
+  const float tmid = 0.5f * (r.t0[i] + r.t2[i]);
+  int tb = (int)floorf((tmid + lat_lim) * (n_lat / (2.f * lat_lim)));
   tb = min(n_lat - 1, max(0, tb));
   key[i] = (unsigned)(ab * n_lat + tb);
 }

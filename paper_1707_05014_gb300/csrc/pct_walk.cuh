@@ -175,48 +175,73 @@ __device__ __forceinline__ void walk_segment(const Geo& g, WalkState& s, const f
     s.run += L;
     s.pos |= moved;
   } else if (abs(sx) <= 1 && abs(sy) <= 1 && abs(sz) <= 1) {
-    // each crossing axis crosses exactly one face; its crossing parameter is
-    // the exact fraction n/d
+    // Each crossing axis crosses exactly one face, at the exact fraction
+    // n/d of the segment. Events are ordered by the float fractions (fast
+    // division, 2 ulp); where two of them lie within 1e-6 of each other the
+    // exact 32x32->64-bit cross-multiplication decides order and ties. Two
+    // distinct fractions differ by at least 1/(d1 d2) but may round alike,
+    // hence the window; a float fraction is 0 exactly when n = 0.
     const uint32_t ddx = (uint32_t)abs(Dx), ddy = (uint32_t)abs(Dy), ddz = (uint32_t)abs(Dz);
     const uint32_t ndx = sx > 0 ? (uint32_t)(nx * kQOne - s.P.x) : (uint32_t)(s.P.x - s.cx * kQOne);
     const uint32_t ndy = sy > 0 ? (uint32_t)(ny * kQOne - s.P.y) : (uint32_t)(s.P.y - s.cy * kQOne);
     const uint32_t ndz = sz > 0 ? (uint32_t)(nz * kQOne - s.P.z) : (uint32_t)(s.P.z - s.cz * kQOne);
-    bool rx = sx != 0, ry = sy != 0, rz = sz != 0;  // crossings not yet taken
-    uint32_t pn = 0, pd = 1;                         // previous event tau = pn / pd
+    float tx = sx ? __fdividef((float)ndx, (float)ddx) : INFINITY;
+    float ty = sy ? __fdividef((float)ndy, (float)ddy) : INFINITY;
+    float tz = sz ? __fdividef((float)ndz, (float)ddz) : INFINITY;
     float tprev = 0.f;
-    while (rx | ry | rz) {
-      uint32_t bn = rx ? ndx : (ry ? ndy : ndz);
-      uint32_t bd = rx ? ddx : (ry ? ddy : ddz);
-      if (ry && (uint64_t)ndy * bd < (uint64_t)bn * ddy) {
-        bn = ndy;
-        bd = ddy;
+    bool first = true;
+    uint32_t ln = 0, ld = 1;  // exact fraction of the latest event
+    for (;;) {
+      const float m = fminf(tx, fminf(ty, tz));
+      if (m == INFINITY) break;
+      const float lim = __fmaf_rn(m, 1e-6f, m) + 1e-7f;
+      bool ex = tx <= lim, ey = ty <= lim, ez = tz <= lim;
+      uint32_t bn, bd;
+      if ((int)ex + (int)ey + (int)ez > 1) {
+        // near tie: keep the exact minima only
+        bn = 0xffffffffu;
+        bd = 1;
+        if (ex) {
+          bn = ndx;
+          bd = ddx;
+        }
+        if (ey && (uint64_t)ndy * bd < (uint64_t)bn * ddy) {
+          bn = ndy;
+          bd = ddy;
+        }
+        if (ez && (uint64_t)ndz * bd < (uint64_t)bn * ddz) {
+          bn = ndz;
+          bd = ddz;
+        }
+        ex = ex && (uint64_t)ndx * bd == (uint64_t)bn * ddx;
+        ey = ey && (uint64_t)ndy * bd == (uint64_t)bn * ddy;
+        ez = ez && (uint64_t)ndz * bd == (uint64_t)bn * ddz;
+      } else {
+        bn = ex ? ndx : (ey ? ndy : ndz);
+        bd = ex ? ddx : (ey ? ddy : ddz);
       }
-      if (rz && (uint64_t)ndz * bd < (uint64_t)bn * ddz) {
-        bn = ndz;
-        bd = ddz;
-      }
-      const float tc = __fdividef((float)bn, (float)bd);
-      s.run += (tc - tprev) * L;
-      s.pos |= (uint64_t)bn * pd > (uint64_t)pn * bd;
+      s.run += (m - tprev) * L;
+      s.pos |= !first || bn > 0;  // later events are exactly after the previous one
       emit_run(g, s, visit);
-      if (rx && (uint64_t)ndx * bd == (uint64_t)bn * ddx) {
+      if (ex) {
         s.cx += sx;
-        rx = false;
+        tx = INFINITY;
       }
-      if (ry && (uint64_t)ndy * bd == (uint64_t)bn * ddy) {
+      if (ey) {
         s.cy += sy;
-        ry = false;
+        ty = INFINITY;
       }
-      if (rz && (uint64_t)ndz * bd == (uint64_t)bn * ddz) {
+      if (ez) {
         s.cz += sz;
-        rz = false;
+        tz = INFINITY;
       }
-      pn = bn;
-      pd = bd;
-      tprev = tc;
+      tprev = m;
+      first = false;
+      ln = bn;
+      ld = bd;
     }
     s.run += (1.f - tprev) * L;
-    s.pos |= pn < pd;
+    s.pos |= ln < ld;
   } else {
     // general case: an axis may cross several faces
     const uint32_t adx = (uint32_t)abs(Dx), ady = (uint32_t)abs(Dy), adz = (uint32_t)abs(Dz);
