@@ -179,6 +179,32 @@ PCT_API pct_status pct_sync(pct_ctx *ctx);
 /* Kernel launches queued by this context since creation (for accounting). */
 PCT_API int64_t pct_launch_count(const pct_ctx *ctx);
 
+/* One DROP block update that allocates no device or host memory, for callers
+ * that cannot allocate once they run (services that reserve all GPU memory
+ * at start-up for a fixed plan, plugins whose host application owns every
+ * device allocation). The paper has no counterpart; it is the same update as
+ * one block of pct_iterate without a context.
+ *
+ * h: the histories of ONE block, DEVICE pointers, used in place in the given
+ * order. x: DEVICE array of nx*ny*nz floats, read and updated in place:
+ * x_j += lambda/s_j * sum_i a_ij (b_i - a_i.x)/|a_i|^2. cfg: lambda,
+ * node_step_mm, flags (PCT_FLAG_CLAMP, PCT_FLAG_NO_KAHAN) and clamp_min are
+ * used; n_blocks, threads_per_proton and cta_threads are ignored. stream: a
+ * cudaStream_t (NULL = the legacy default stream).
+ *
+ * Scratch: a fixed 16.1 MiB device array inside the library (its update
+ * accumulator, run counts and MLP table) that every GPU loading the library
+ * holds until exit. Grids above 2,097,152 voxels return PCT_ERR_CAPACITY.
+ * The first call on a device looks up that array's device address with the
+ * device current; make the first call before any stream capture. Every call
+ * uses the same array and clears what must start at zero, so calls that
+ * overlap on the GPU (different streams or threads, same device) race.
+ * Validates the records (as pct_load_histories does) and synchronises the
+ * stream once to report PCT_ERR_INVALID_DATA; the update itself is queued
+ * asynchronously. No cudaMalloc, cudaFree or other allocating call is made. */
+PCT_API pct_status pct_drop_block_noalloc(const pct_grid *grid, const pct_config *cfg, const pct_histories *h,
+                                          float *x, void *stream);
+
 /* Text for the last error of the calling thread ("" if none). */
 PCT_API const char *pct_last_error(void);
 

@@ -96,6 +96,8 @@ pct_status sync_and_check(pct_ctx* c) {
 
 }  // namespace
 
+void pct::set_error_text(const char* msg) { g_err = msg; }
+
 extern "C" {
 
 const char* pct_last_error(void) { return g_err.c_str(); }

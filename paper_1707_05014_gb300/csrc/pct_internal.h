@@ -63,4 +63,7 @@ cudaError_t launch_row_fill(const Geo& g, const Rec& r, const float4* tab, int64
                             const int64_t* where, const int64_t* row_ptr, int32_t* vox, float* len, int32_t* nodes,
                             cudaStream_t s);
 
+// Set the text that pct_last_error() returns on the calling thread.
+void set_error_text(const char* msg);
+
 }  // namespace pct
