@@ -181,6 +181,90 @@ def run_reference(args):
     return 0
 
 
+def run_batched(args):
+    """Batched variant: 32 independent reconstructions of uneven size advanced by
+    one persistent launch per sweep (pct_batch_*), autotuned; the same sweep
+    done one context at a time (pct_iterate) is timed beside it."""
+    import torch
+
+    from paper_1707_05014_gb300 import build as B
+    from paper_1707_05014_gb300 import pct as P
+    from paper_1707_05014_gb300 import synthetic as S
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    torch.cuda.set_device(local)
+    B.build()
+    wls = S.batch_workloads(n_recon=args.n_recon, seed=4 + rank)
+    ctxs, ops_per_sweep, total = [], 0.0, 0
+    for w in wls:
+        rec = S.make_histories_device(w, device=f"cuda:{local}")
+        c = P.Context(w.grid, n_blocks=w.n_blocks, device=local)
+        c.load(rec)
+        k = min(w.n, 20_000)
+        rs = P.Context(w.grid, n_blocks=1, device=local)
+        rs.load({f: v[:k] for f, v in rec.items()})
+        runs = float(rs.rows(0, k)[0][-1].item()) / k
+        rs.close()
+        del rec
+        ops_per_sweep += w.n * (OPS_PER_MLP_NODE * (c.K + 1) + OPS_PER_RUN * runs)
+        total += w.n
+        ctxs.append(c)
+    torch.cuda.empty_cache()
+    batch = P.Batch(ctxs)
+    tune = batch.autotune()
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        batch.iterate(1)
+    batch.sync()
+    clocks = ClockSampler(local)
+    clocks.start()
+    l0 = batch.launches
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        batch.iterate(1)
+    e1.record(stream)
+    batch.sync()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    launches = batch.launches - l0
+    # the same sweeps one reconstruction at a time (pct_iterate, one graph each)
+    s0 = torch.cuda.Event(enable_timing=True)
+    s1 = torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    for c in ctxs:
+        c.iterate(1)
+    s1.record(stream)
+    torch.cuda.synchronize()
+    seq_ms = s0.elapsed_time(s1)
+    batch.close()
+    value = total * args.steps * world / (ms / 1e3)
+    alu_peak = ALU_LANES_PER_SM * N_SMS * _peaks()[0].get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    achieved = ops_per_sweep * args.steps / (ms / 1e3) / 1e12
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"batched{len(wls)}", "reconstructions": len(wls), "histories": total,
+                       "grids": "64x64x32 .. 160x160x64 over 200 mm", "histories_each": "2M-40M log-uniform",
+                       "n_blocks": 10, "step": "one DROP sweep of every reconstruction (one persistent launch)",
+                       "parallelism": f"replicas{world}"},
+            "roofline": {"kernel": "batch_kernel", "bound": "alu", "achieved": achieved, "peak": alu_peak,
+                         "unit": "Tops/s", "frac": achieved / alu_peak, "traffic": None},
+            "autotune": tune, "sequential_contexts_value": total / (seq_ms / 1e3),
+            "gpu_launches": launches, "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    for c in ctxs:
+        c.close()
+    return 0
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -331,9 +415,13 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=1_000_000)
     ap.add_argument("--ref-sample", type=int, default=200_000)
     ap.add_argument("--no-sort", action="store_true", help="keep each block in load order (A/B of the ordering)")
+    ap.add_argument("--workload", default="head", choices=["head", "batched"])
+    ap.add_argument("--n-recon", type=int, default=32, help="reconstructions of the batched workload")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        return run_batched(args)
     return run_ours(args)
 
 

@@ -179,6 +179,67 @@ PCT_API pct_status pct_sync(pct_ctx *ctx);
 /* Kernel launches queued by this context since creation (for accounting). */
 PCT_API int64_t pct_launch_count(const pct_ctx *ctx);
 
+/* ---- Batched reconstructions (no counterpart in the paper: a system
+ * feature). Several loaded contexts on one device, of uneven size, advance
+ * together. Two modes, chosen by pct_batch_autotune (or set in the config):
+ * PCT_BATCH_PERSISTENT -- ONE persistent launch per call: CTAs take work items
+ * (a chunk of one block's histories, or a voxel tile of one block update) from
+ * a fixed block-major queue over all reconstructions; per-reconstruction
+ * counters with bounded waits keep each reconstruction's DROP stages in order
+ * (Sec. 2.1, Fig. 1: block b starts from the result of block b-1).
+ * PCT_BATCH_GRAPH_BRANCHES -- each reconstruction's stages as a chain of the
+ * per-block kernels; the chains run as parallel branches of one CUDA graph.
+ * Either way each reconstruction's result equals its own pct_iterate up to
+ * floating-point summation order. ---- */
+
+typedef struct pct_batch pct_batch;
+
+#define PCT_BATCH_PERSISTENT 1     /* one persistent launch per call (work queue)      */
+#define PCT_BATCH_GRAPH_BRANCHES 2 /* each reconstruction a chain of per-block kernels;
+                                      the chains are parallel branches of one graph    */
+
+typedef struct pct_batch_config {
+  int32_t mode;                   /* PCT_BATCH_*; other values: PCT_BATCH_GRAPH_BRANCHES */
+  int32_t branches;               /* graph-branch mode: concurrent branches (1..8);
+                                     <= 0: min(8, n)                                    */
+  int32_t chunk;                  /* histories per work item; <= 0: 4096                   */
+  int32_t ctas_per_sm;            /* resident CTAs per SM; <= 0 or above the occupancy
+                                     limit: the occupancy limit                            */
+  int32_t apply_tiles;            /* voxel tiles per block update; <= 0: one per 32768
+                                     voxels, at most 64                                    */
+  double wait_limit_s;            /* bound on every wait inside the launch; <= 0: 2 s       */
+  int32_t debug_unreachable_wait; /* test hook: non-zero makes every block-update wait
+                                     unreachable, so the bound runs out and the call
+                                     reports PCT_ERR_TIMEOUT (the GPU stays usable)        */
+} pct_batch_config;
+
+/* Group n loaded contexts (same device) for batched sweeps. cfg may be NULL
+ * (defaults). The contexts must outlive the batch and must not be reloaded
+ * while it exists. */
+PCT_API pct_status pct_batch_create(pct_batch **out, pct_ctx *const *ctxs, int32_t n, const pct_batch_config *cfg);
+PCT_API pct_status pct_batch_destroy(pct_batch *batch);
+
+/* n_sweeps DROP sweeps of every reconstruction in one persistent launch
+ * (captured once per n_sweeps as a CUDA graph), queued on `stream` (a
+ * cudaStream_t; NULL = the batch's own stream). Asynchronous. */
+PCT_API pct_status pct_batch_iterate(pct_batch *batch, int32_t n_sweeps, void *stream);
+
+/* Wait for the batch's work on `stream` (NULL = own stream); returns
+ * PCT_ERR_TIMEOUT if a bounded wait ran out: the blocks not applied in that
+ * call are dropped (update buffers cleared), x stays finite and the contexts
+ * stay usable. */
+PCT_API pct_status pct_batch_sync(pct_batch *batch, void *stream);
+
+/* Time one sweep for each candidate -- graph branches with 1, 4 or 8
+ * branches; persistent with chunk in {2048, 4096, 8192} and CTAs per SM in
+ * {occupancy limit, limit - 1, limit / 2} -- keep the fastest, and restore
+ * every reconstruction's x. Writes the chosen configuration and its sweep
+ * time (ms). */
+PCT_API pct_status pct_batch_autotune(pct_batch *batch, pct_batch_config *chosen, float *best_ms);
+
+/* Kernel launches made by the batch (for accounting). */
+PCT_API int64_t pct_batch_launch_count(const pct_batch *batch);
+
 /* One DROP block update that allocates no device or host memory, for callers
  * that cannot allocate once they run (services that reserve all GPU memory
  * at start-up for a fixed plan, plugins whose host application owns every

@@ -1,0 +1,42 @@
+// Context object behind the C ABI's pct_ctx handle (shared by the library's
+// translation units; not part of the ABI).
+#pragma once
+
+#include <stdint.h>
+
+#include "../../include/pct.h"
+#include "pct_internal.h"
+
+struct pct_ctx {
+  int device = 0;
+  pct_grid grid{};
+  pct_config cfg{};
+  pct::Geo geo{};
+  double R = 0, du = 0;
+  int K = 0, E = 0;
+  int64_t M = 0;
+  float pos_limit = 0;
+  cudaStream_t own_stream = nullptr;  // created by the context; also the capture stream
+  cudaStream_t stream = nullptr;      // where work is queued
+  double* tab64 = nullptr;
+  float4* tab32 = nullptr;
+  int64_t n = 0;
+  float* rec_store = nullptr;  // owned copy of the 11 record arrays (null when borrowed)
+  pct::Rec rec{};
+  int64_t* where = nullptr;    // load index -> stored position (null: stored in load order)
+  float* x = nullptr;
+  float* delta = nullptr;
+  float* inv_s = nullptr;  // B x M
+  unsigned int* cnt = nullptr;
+  unsigned long long* first_bad = nullptr;
+  cudaGraphExec_t sweep = nullptr;
+  cudaEvent_t* ev = nullptr;  // 3 per block (profiling): fused start, fused end, apply end
+  bool swept = false;
+  int64_t launches = 0;
+  bool loaded = false;
+};
+
+namespace pct {
+// First history of DROP block b: b * n / B (blocks are contiguous ranges).
+inline int64_t block_first(const pct_ctx* c, int b) { return (int64_t)b * c->n / c->cfg.n_blocks; }
+}  // namespace pct

@@ -1,0 +1,91 @@
+// Per-history DROP contribution (arXiv 1707.05014 Sec. 2.1, Fig. 1):
+//   r_i = lambda (b_i - a_i.x) / |a_i|^2,   delta_j += r_i a_ij
+// with a_i the MLP row (Sec. 2) walked on the fly. Shared by the per-block
+// kernel and the batched persistent kernel.
+#pragma once
+
+#include "pct_walk.cuh"
+
+namespace pct {
+
+// Plain (weak) global load, cached in L1. Written as PTX so the compiler
+// cannot turn it into a read-only (non-coherent) load: under the PTX memory
+// model a weak load ordered after an acquire (counter read + fence) and a CTA
+// barrier observes every write released before that counter was set.
+__device__ __forceinline__ float ld_weak(const float* p) {
+  float v;
+  asm("ld.global.f32 %0, [%1];" : "=f"(v) : "l"(p));
+  return v;
+}
+
+// MLP nodes -> walk -> compensated a_i.x and |a_i|^2 -> relaxed residual ->
+// scatter-add into delta. The walk keeps the row (voxel, chord) in
+// thread-local memory so the scatter replays it instead of walking again; a
+// row longer than kRowCap runs (none for valid records on the supported
+// grids) is walked a second time instead. flags & 2: plain instead of
+// compensated summation.
+//
+// kCoherent: x may change while the kernel runs (the batched persistent
+// kernel applies block updates between work items), so x is read with plain
+// weak loads instead of the read-only path (which assumes data that never
+// changes during the launch).
+template <bool kCoherent = false>
+__device__ __forceinline__ void drop_history(const Geo& g, const float4* __restrict__ tab, const Rec& r, int64_t i,
+                                             const float* __restrict__ x, float* __restrict__ delta, float lambda,
+                                             int flags) {
+  auto xload = [&](int j) { return kCoherent ? ld_weak(x + j) : __ldg(x + j); };
+  const RecV v = load_rec(r, i);
+  uint2 row[kRowCap];
+  int nrow = 0;
+  float y = 0.f, c = 0.f, nn = 0.f;
+  if (flags & 2) {
+    walk_proton(g, tab, v, [&](int j, float l) {
+      y = __fmaf_rn(l, xload(j), y);
+      nn = __fmaf_rn(l, l, nn);
+      if (nrow < kRowCap) row[nrow] = make_uint2((unsigned)j, __float_as_uint(l));
+      ++nrow;
+    });
+  } else {
+    // Kahan-compensated sum of l * x_j: the true sum is y - c
+    walk_proton(g, tab, v, [&](int j, float l) {
+      const float term = __fsub_rn(__fmul_rn(l, xload(j)), c);
+      const float t = __fadd_rn(y, term);
+      c = __fsub_rn(__fsub_rn(t, y), term);
+      y = t;
+      nn = __fmaf_rn(l, l, nn);
+      if (nrow < kRowCap) row[nrow] = make_uint2((unsigned)j, __float_as_uint(l));
+      ++nrow;
+    });
+  }
+  if (!(nn > 0.f)) return;
+  const float res = __fadd_rn(__fsub_rn(v.wepl, y), c);
+  const float ri = lambda * res / nn;
+  if (nrow <= kRowCap) {
+    for (int q = 0; q < nrow; ++q) {
+      const uint2 e = row[q];
+      atomicAdd(delta + e.x, __uint_as_float(e.y) * ri);
+    }
+  } else {
+    walk_proton(g, tab, v, [&](int j, float l) { atomicAdd(delta + j, l * ri); });
+  }
+}
+
+// x_j += delta_j / s_j (optionally clamped), delta_j = 0. kCoherent: x and
+// delta are read and written at L2 (other CTAs of the same launch use them).
+template <bool kCoherent = false>
+__device__ __forceinline__ void apply_voxel(float* __restrict__ x, float* __restrict__ delta,
+                                            const float* __restrict__ inv_s, int64_t j, int clamp, float clamp_min) {
+  if (kCoherent) {
+    float xv = __fmaf_rn(__ldcg(delta + j), inv_s[j], __ldcg(x + j));
+    if (clamp) xv = fmaxf(xv, clamp_min);
+    __stcg(x + j, xv);
+    __stcg(delta + j, 0.f);
+  } else {
+    float xv = __fmaf_rn(delta[j], inv_s[j], x[j]);
+    if (clamp) xv = fmaxf(xv, clamp_min);
+    x[j] = xv;
+    delta[j] = 0.f;
+  }
+}
+
+}  // namespace pct

@@ -6,7 +6,7 @@
 //   x_j += delta_j / s_j     (s_j = number of runs of block b in voxel j)
 // The fused kernel computes a_i twice from the MLP (once for a_i.x and
 // |a_i|^2, once for the scatter) instead of storing it.
-#include "pct_walk.cuh"
+#include "pct_drop.cuh"
 
 namespace pct {
 namespace {
@@ -55,11 +55,7 @@ __global__ void counts_to_float_kernel(const unsigned int* __restrict__ cnt, flo
   out[j] = (float)cnt[j];
 }
 
-// One thread per proton: MLP nodes -> walk -> compensated a_i.x and |a_i|^2
-// -> relaxed residual -> scatter-add into delta. The first pass keeps the
-// row (voxel, chord) in thread-local memory so the scatter replays it instead
-// of walking again; a row longer than kRowCap runs (none for valid records on
-// the supported grids) is walked a second time instead.
+// One thread per proton (see drop_history).
 __global__ void __launch_bounds__(128) drop_fused_kernel(Geo g, Rec r, const float4* __restrict__ tab_g,
                                                           int64_t first, int64_t count, const float* __restrict__ x,
                                                           float* __restrict__ delta, float lambda, int flags) {
@@ -67,50 +63,14 @@ __global__ void __launch_bounds__(128) drop_fused_kernel(Geo g, Rec r, const flo
   load_table(tab_g, tab, g.K + 1);
   int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= count) return;
-  const RecV v = load_rec(r, first + p);
-  uint2 row[kRowCap];
-  int nrow = 0;
-  float y = 0.f, c = 0.f, nn = 0.f;
-  if (flags & 2) {
-    walk_proton(g, tab, v, [&](int j, float l) {
-      y = __fmaf_rn(l, __ldg(x + j), y);
-      nn = __fmaf_rn(l, l, nn);
-      if (nrow < kRowCap) row[nrow] = make_uint2((unsigned)j, __float_as_uint(l));
-      ++nrow;
-    });
-  } else {
-    // Kahan-compensated sum of l * x_j: the true sum is y - c
-    walk_proton(g, tab, v, [&](int j, float l) {
-      const float term = __fsub_rn(__fmul_rn(l, __ldg(x + j)), c);
-      const float t = __fadd_rn(y, term);
-      c = __fsub_rn(__fsub_rn(t, y), term);
-      y = t;
-      nn = __fmaf_rn(l, l, nn);
-      if (nrow < kRowCap) row[nrow] = make_uint2((unsigned)j, __float_as_uint(l));
-      ++nrow;
-    });
-  }
-  if (!(nn > 0.f)) return;
-  const float res = __fadd_rn(__fsub_rn(v.wepl, y), c);
-  const float ri = lambda * res / nn;
-  if (nrow <= kRowCap) {
-    for (int q = 0; q < nrow; ++q) {
-      const uint2 e = row[q];
-      atomicAdd(delta + e.x, __uint_as_float(e.y) * ri);
-    }
-  } else {
-    walk_proton(g, tab, v, [&](int j, float l) { atomicAdd(delta + j, l * ri); });
-  }
+  drop_history(g, tab, r, first + p, x, delta, lambda, flags);
 }
 
 __global__ void drop_apply_kernel(float* __restrict__ x, float* __restrict__ delta, const float* __restrict__ inv_s,
                                   int64_t M, int clamp, float clamp_min) {
   int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= M) return;
-  float xv = __fmaf_rn(delta[j], inv_s[j], x[j]);
-  if (clamp) xv = fmaxf(xv, clamp_min);
-  x[j] = xv;
-  delta[j] = 0.f;
+  apply_voxel(x, delta, inv_s, j, clamp, clamp_min);
 }
 
 __global__ void row_count_kernel(Geo g, Rec r, const float4* __restrict__ tab_g, int64_t first, int64_t count,

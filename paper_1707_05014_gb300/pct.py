@@ -71,6 +71,12 @@ _SIGS = {
     "pct_get_rsp": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int],
     "pct_sync": [ctypes.c_void_p],
     "pct_last_sweep_times": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
+    "pct_batch_create": [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p), ctypes.c_int32,
+                         ctypes.c_void_p],
+    "pct_batch_destroy": [ctypes.c_void_p],
+    "pct_batch_iterate": [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p],
+    "pct_batch_sync": [ctypes.c_void_p, ctypes.c_void_p],
+    "pct_batch_autotune": [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_float)],
 }
 
 
@@ -90,6 +96,8 @@ def load_library(path: str = LIB_PATH):
     L.pct_last_error.restype = ctypes.c_char_p
     L.pct_launch_count.argtypes = [ctypes.c_void_p]
     L.pct_launch_count.restype = ctypes.c_int64
+    L.pct_batch_launch_count.argtypes = [ctypes.c_void_p]
+    L.pct_batch_launch_count.restype = ctypes.c_int64
     if path == LIB_PATH:
         _lib = L
     return L
@@ -286,3 +294,65 @@ class Context:
     @property
     def launches(self) -> int:
         return int(self._L.pct_launch_count(self._h))
+
+
+BATCH_PERSISTENT = 1
+BATCH_GRAPH_BRANCHES = 2
+
+
+class BatchConfig(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("branches", ctypes.c_int32), ("chunk", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("apply_tiles", ctypes.c_int32),
+                ("wait_limit_s", ctypes.c_double), ("debug_unreachable_wait", ctypes.c_int32)]
+
+
+class Batch:
+    """Several loaded contexts advanced together by one persistent launch per
+    call (pct_batch_*). The contexts must stay alive and loaded."""
+
+    def __init__(self, contexts, mode: int = BATCH_GRAPH_BRANCHES, branches: int = 0, chunk: int = 0,
+                 ctas_per_sm: int = 0, apply_tiles: int = 0, wait_limit_s: float = 0.0,
+                 debug_unreachable_wait: bool = False):
+        L = load_library()
+        self._L = L
+        self.contexts = list(contexts)
+        arr = (ctypes.c_void_p * len(self.contexts))(*[c._h.value for c in self.contexts])
+        self.cfg = BatchConfig(int(mode), int(branches), int(chunk), int(ctas_per_sm), int(apply_tiles),
+                               float(wait_limit_s), 1 if debug_unreachable_wait else 0)
+        h = ctypes.c_void_p()
+        _check(L.pct_batch_create(ctypes.byref(h), arr, len(self.contexts), ctypes.byref(self.cfg)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._L.pct_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def iterate(self, n_sweeps: int) -> None:
+        _check(self._L.pct_batch_iterate(self._h, int(n_sweeps), _stream_ptr()))
+
+    def sync(self) -> None:
+        _check(self._L.pct_batch_sync(self._h, _stream_ptr()))
+
+    def autotune(self):
+        chosen = BatchConfig()
+        ms = ctypes.c_float(0.0)
+        _check(self._L.pct_batch_autotune(self._h, ctypes.byref(chosen), ctypes.byref(ms)))
+        return {"mode": "persistent" if chosen.mode == BATCH_PERSISTENT else "graph_branches",
+                "branches": chosen.branches, "chunk": chosen.chunk, "ctas_per_sm": chosen.ctas_per_sm,
+                "apply_tiles": chosen.apply_tiles, "sweep_ms": ms.value}
+
+    @property
+    def launches(self) -> int:
+        return int(self._L.pct_batch_launch_count(self._h))

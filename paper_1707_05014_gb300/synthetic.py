@@ -280,6 +280,26 @@ def head_workload(n: int = 50_000_000, seed: int = 2) -> Workload:
     return Workload(f"head160_{n}", g, n, seed, 90, g.radius, 40.0, 10, 10, "head")
 
 
+def batch_workloads(n_recon: int = 32, seed: int = 4, n_min: int = 2_000_000, n_max: int = 40_000_000,
+                    n_blocks: int = 10):
+    """Independent reconstructions of uneven size: grids from 64x64x32 to
+    160x160x64 voxels over a 200 mm field (nx log-uniform, nz = 0.4 nx clamped
+    to [32, 64]) and 2M-40M histories each (log-uniform), seeded; random head
+    phantoms (+-10 % jitter), 90 angles."""
+    rng = np.random.Generator(np.random.Philox(seed))
+    out = []
+    for r in range(n_recon):
+        nx = int(round(math.exp(rng.uniform(math.log(64), math.log(160))) / 8.0)) * 8
+        nx = min(160, max(64, nx))
+        nz = min(64, max(32, int(round(0.4 * nx / 2.0)) * 2))
+        h = 200.0 / nx
+        n = int(math.exp(rng.uniform(math.log(n_min), math.log(n_max))))
+        g = Grid(nx, nx, nz, h, h, h)
+        out.append(Workload(f"batch{r}_{nx}x{nx}x{nz}_{n}", g, n, seed * 1000 + r, 90, g.radius,
+                            min(40.0, 0.5 * nz * h - 2.0), n_blocks, 10, "head", 0.1))
+    return out
+
+
 def slab_sigma(length_mm: float) -> Tuple[float, float]:
     """Generator recipe for the exit-state spread: slope sigma 14.7 mrad for
     a 64 mm slab scaled by sqrt(length/64 mm); returned with the length."""

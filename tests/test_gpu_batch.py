@@ -1,0 +1,100 @@
+"""Batched persistent launch: several reconstructions of uneven size advance in
+one launch per call; each result equals its own context's pct_iterate (the
+same DROP stages, Sec. 2.1 / Fig. 1) up to summation order, and a bounded wait
+that cannot be met ends the launch with PCT_ERR_TIMEOUT instead of a hang."""
+import numpy as np
+import pytest
+
+from paper_1707_05014_gb300 import synthetic as S
+
+pytestmark = pytest.mark.gpu
+
+RSP_TOL = 1e-3
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA GPU required for -m gpu tests")
+    from paper_1707_05014_gb300 import build
+    from paper_1707_05014_gb300 import pct
+
+    build.build()
+    return pct
+
+
+def _workloads():
+    return [
+        (S.tiny_workload(30_000, seed=51), 3),
+        (S.Workload("head_small", S.Grid(64, 64, 32, 3.125, 3.125, 3.125), 80_000, 52, 90, 100.0, 45.0, 7, 2, "head"), 7),
+        (S.tiny_workload(7_001, seed=53), 1),
+        (S.Workload("head80", S.Grid(80, 80, 40, 2.5, 2.5, 2.5), 50_000, 54, 45, 100.0, 45.0, 5, 2, "head"), 5),
+    ]
+
+
+@pytest.mark.parametrize("mode,chunk", [(1, 0), (1, 1000), (2, 0)])
+def test_batch_matches_individual_contexts(P, mode, chunk):
+    wls = _workloads()
+    recs = [S.make_histories(w) for w, _ in wls]
+    refs = []
+    for (w, B), r in zip(wls, recs):
+        with P.Context(w.grid, n_blocks=B) as c:
+            c.load(r)
+            c.iterate(2)
+            refs.append(c.get_rsp().astype(np.float64))
+    ctxs = []
+    for (w, B), r in zip(wls, recs):
+        c = P.Context(w.grid, n_blocks=B)
+        c.load(r)
+        ctxs.append(c)
+    with P.Batch(ctxs, mode=mode, chunk=chunk) as b:
+        b.iterate(1)
+        b.iterate(1)
+        b.sync()
+        per_call = 1 if mode == 1 else sum(2 * B for _, B in wls)
+        assert b.launches == 2 * per_call
+    for c, ref in zip(ctxs, refs):
+        x = c.get_rsp().astype(np.float64)
+        err = np.abs(x - ref) / np.maximum(np.abs(ref), 1.0)
+        assert err.max() <= RSP_TOL, err.max()
+        c.close()
+
+
+def test_batch_autotune_keeps_results(P):
+    wls = _workloads()[:2]
+    ctxs = []
+    for w, B in wls:
+        c = P.Context(w.grid, n_blocks=B)
+        c.load(S.make_histories(w))
+        ctxs.append(c)
+    with P.Batch(ctxs) as b:
+        choice = b.autotune()
+        assert choice["mode"] in ("persistent", "graph_branches") and choice["sweep_ms"] > 0
+        for c in ctxs:  # autotuning restores x
+            assert float(np.abs(c.get_rsp()).max()) == 0.0
+        b.iterate(1)
+        b.sync()
+    for c in ctxs:
+        assert np.isfinite(c.get_rsp()).all()
+        c.close()
+
+
+def test_bounded_wait_reports_timeout_and_gpu_stays_usable(P):
+    w, B = _workloads()[0]
+    rec = S.make_histories(w)
+    c = P.Context(w.grid, n_blocks=B)
+    c.load(rec)
+    with P.Batch([c], mode=P.BATCH_PERSISTENT, wait_limit_s=0.05, debug_unreachable_wait=True) as b:
+        b.iterate(1)
+        with pytest.raises(P.PctError) as ei:
+            b.sync()
+        assert ei.value.code == -6
+    # the context and the GPU keep working
+    with P.Batch([c], mode=P.BATCH_PERSISTENT) as b:
+        b.iterate(1)
+        b.sync()
+    c.iterate(1)
+    assert np.isfinite(c.get_rsp()).all()
+    c.close()
