@@ -148,6 +148,16 @@ PCT_API pct_status pct_load_histories(pct_ctx *ctx, const pct_histories *h, int 
 PCT_API pct_status pct_mlp_rows(pct_ctx *ctx, int64_t first, int64_t count, int64_t *row_ptr, int32_t *vox, float *len,
                         int64_t cap, int32_t *nodes, int64_t *needed);
 
+/* Forward projection y[p] = a_i.x for histories i = first+p (load order) of
+ * the loaded set, with the current x and the fused kernel's arithmetic
+ * (compensated unless PCT_FLAG_NO_KAHAN). y: DEVICE, count floats.
+ * Asynchronous. (Sec. 2: a_i.x is the model WEPL of history i.) */
+PCT_API pct_status pct_project(pct_ctx *ctx, int64_t first, int64_t count, float *y);
+
+/* Data residual sum_i (b_i - a_i.x)^2 over all loaded histories with the
+ * current x, accumulated in double; written to host *sum_sq. Synchronises. */
+PCT_API pct_status pct_residual(pct_ctx *ctx, double *sum_sq);
+
 /* Run counts s_j of DROP block `block` as float (exact integers), M values,
  * written to DEVICE memory `out`. */
 PCT_API pct_status pct_block_counts(pct_ctx *ctx, int32_t block, float *out);

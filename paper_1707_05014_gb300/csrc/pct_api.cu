@@ -164,7 +164,8 @@ pct_status pct_create(pct_ctx** out, const pct_grid* grid, const pct_config* cfg
         cudaMalloc((void**)&c->x, M * sizeof(float)) != cudaSuccess ||
         cudaMalloc((void**)&c->delta, M * sizeof(float)) != cudaSuccess ||
         cudaMalloc((void**)&c->cnt, M * sizeof(unsigned int)) != cudaSuccess ||
-        cudaMalloc((void**)&c->first_bad, sizeof(unsigned long long)) != cudaSuccess) {
+        cudaMalloc((void**)&c->first_bad, sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMalloc((void**)&c->acc, sizeof(double)) != cudaSuccess) {
       (void)cudaGetLastError();
       st = fail(PCT_ERR_NO_MEMORY, "device allocation failed for a %lld-voxel grid", (long long)c->M);
       break;
@@ -206,6 +207,7 @@ pct_status pct_destroy(pct_ctx* c) {
   cudaFree(c->delta);
   cudaFree(c->cnt);
   cudaFree(c->first_bad);
+  cudaFree(c->acc);
   if (c->ev) {
     for (int i = 0; i < 3 * c->cfg.n_blocks; ++i) cudaEventDestroy(c->ev[i]);
     delete[] c->ev;
@@ -377,6 +379,27 @@ pct_status pct_mlp_rows(pct_ctx* c, int64_t first, int64_t count, int64_t* row_p
   PCT_CK(pct::launch_row_fill(c->geo, c->rec, c->tab32, first, count, c->where, row_ptr, vox, len, nodes,
                               c->stream));
   c->launches += 1;
+  return sync_and_check(c);
+}
+
+pct_status pct_project(pct_ctx* c, int64_t first, int64_t count, float* y) {
+  if (!c || (count > 0 && !y)) return fail(PCT_ERR_INVALID_ARG, "ctx or y is NULL");
+  if (!c->loaded) return fail(PCT_ERR_STATE, "no histories loaded");
+  if (first < 0 || count < 0 || first + count > c->n) return fail(PCT_ERR_INVALID_ARG, "range outside [0, n)");
+  PCT_CK(cudaSetDevice(c->device));
+  PCT_CK(pct::launch_project(c->geo, c->rec, c->tab32, first, count, c->where, c->x, c->cfg.flags, y, c->stream));
+  c->launches += 1;
+  return PCT_OK;
+}
+
+pct_status pct_residual(pct_ctx* c, double* sum_sq) {
+  if (!c || !sum_sq) return fail(PCT_ERR_INVALID_ARG, "ctx or sum_sq is NULL");
+  if (!c->loaded) return fail(PCT_ERR_STATE, "no histories loaded");
+  PCT_CK(cudaSetDevice(c->device));
+  PCT_CK(cudaMemsetAsync(c->acc, 0, sizeof(double), c->stream));
+  PCT_CK(pct::launch_residual(c->geo, c->rec, c->tab32, c->n, c->x, c->cfg.flags, c->acc, c->stream));
+  c->launches += 1;
+  PCT_CK(cudaMemcpyAsync(sum_sq, c->acc, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   return sync_and_check(c);
 }
 

@@ -29,6 +29,7 @@ struct pct_ctx {
   float* inv_s = nullptr;  // B x M
   unsigned int* cnt = nullptr;
   unsigned long long* first_bad = nullptr;
+  double* acc = nullptr;  // residual accumulator
   cudaGraphExec_t sweep = nullptr;
   cudaEvent_t* ev = nullptr;  // 3 per block (profiling): fused start, fused end, apply end
   bool swept = false;

@@ -66,6 +66,55 @@ __global__ void __launch_bounds__(128) drop_fused_kernel(Geo g, Rec r, const flo
   drop_history(g, tab, r, first + p, x, delta, lambda, flags);
 }
 
+// Compensated a_i.x (or plain with flags & 2), the arithmetic of the fused
+// kernel's first pass. Returns y - c (Kahan: the true sum is y - c).
+__device__ __forceinline__ float project_history(const Geo& g, const float4* __restrict__ tab, const RecV& v,
+                                                 const float* __restrict__ x, int flags) {
+  float y = 0.f, c = 0.f;
+  if (flags & 2) {
+    walk_proton(g, tab, v, [&](int j, float l) { y = __fmaf_rn(l, __ldg(x + j), y); });
+    return y;
+  }
+  walk_proton(g, tab, v, [&](int j, float l) {
+    const float term = __fsub_rn(__fmul_rn(l, __ldg(x + j)), c);
+    const float t = __fadd_rn(y, term);
+    c = __fsub_rn(__fsub_rn(t, y), term);
+    y = t;
+  });
+  return __fsub_rn(y, c);
+}
+
+__global__ void __launch_bounds__(128) project_kernel(Geo g, Rec r, const float4* __restrict__ tab_g, int64_t first,
+                                                      int64_t count, const int64_t* __restrict__ where,
+                                                      const float* __restrict__ x, int flags, float* __restrict__ y) {
+  extern __shared__ float4 tab[];
+  load_table(tab_g, tab, g.K + 1);
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= count) return;
+  const RecV v = load_rec(r, where ? where[first + p] : first + p);
+  y[p] = project_history(g, tab, v, x, flags);
+}
+
+// sum_i (b_i - a_i.x)^2 over histories [0, n): per-CTA double reduction, one
+// double atomic per CTA.
+__global__ void __launch_bounds__(128) residual_kernel(Geo g, Rec r, const float4* __restrict__ tab_g, int64_t n,
+                                                       const float* __restrict__ x, int flags, double* acc) {
+  extern __shared__ float4 tab[];
+  __shared__ double part[4];
+  load_table(tab_g, tab, g.K + 1);
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double rr = 0.0;
+  if (p < n) {
+    const RecV v = load_rec(r, p);
+    const double res = (double)v.wepl - (double)project_history(g, tab, v, x, flags);
+    rr = res * res;
+  }
+  for (int o = 16; o > 0; o >>= 1) rr += __shfl_down_sync(0xffffffffu, rr, o);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = rr;
+  __syncthreads();
+  if (threadIdx.x == 0) atomicAdd(acc, part[0] + part[1] + part[2] + part[3]);
+}
+
 __global__ void drop_apply_kernel(float* __restrict__ x, float* __restrict__ delta, const float* __restrict__ inv_s,
                                   int64_t M, int clamp, float clamp_min) {
   int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -286,6 +335,21 @@ cudaError_t launch_drop_fused(const Geo& g, const Rec& r, const float4* tab, int
   threads = 128;
   drop_fused_kernel<<<grid_for(count, threads), threads, (g.K + 1) * sizeof(float4), s>>>(g, r, tab, first, count, x,
                                                                                            delta, lambda, flags);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_project(const Geo& g, const Rec& r, const float4* tab, int64_t first, int64_t count,
+                           const int64_t* where, const float* x, int flags, float* y, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  project_kernel<<<grid_for(count, 128), 128, (g.K + 1) * sizeof(float4), s>>>(g, r, tab, first, count, where, x,
+                                                                                flags, y);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_residual(const Geo& g, const Rec& r, const float4* tab, int64_t n, const float* x, int flags,
+                            double* acc, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  residual_kernel<<<grid_for(n, 128), 128, (g.K + 1) * sizeof(float4), s>>>(g, r, tab, n, x, flags, acc);
   return cudaGetLastError();
 }
 

@@ -66,6 +66,8 @@ _SIGS = {
     "pct_mlp_rows": [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
                      ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)],
     "pct_block_counts": [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p],
+    "pct_project": [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p],
+    "pct_residual": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)],
     "pct_set_x0": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int],
     "pct_iterate": [ctypes.c_void_p, ctypes.c_int32],
     "pct_get_rsp": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int],
@@ -243,6 +245,22 @@ class Context:
         n = int(need.value)
         out = (rp, vox[:n], ln[:n])
         return out + (nodes,) if with_nodes else out
+
+    def project(self, first: int = 0, count: Optional[int] = None):
+        """a_i.x for histories [first, first+count) (load order) as a CUDA tensor."""
+        torch = _torch()
+        count = self.n - first if count is None else count
+        y = torch.empty(count, dtype=torch.float32, device=torch.device("cuda", self.device))
+        self._bind_stream()
+        _check(self._L.pct_project(self._h, int(first), int(count), ctypes.c_void_p(y.data_ptr())))
+        return y
+
+    def residual(self) -> float:
+        """sum_i (b_i - a_i.x)^2 over all loaded histories (synchronising)."""
+        out = ctypes.c_double(0.0)
+        self._bind_stream()
+        _check(self._L.pct_residual(self._h, ctypes.byref(out)))
+        return out.value
 
     def block_counts(self, block: int):
         torch = _torch()

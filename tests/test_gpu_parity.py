@@ -175,3 +175,26 @@ def test_device_borrow_equals_host_copy(pct):
     # same inputs, same launch order: only atomic ordering differs
     assert np.abs(out[0] - out[1]).max() <= 1e-4 * max(1.0, np.abs(out[0]).max())
     assert np.abs(out[0] - out[2]).max() <= 1e-4 * max(1.0, np.abs(out[0]).max())
+
+
+@pytest.mark.parametrize("kahan", [True, False])
+def test_projection_and_residual_match_oracle(pct, oracle, kahan):
+    # a_i.x (Sec. 2: the model WEPL) with the fused kernel's arithmetic against
+    # the oracle's FP64 sum over the same rows (FP32-order nodes)
+    wl = S.head_workload(20_000, seed=61)
+    g = wl.grid
+    rec = S.make_histories(wl)
+    x0 = S.voxelize(wl.phantom(), g, ss=2).astype(np.float32)
+    flags = 0 if kahan else pct.FLAG_NO_KAHAN
+    with pct.Context(g, n_blocks=4, flags=flags) as ctx:
+        ctx.load(rec)
+        ctx.set_x0(x0)
+        y = ctx.project(0, 20_000).cpu().numpy().astype(np.float64)
+        y2 = ctx.project(777, 1000).cpu().numpy().astype(np.float64)
+        rr = ctx.residual()
+    yo = oracle.project(g, rec, x0.astype(np.float64), mode=oracle.MODE_FP32)
+    tol = 1e-5 if kahan else 1e-4
+    assert np.all(np.abs(y - yo) <= tol * np.maximum(np.abs(yo), 1.0))
+    assert np.array_equal(y2, y[777:1777])
+    ro = float(((rec["wepl"].astype(np.float64) - yo) ** 2).sum())
+    assert abs(rr - ro) <= 1e-4 * ro
