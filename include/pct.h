@@ -250,6 +250,42 @@ PCT_API pct_status pct_batch_autotune(pct_batch *batch, pct_batch_config *chosen
 /* Kernel launches made by the batch (for accounting). */
 PCT_API int64_t pct_batch_launch_count(const pct_batch *batch);
 
+/* ---- Learned warm start (no counterpart in the paper: a system feature).
+ * A 3-D U-Net f (4 levels, 16/32/64/128 channels, 3x3x3 convolutions,
+ * stride-2 down, nearest-x2-up + conv, additive skips, ReLU) maps the image
+ * x1 after the first DROP sweep to x0 = x1 + f(x1), a starting image closer to
+ * the converged reconstruction. BF16 weights and activations, FP32
+ * accumulation on the tensor cores, FP32 master weights and Adam. Volumes are
+ * nz x ny x nx floats in the reconstruction's voxel order (x fastest); each
+ * dimension a multiple of 8. ---- */
+typedef struct pct_net pct_net;
+
+/* Create a network for nz x ny x nx volumes; He-normal weights from `seed`. */
+PCT_API pct_status pct_net_create(pct_net **out, int32_t nz, int32_t ny, int32_t nx, uint64_t seed, int device);
+PCT_API pct_status pct_net_destroy(pct_net *net);
+
+/* Number of FP32 parameters (15 layers: 27*Cin*Cout weights [tap][ci][co]
+ * then Cout biases each; channel counts padded to >= 16). */
+PCT_API int64_t pct_net_param_count(const pct_net *net);
+/* Copy the FP32 master parameters to / from HOST memory. */
+PCT_API pct_status pct_net_get_params(pct_net *net, float *out);
+PCT_API pct_status pct_net_set_params(pct_net *net, const float *in);
+
+/* x0 = x1 + f(x1); x1, x0 DEVICE arrays. Asynchronous on `stream` (NULL =
+ * the network's own stream). */
+PCT_API pct_status pct_net_forward(pct_net *net, const float *x1, float *x0, void *stream);
+
+/* Forward + backward of the L1 loss mean|x1 + f(x1) - target| without an
+ * update: writes the loss (host *loss) and dLoss/dparams (HOST grads, may be
+ * NULL). x0_scratch: DEVICE array of one volume. Synchronises. */
+PCT_API pct_status pct_net_gradients(pct_net *net, const float *x1, const float *target, float *x0_scratch,
+                                     float *grads, double *loss);
+
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8) on the L1 loss of one pair.
+ * loss may be NULL (then no synchronisation). */
+PCT_API pct_status pct_net_train_step(pct_net *net, const float *x1, const float *target, float *x0_scratch,
+                                      float lr, double *loss, void *stream);
+
 /* One DROP block update that allocates no device or host memory, for callers
  * that cannot allocate once they run (services that reserve all GPU memory
  * at start-up for a fixed plan, plugins whose host application owns every

@@ -79,6 +79,16 @@ _SIGS = {
     "pct_batch_iterate": [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p],
     "pct_batch_sync": [ctypes.c_void_p, ctypes.c_void_p],
     "pct_batch_autotune": [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_float)],
+    "pct_net_create": [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                       ctypes.c_uint64, ctypes.c_int],
+    "pct_net_destroy": [ctypes.c_void_p],
+    "pct_net_get_params": [ctypes.c_void_p, ctypes.c_void_p],
+    "pct_net_set_params": [ctypes.c_void_p, ctypes.c_void_p],
+    "pct_net_forward": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
+    "pct_net_gradients": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                          ctypes.POINTER(ctypes.c_double)],
+    "pct_net_train_step": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_float,
+                           ctypes.POINTER(ctypes.c_double), ctypes.c_void_p],
 }
 
 
@@ -100,6 +110,8 @@ def load_library(path: str = LIB_PATH):
     L.pct_launch_count.restype = ctypes.c_int64
     L.pct_batch_launch_count.argtypes = [ctypes.c_void_p]
     L.pct_batch_launch_count.restype = ctypes.c_int64
+    L.pct_net_param_count.argtypes = [ctypes.c_void_p]
+    L.pct_net_param_count.restype = ctypes.c_int64
     if path == LIB_PATH:
         _lib = L
     return L
@@ -374,3 +386,80 @@ class Batch:
     @property
     def launches(self) -> int:
         return int(self._L.pct_batch_launch_count(self._h))
+
+
+class Net:
+    """Warm-start network (pct_net_*): x0 = x1 + f(x1) for nz x ny x nx volumes
+    (CUDA float tensors in the reconstruction's voxel order)."""
+
+    def __init__(self, nz: int, ny: int, nx: int, seed: int = 0, device: int = 0):
+        L = load_library()
+        self._L = L
+        self.shape = (nz, ny, nx)
+        self.device = device
+        h = ctypes.c_void_p()
+        _check(L.pct_net_create(ctypes.byref(h), int(nz), int(ny), int(nx), int(seed), int(device)))
+        self._h = h
+        self.n_params = int(L.pct_net_param_count(h))
+        self._scratch = None
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._L.pct_net_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _x0(self):
+        torch = _torch()
+        if self._scratch is None:
+            n = self.shape[0] * self.shape[1] * self.shape[2]
+            self._scratch = torch.empty(n, dtype=torch.float32, device=torch.device("cuda", self.device))
+        return self._scratch
+
+    def get_params(self) -> np.ndarray:
+        out = np.empty(self.n_params, dtype=np.float32)
+        _check(self._L.pct_net_get_params(self._h, out.ctypes.data_as(ctypes.c_void_p)))
+        return out
+
+    def set_params(self, p: np.ndarray) -> None:
+        a = np.ascontiguousarray(p, dtype=np.float32)
+        assert a.size == self.n_params
+        _check(self._L.pct_net_set_params(self._h, a.ctypes.data_as(ctypes.c_void_p)))
+
+    def forward(self, x1):
+        torch = _torch()
+        x1 = x1.to(torch.float32).contiguous()
+        x0 = torch.empty_like(x1)
+        _check(self._L.pct_net_forward(self._h, ctypes.c_void_p(x1.data_ptr()), ctypes.c_void_p(x0.data_ptr()),
+                                       _stream_ptr()))
+        return x0
+
+    def gradients(self, x1, target):
+        torch = _torch()
+        x1 = x1.to(torch.float32).contiguous()
+        target = target.to(torch.float32).contiguous()
+        torch.cuda.synchronize()
+        g = np.empty(self.n_params, dtype=np.float32)
+        loss = ctypes.c_double(0.0)
+        _check(self._L.pct_net_gradients(self._h, ctypes.c_void_p(x1.data_ptr()), ctypes.c_void_p(target.data_ptr()),
+                                         ctypes.c_void_p(self._x0().data_ptr()), g.ctypes.data_as(ctypes.c_void_p),
+                                         ctypes.byref(loss)))
+        return loss.value, g
+
+    def train_step(self, x1, target, lr: float = 1e-3, want_loss: bool = True):
+        loss = ctypes.c_double(0.0)
+        _check(self._L.pct_net_train_step(self._h, ctypes.c_void_p(x1.data_ptr()), ctypes.c_void_p(target.data_ptr()),
+                                          ctypes.c_void_p(self._x0().data_ptr()), float(lr),
+                                          ctypes.byref(loss) if want_loss else None, _stream_ptr()))
+        return loss.value if want_loss else None

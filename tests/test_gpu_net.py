@@ -1,0 +1,102 @@
+"""Warm-start network kernels (tensor-core implicit GEMMs) against the FP64
+reference oracle/unet.py: forward output, every parameter gradient, and a
+training run that lowers the loss."""
+import numpy as np
+import pytest
+
+from oracle import unet as U
+
+pytestmark = pytest.mark.gpu
+
+SHAPE = (8, 16, 24)
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA GPU required for -m gpu tests")
+    from paper_1707_05014_gb300 import build
+    from paper_1707_05014_gb300 import pct
+
+    build.build()
+    return pct
+
+
+def _data(seed=0):
+    rng = np.random.Generator(np.random.Philox(seed))
+    x1 = rng.random(SHAPE) * 1.5
+    target = x1 + 0.2 * rng.standard_normal(SHAPE)
+    p = U.init_params(seed + 1)
+    off = 0
+    for ci, co, _, _ in U.SPEC:  # small non-zero biases
+        off += 27 * ci * co
+        p[off:off + co] = 0.05 * rng.standard_normal(co)
+        off += co
+    return x1, target, p.astype(np.float32).astype(np.float64)
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+
+
+def test_param_layout_matches_reference(P):
+    with P.Net(*SHAPE) as net:
+        assert net.n_params == U.param_count()
+        p = net.get_params()
+        assert np.all(np.isfinite(p))
+
+
+def test_forward_matches_reference(P):
+    import torch
+
+    x1, _, p = _data(1)
+    with P.Net(*SHAPE) as net:
+        net.set_params(p)
+        x0 = net.forward(torch.tensor(x1.ravel(), dtype=torch.float32, device="cuda")).cpu().numpy()
+    ref16, _ = U.forward(p, x1.astype(np.float32).astype(np.float64), bf16=True)
+    ref64, _ = U.forward(p, x1.astype(np.float32).astype(np.float64), bf16=False)
+    f_gpu = x0 - x1.ravel()
+    assert _rel(f_gpu, (ref16 - x1).ravel()) < 1e-2
+    assert _rel(f_gpu, (ref64 - x1).ravel()) < 5e-2
+
+
+def test_gradients_match_reference(P):
+    import torch
+
+    x1, target, p = _data(2)
+    x1 = x1.astype(np.float32).astype(np.float64)
+    target = target.astype(np.float32).astype(np.float64)
+    with P.Net(*SHAPE) as net:
+        net.set_params(p)
+        loss, g = net.gradients(torch.tensor(x1.ravel(), dtype=torch.float32, device="cuda"),
+                                torch.tensor(target.ravel(), dtype=torch.float32, device="cuda"))
+    rloss, rg = U.loss_and_grads(p, x1, target, bf16=True)
+    assert abs(loss - rloss) < 1e-3 * rloss
+    off = 0
+    for li, (ci, co, _, _) in enumerate(U.SPEC):
+        n = 27 * ci * co + co
+        a, b = g[off:off + n].astype(np.float64), rg[off:off + n]
+        if np.linalg.norm(b) > 0:
+            assert _rel(a, b) < 5e-2, (li, _rel(a, b))
+        off += n
+
+
+def test_training_lowers_the_loss(P):
+    import torch
+
+    rng = np.random.Generator(np.random.Philox(9))
+    x1 = rng.random(SHAPE).astype(np.float32)
+    # target: a smoothed copy (what the warm start learns: denoise/deblur)
+    t = x1.copy()
+    for ax in range(3):
+        t = (np.roll(t, 1, ax) + t + np.roll(t, -1, ax)) / 3.0
+    dx1 = torch.tensor(x1.ravel(), device="cuda")
+    dt = torch.tensor(t.ravel(), device="cuda")
+    with P.Net(*SHAPE, seed=4) as net:
+        l0 = net.train_step(dx1, dt, lr=2e-3)
+        for _ in range(150):
+            net.train_step(dx1, dt, lr=2e-3, want_loss=False)
+        l1 = net.train_step(dx1, dt, lr=2e-3)
+    assert l1 < 0.5 * l0

@@ -1,0 +1,80 @@
+"""Pins for the FP64 reference of the warm-start network (oracle/unet.py):
+convolution against scipy's correlate, exact adjoint (dot-product) identities
+for every linear step, and the full gradient against central differences."""
+import numpy as np
+import pytest
+
+from oracle import unet as U
+
+
+def test_conv_matches_scipy_correlate():
+    ndimage = pytest.importorskip("scipy.ndimage")
+    rng = np.random.Generator(np.random.Philox(1))
+    x = rng.standard_normal((6, 7, 5, 1))
+    W = rng.standard_normal((27, 1, 1))
+    y = U.conv(x, W, np.zeros(1), 1)[..., 0]
+    k = W[:, 0, 0].reshape(3, 3, 3)
+    ref = ndimage.correlate(x[..., 0], k, mode="constant", cval=0.0)
+    assert np.abs(y - ref).max() < 1e-12
+
+
+def test_stride2_is_subsampled_stride1_and_up_is_repeat():
+    rng = np.random.Generator(np.random.Philox(2))
+    x = rng.standard_normal((8, 6, 4, 3))
+    W = rng.standard_normal((27, 3, 2))
+    b = rng.standard_normal(2)
+    assert np.abs(U.conv(x, W, b, 2) - U.conv(x, W, b, 1)[::2, ::2, ::2]).max() < 1e-12
+    u = U.up2(x)
+    assert u.shape == (16, 12, 8, 3) and np.array_equal(u[1::2, ::2, 1::2], x)
+
+
+@pytest.mark.parametrize("stride", [1, 2])
+def test_adjoints(stride):
+    rng = np.random.Generator(np.random.Philox(3 + stride))
+    x = rng.standard_normal((8, 6, 4, 3))
+    W = rng.standard_normal((27, 3, 5))
+    y = U.conv(x, W, np.zeros(5), stride)
+    g = rng.standard_normal(y.shape)
+    lhs = float((y * g).sum())
+    assert abs(lhs - float((x * U.conv_adjoint(x.shape, g, W, stride)).sum())) < 1e-9 * abs(lhs)
+    assert abs(lhs - float((W * U.conv_wgrad(x, g, stride)).sum())) < 1e-9 * abs(lhs)
+    u = rng.standard_normal((4, 3, 2, 3))
+    v = rng.standard_normal((8, 6, 4, 3))
+    assert abs(float((U.up2(u) * v).sum()) - float((u * U.down2_sum(v)).sum())) < 1e-9
+
+
+def test_gradient_matches_central_differences():
+    rng = np.random.Generator(np.random.Philox(7))
+    p = U.init_params(3)
+    p += 0.01 * rng.standard_normal(p.size) * (p != 0)
+    # non-zero biases so every layer's bias gradient is exercised
+    off = 0
+    for ci, co, _, _ in U.SPEC:
+        off += 27 * ci * co
+        p[off:off + co] = 0.05 * rng.standard_normal(co)
+        off += co
+    x1 = rng.random((8, 16, 8))
+    target = x1 + 0.3 * rng.standard_normal(x1.shape)
+    loss, g = U.loss_and_grads(p, x1, target)
+    # probe parameters with a clear gradient in every layer
+    offs, o = [], 0
+    for ci, co, _, _ in U.SPEC:
+        offs.append((o, 27 * ci * co + co))
+        o += 27 * ci * co + co
+    idx = []
+    for lo, n in offs:
+        seg = np.abs(g[lo:lo + n])
+        idx.extend(lo + np.argsort(seg)[-2:])
+    eps = 1e-6
+    for i in idx:
+        e = np.zeros_like(p)
+        e[i] = eps
+        fd = (U.loss_and_grads(p + e, x1, target)[0] - U.loss_and_grads(p - e, x1, target)[0]) / (2 * eps)
+        assert abs(fd - g[i]) <= 1e-4 * abs(g[i]) + 1e-9, (i, fd, g[i])
+
+
+def test_bf16_rounding_is_round_half_even():
+    v = np.array([1.0, 1.0 + 2**-8, 1.0 + 3 * 2**-9, -2.5, 3.0e38])
+    r = U.to_bf16(v)
+    assert r[0] == 1.0 and r[1] == 1.0  # tie to even
+    assert r[2] == 1.0 + 2**-7 and r[3] == -2.5
