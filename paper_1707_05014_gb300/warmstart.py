@@ -1,0 +1,131 @@
+"""Warm-started reconstruction: plain DROP sweeps plus the learned initial image.
+
+Solve (every step runs in the library's kernels; this module only sequences
+the calls):
+  1. one DROP sweep from x = 0 gives x1 (Sec. 2.1, Fig. 1);
+  2. the network gives x0' = x1 + f(x1);
+  3. fallback: if the data residual |b - A x0'|^2 is larger than that of x1,
+     keep x1 (the plain solver is the judge);
+  4. further DROP sweeps from the chosen image.
+
+Training pairs are (x1, x_S): the first sweep and the plain solver's result
+after S sweeps, from seeded random head phantoms (synthetic.py). The network
+learns to jump from the first sweep towards the plain solver's answer.
+"""
+from __future__ import annotations
+
+import time
+from typing import Callable, Dict, List, Optional, Sequence, Tuple
+
+import numpy as np
+
+from . import pct as P
+from . import synthetic as S
+
+
+def training_grid() -> S.Grid:
+    """200 x 200 x 48 voxels of 1 x 1 x 2 mm (1.92M voxels)."""
+    return S.Grid(200, 200, 48, 1.0, 1.0, 2.0)
+
+
+def head_workload(grid: S.Grid, n: int, seed: int, n_blocks: int = 10) -> S.Workload:
+    """Seeded random head (outer semi-axes and inserts jittered by +-15 %)."""
+    return S.Workload(f"warm_head{seed}_{n}", grid, n, seed, 90, grid.radius,
+                      min(46.0, 0.5 * grid.nz * grid.hz - 2.0), n_blocks, 10, "head", 0.15)
+
+
+def plain_pair(wl: S.Workload, sweeps: int, device: int = 0, lam: float = 1.0):
+    """(x1, x_sweeps) of one plain-solver reconstruction, as CUDA tensors."""
+    import torch
+
+    rec = S.make_histories_device(wl, device=f"cuda:{device}")
+    with P.Context(wl.grid, n_blocks=wl.n_blocks, lam=lam, device=device) as ctx:
+        ctx.load(rec)
+        del rec
+        ctx.iterate(1)
+        x1 = ctx.get_rsp(device=True)
+        ctx.iterate(sweeps - 1)
+        xs = ctx.get_rsp(device=True)
+        torch.cuda.synchronize()
+    return x1, xs
+
+
+def make_training_pairs(grid: S.Grid, n_pairs: int, n_histories: int, sweeps: int, seed0: int = 1000,
+                        device: int = 0, log: Optional[Callable[[str], None]] = None):
+    pairs = []
+    t0 = time.time()
+    for k in range(n_pairs):
+        pairs.append(plain_pair(head_workload(grid, n_histories, seed0 + k), sweeps, device))
+        if log and (k + 1) % 25 == 0:
+            log(f"training pairs {k + 1}/{n_pairs} ({time.time() - t0:.0f} s)")
+    return pairs
+
+
+def train(net: P.Net, pairs: Sequence[Tuple], epochs: int, lr: float = 1e-3, seed: int = 0,
+          log: Optional[Callable[[str], None]] = None) -> List[float]:
+    """Adam on the L1 loss, one pair per step, shuffled every epoch; returns the
+    mean loss of each epoch."""
+    rng = np.random.Generator(np.random.Philox(seed))
+    hist = []
+    for ep in range(epochs):
+        order = rng.permutation(len(pairs))
+        losses = []
+        for i, k in enumerate(order):
+            x1, xs = pairs[k]
+            want = i % 8 == 0
+            l = net.train_step(x1, xs, lr=lr * (0.5 ** (ep // max(1, epochs // 3))), want_loss=want)
+            if want:
+                losses.append(l)
+        hist.append(float(np.mean(losses)))
+        if log:
+            log(f"epoch {ep + 1}/{epochs}: L1 {hist[-1]:.5f}")
+    return hist
+
+
+def solve_to_target(ctx: P.Context, x_true: np.ndarray, grid: S.Grid, target: float, max_sweeps: int,
+                    net: Optional[P.Net] = None) -> Dict:
+    """Sweeps until the mean RSP error (interior ROI) is <= target. Times only
+    the GPU work (sweeps, network, residual check) with CUDA events; the error
+    evaluation against the known phantom is outside the timed region."""
+    import torch
+
+    stream = torch.cuda.current_stream()
+    t_ms = 0.0
+    errs = []
+    used_net = False
+
+    def timed(fn):
+        nonlocal t_ms
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_ms += e0.elapsed_time(e1)
+        return out
+
+    def err():
+        return S.mean_rsp_error(ctx.get_rsp().astype(np.float64), x_true, grid)
+
+    sweeps = 0
+    timed(lambda: ctx.iterate(1))
+    sweeps = 1
+    if net is not None:
+        def warm():
+            x1 = ctx.get_rsp(device=True)
+            r1 = ctx.residual()
+            x0 = net.forward(x1)
+            ctx.set_x0(x0)
+            r0 = ctx.residual()
+            if r0 > r1:  # fallback: the plain solver's image is better
+                ctx.set_x0(x1)
+                return False
+            return True
+        used_net = timed(warm)
+    errs.append(err())
+    while errs[-1] > target and sweeps < max_sweeps:
+        timed(lambda: ctx.iterate(1))
+        sweeps += 1
+        errs.append(err())
+    return {"reached": errs[-1] <= target, "sweeps": sweeps, "ms": t_ms, "errors": errs, "net_used": used_net}
