@@ -377,6 +377,71 @@ def run_precision(args):
     return 0
 
 
+def run_warmstart(args):
+    """Learned warm start: 200 plain-solver reconstructions of seeded random
+    heads (200x200x48 grid, 1x1x2 mm) train the network; on held-out heads with
+    1e9 histories, time to <= 1 % mean RSP error of the warm-started solve
+    against the plain solver (CUDA events on the GPU work; the error check
+    against the known phantom is outside the timed region)."""
+    import numpy as np
+    import torch
+
+    from paper_1707_05014_gb300 import build as B
+    from paper_1707_05014_gb300 import pct as P
+    from paper_1707_05014_gb300 import synthetic as S
+    from paper_1707_05014_gb300 import warmstart as W
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    B.build()
+    g = W.training_grid()
+    log = lambda m: print(m, file=sys.stderr, flush=True)  # noqa: E731
+    t0 = time.time()
+    pairs = W.make_training_pairs(g, args.ws_pairs, args.ws_train_n, args.ws_train_sweeps, device=local, log=log,
+                                  blocks=args.ws_blocks)
+    t_data = time.time() - t0
+    net = P.Net(g.nz, g.ny, g.nx, seed=7, device=local)
+    t0 = time.time()
+    hist = W.train(net, pairs, epochs=args.ws_epochs, lr=1e-3, log=log)
+    torch.cuda.synchronize()
+    t_train = time.time() - t0
+    del pairs
+    torch.cuda.empty_cache()
+    results = []
+    for k in range(args.ws_tests):
+        wl = W.head_workload(g, args.ws_test_n, 5000 + k, n_blocks=args.ws_blocks)
+        x_true = S.voxelize(wl.phantom(), g, ss=2)
+        rec = S.make_histories_device(wl, device=f"cuda:{local}")
+        ctx = P.Context(g, n_blocks=wl.n_blocks, device=local)
+        ctx.load(rec)
+        del rec
+        torch.cuda.empty_cache()
+        zero = np.zeros(g.m, dtype=np.float32)
+        r = {"seed": 5000 + k}
+        for name, use in (("plain", None), ("warm", net)):
+            ctx.set_x0(zero)
+            r[name] = W.solve_to_target(ctx, x_true, g, args.ws_target, args.ws_max_sweeps, net=use)
+            log(f"test {k} {name}: {r[name]}")
+        ctx.close()
+        results.append(r)
+    plain_ms = [r["plain"]["ms"] for r in results if r["plain"]["reached"]]
+    warm_ms = [r["warm"]["ms"] for r in results if r["warm"]["reached"]]
+    line = {
+        "metric": "time-to-image at <=1% mean RSP error", "value": statistics.mean(warm_ms) / 1e3 if warm_ms else None,
+        "unit": "s", "n_gpus": 1, "higher_is_better": False, "data": "synthetic", "dtype": "f32",
+        "config": {"workload": f"warmstart_head200x200x48_{args.ws_test_n}", "grid": "200x200x48 @ 1x1x2 mm",
+                   "test_histories": args.ws_test_n, "n_blocks": args.ws_blocks, "target_error": args.ws_target,
+                   "training_pairs": args.ws_pairs, "training_histories": args.ws_train_n,
+                   "training_target": f"plain solver after {args.ws_train_sweeps} sweeps", "epochs": args.ws_epochs},
+        "plain_seconds": statistics.mean(plain_ms) / 1e3 if plain_ms else None,
+        "speedup": (statistics.mean(plain_ms) / statistics.mean(warm_ms)) if plain_ms and warm_ms else None,
+        "tests": results, "train_loss": hist, "training_data_s": t_data, "training_s": t_train,
+    }
+    print(json.dumps(line), flush=True)
+    net.close()
+    return 0
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -527,7 +592,16 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=1_000_000)
     ap.add_argument("--ref-sample", type=int, default=200_000)
     ap.add_argument("--no-sort", action="store_true", help="keep each block in load order (A/B of the ordering)")
-    ap.add_argument("--workload", default="head", choices=["head", "batched", "precision"])
+    ap.add_argument("--workload", default="head", choices=["head", "batched", "precision", "warmstart"])
+    ap.add_argument("--ws-pairs", type=int, default=200)
+    ap.add_argument("--ws-train-n", type=int, default=50_000_000)
+    ap.add_argument("--ws-train-sweeps", type=int, default=3)
+    ap.add_argument("--ws-blocks", type=int, default=50)
+    ap.add_argument("--ws-epochs", type=int, default=10)
+    ap.add_argument("--ws-tests", type=int, default=2)
+    ap.add_argument("--ws-test-n", type=int, default=1_000_000_000)
+    ap.add_argument("--ws-target", type=float, default=0.01)
+    ap.add_argument("--ws-max-sweeps", type=int, default=10)
     ap.add_argument("--precision-subset", type=int, default=1_000_000, help="oracle subset of the precision run")
     ap.add_argument("--n-recon", type=int, default=32, help="reconstructions of the batched workload")
     args = ap.parse_args()
@@ -537,6 +611,8 @@ def main():
         return run_batched(args)
     if args.workload == "precision":
         return run_precision(args)
+    if args.workload == "warmstart":
+        return run_warmstart(args)
     return run_ours(args)
 
 

@@ -154,9 +154,11 @@ PCT_API pct_status pct_mlp_rows(pct_ctx *ctx, int64_t first, int64_t count, int6
  * Asynchronous. (Sec. 2: a_i.x is the model WEPL of history i.) */
 PCT_API pct_status pct_project(pct_ctx *ctx, int64_t first, int64_t count, float *y);
 
-/* Data residual sum_i (b_i - a_i.x)^2 over all loaded histories with the
- * current x, accumulated in double; written to host *sum_sq. Synchronises. */
-PCT_API pct_status pct_residual(pct_ctx *ctx, double *sum_sq);
+/* Data residual sum_i (b_i - a_i.x)^2 with the current x over every
+ * stride-th stored history (stride 1: all of them; a larger stride gives an
+ * unbiased sample, since every block spans all angles), accumulated in
+ * double; written to host *sum_sq. Synchronises. */
+PCT_API pct_status pct_residual(pct_ctx *ctx, int64_t stride, double *sum_sq);
 
 /* Run counts s_j of DROP block `block` as float (exact integers), M values,
  * written to DEVICE memory `out`. */

@@ -392,12 +392,13 @@ pct_status pct_project(pct_ctx* c, int64_t first, int64_t count, float* y) {
   return PCT_OK;
 }
 
-pct_status pct_residual(pct_ctx* c, double* sum_sq) {
+pct_status pct_residual(pct_ctx* c, int64_t stride, double* sum_sq) {
   if (!c || !sum_sq) return fail(PCT_ERR_INVALID_ARG, "ctx or sum_sq is NULL");
+  if (stride < 1) return fail(PCT_ERR_INVALID_ARG, "stride must be >= 1");
   if (!c->loaded) return fail(PCT_ERR_STATE, "no histories loaded");
   PCT_CK(cudaSetDevice(c->device));
   PCT_CK(cudaMemsetAsync(c->acc, 0, sizeof(double), c->stream));
-  PCT_CK(pct::launch_residual(c->geo, c->rec, c->tab32, c->n, c->x, c->cfg.flags, c->acc, c->stream));
+  PCT_CK(pct::launch_residual(c->geo, c->rec, c->tab32, c->n, stride, c->x, c->cfg.flags, c->acc, c->stream));
   c->launches += 1;
   PCT_CK(cudaMemcpyAsync(sum_sq, c->acc, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   return sync_and_check(c);

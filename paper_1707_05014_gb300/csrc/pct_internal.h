@@ -59,9 +59,9 @@ cudaError_t launch_drop_apply(float* x, float* delta, const float* inv_s, int64_
 // y[p] = a_i.x for histories first+p (load order through `where`, if given).
 cudaError_t launch_project(const Geo& g, const Rec& r, const float4* tab, int64_t first, int64_t count,
                            const int64_t* where, const float* x, int flags, float* y, cudaStream_t s);
-// *acc += sum over stored histories [0, n) of (b_i - a_i.x)^2.
-cudaError_t launch_residual(const Geo& g, const Rec& r, const float4* tab, int64_t n, const float* x, int flags,
-                            double* acc, cudaStream_t s);
+// *acc += sum over stored histories i = 0, stride, ... < n of (b_i - a_i.x)^2.
+cudaError_t launch_residual(const Geo& g, const Rec& r, const float4* tab, int64_t n, int64_t stride, const float* x,
+                            int flags, double* acc, cudaStream_t s);
 cudaError_t launch_row_counts(const Geo& g, const Rec& r, const float4* tab, int64_t first, int64_t count,
                               const int64_t* where, int64_t* row_ptr, cudaStream_t s);
 cudaError_t launch_scan_rows(int64_t* row_ptr, int64_t count, cudaStream_t s);

@@ -95,14 +95,15 @@ __global__ void __launch_bounds__(128) project_kernel(Geo g, Rec r, const float4
   y[p] = project_history(g, tab, v, x, flags);
 }
 
-// sum_i (b_i - a_i.x)^2 over histories [0, n): per-CTA double reduction, one
-// double atomic per CTA.
+// sum over i = 0, stride, 2 stride, ... < n of (b_i - a_i.x)^2: per-CTA
+// double reduction, one double atomic per CTA.
 __global__ void __launch_bounds__(128) residual_kernel(Geo g, Rec r, const float4* __restrict__ tab_g, int64_t n,
-                                                       const float* __restrict__ x, int flags, double* acc) {
+                                                       int64_t stride, const float* __restrict__ x, int flags,
+                                                       double* acc) {
   extern __shared__ float4 tab[];
   __shared__ double part[4];
   load_table(tab_g, tab, g.K + 1);
-  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * stride;
   double rr = 0.0;
   if (p < n) {
     const RecV v = load_rec(r, p);
@@ -346,10 +347,11 @@ cudaError_t launch_project(const Geo& g, const Rec& r, const float4* tab, int64_
   return cudaGetLastError();
 }
 
-cudaError_t launch_residual(const Geo& g, const Rec& r, const float4* tab, int64_t n, const float* x, int flags,
-                            double* acc, cudaStream_t s) {
+cudaError_t launch_residual(const Geo& g, const Rec& r, const float4* tab, int64_t n, int64_t stride, const float* x,
+                            int flags, double* acc, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  residual_kernel<<<grid_for(n, 128), 128, (g.K + 1) * sizeof(float4), s>>>(g, r, tab, n, x, flags, acc);
+  const int64_t m = (n + stride - 1) / stride;
+  residual_kernel<<<grid_for(m, 128), 128, (g.K + 1) * sizeof(float4), s>>>(g, r, tab, n, stride, x, flags, acc);
   return cudaGetLastError();
 }
 

@@ -67,7 +67,7 @@ _SIGS = {
                      ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)],
     "pct_block_counts": [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p],
     "pct_project": [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p],
-    "pct_residual": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)],
+    "pct_residual": [ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)],
     "pct_set_x0": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int],
     "pct_iterate": [ctypes.c_void_p, ctypes.c_int32],
     "pct_get_rsp": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int],
@@ -267,11 +267,11 @@ class Context:
         _check(self._L.pct_project(self._h, int(first), int(count), ctypes.c_void_p(y.data_ptr())))
         return y
 
-    def residual(self) -> float:
-        """sum_i (b_i - a_i.x)^2 over all loaded histories (synchronising)."""
+    def residual(self, stride: int = 1) -> float:
+        """sum (b_i - a_i.x)^2 over every stride-th stored history (synchronising)."""
         out = ctypes.c_double(0.0)
         self._bind_stream()
-        _check(self._L.pct_residual(self._h, ctypes.byref(out)))
+        _check(self._L.pct_residual(self._h, int(stride), ctypes.byref(out)))
         return out.value
 
     def block_counts(self, block: int):
