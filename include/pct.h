@@ -73,6 +73,13 @@ typedef struct pct_config {
 #define PCT_FLAG_NO_KAHAN 2 /* plain instead of compensated a_i.x (precision study) */
 #define PCT_FLAG_PROFILE 4  /* record CUDA events around every fused launch
                                (read with pct_last_sweep_times)               */
+#define PCT_FLAG_CARP 16    /* pct_iterate runs CARP (Sec. 2.2, Fig. 2) instead of
+                               DROP: the n_blocks blocks are CARP strings; each
+                               string projects from the same x (its estimate
+                               x_s = x + lambda S_s^-1 sum_i a_i r_i), and x
+                               becomes the component average of the string
+                               estimates over the strings touching each voxel.
+                               Not accepted by pct_batch_create.             */
 #define PCT_FLAG_NO_SORT 8  /* keep each block in load order (default: each
                                block is stored ordered by gantry angle and
                                entry lateral position, which keeps the lanes

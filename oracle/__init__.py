@@ -13,6 +13,7 @@ Schulte et al. 2008 that Sec. 2 cites):
 * ``project``     -- a_i . x for a range of protons.
 * ``block_counts``-- s_j of one DROP block.
 * ``drop``        -- DROP sweeps, Sec. 2.1 / Fig. 1.
+* ``carp``        -- CARP sweeps, Sec. 2.2 / Fig. 2 (strings + component averaging).
 
 Pins (tests/test_oracle_*.py): table identities (translation / straight-line
 invariance, depth reversal), the constant-scattering special case against the
@@ -88,6 +89,8 @@ def lib():
         L.or_rows.restype = ctypes.c_int64
         L.or_project.argtypes = [gp, dp, rp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, dp, dp]
         L.or_block_counts.argtypes = [gp, dp, rp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp]
+        L.or_carp.argtypes = [gp, dp, rp, ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int, dp,
+                              dp]
         L.or_drop.argtypes = [gp, dp, rp, ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                               ctypes.c_int, ctypes.c_double, dp, dp]
     return _lib
@@ -233,4 +236,21 @@ def drop(g, rec, n_blocks: int, n_sweeps: int, lam: float = 1.0, x0: Optional[np
                        _ptr(resid, ctypes.c_double))
     if rc != 0:
         raise MemoryError("oracle drop: allocation failed")
+    return (x, resid[:n_sweeps]) if return_resid else x
+
+
+def carp(g, rec, n_strings: int, n_sweeps: int, lam: float = 1.0, x0: Optional[np.ndarray] = None,
+         mode: int = MODE_FP32, table=None, flags: int = 0, node_step: float = 0.0, return_resid: bool = False):
+    """CARP reconstruction (Sec. 2.2): strings from a common x0, component
+    averaging. Returns x (float64, M)."""
+    h = _RecHolder(rec)
+    tab = _tab(g, table, flags, node_step)
+    gg = _grid(g, node_step)
+    M = g.nx * g.ny * g.nz
+    x = np.zeros(M) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+    resid = np.zeros(max(n_sweeps, 1))
+    rc = lib().or_carp(ctypes.byref(gg), _ptr(tab, ctypes.c_double), ctypes.byref(h.s), h.n, n_strings, float(lam),
+                       n_sweeps, mode, _ptr(x, ctypes.c_double), _ptr(resid, ctypes.c_double))
+    if rc != 0:
+        raise MemoryError("oracle carp: allocation failed")
     return (x, resid[:n_sweeps]) if return_resid else x

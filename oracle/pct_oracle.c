@@ -561,3 +561,69 @@ int or_drop(const or_grid *g, const double *tab, const or_rec *r, int64_t n, int
   free(row.l);
   return 0;
 }
+
+/* ------------------------------------------------------------------ */
+/* CARP (Sec. 2.2, Fig. 2)                                             */
+/* ------------------------------------------------------------------ */
+
+/*
+ * Every string (block) s starts from the same x0. Reading: a string's own
+ * estimate is one simultaneous relaxed projection over its rows,
+ *   x_s = x0 + lambda S_s^-1 sum_{i in s} a_i (b_i - a_i.x0)/|a_i|^2,
+ * and the new x is the component average over the strings whose rows touch
+ * voxel j:  x_j = (1/|T_j|) sum_{s in T_j} x_s,j  (x_j unchanged if T_j is
+ * empty). Repeated n_sweeps times (the fixed stopping rule of Sec. 2.1-2.2).
+ */
+int or_carp(const or_grid *g, const double *tab, const or_rec *r, int64_t n, int n_strings, double lambda,
+            int n_sweeps, int mode, double *x, double *resid) {
+  or_geom o;
+  or_geometry(g, &o);
+  int64_t M = (int64_t)g->nx * g->ny * g->nz;
+  double *delta = (double *)calloc(M, sizeof(double));
+  double *cnt = (double *)calloc(M, sizeof(double));
+  double *sum = (double *)calloc(M, sizeof(double));
+  double *touch = (double *)calloc(M, sizeof(double));
+  or_row row = {0};
+  if (!delta || !cnt || !sum || !touch) return -1;
+  for (int sw = 0; sw < n_sweeps; ++sw) {
+    double rr = 0.0;
+    memset(sum, 0, M * sizeof(double));
+    memset(touch, 0, M * sizeof(double));
+    for (int b = 0; b < n_strings; ++b) {
+      int64_t lo = (int64_t)b * n / n_strings, hi = (int64_t)(b + 1) * n / n_strings;
+      memset(delta, 0, M * sizeof(double));
+      memset(cnt, 0, M * sizeof(double));
+      for (int64_t i = lo; i < hi; ++i) {
+        or_walk_row(g, &o, tab, r, i, mode, &row);
+        double ax = 0.0, nn = 0.0;
+        for (int64_t q = 0; q < row.n; ++q) {
+          ax += row.l[q] * x[row.j[q]];
+          nn += row.l[q] * row.l[q];
+        }
+        if (nn <= 0.0) continue;
+        double res = (double)r->wepl[i] - ax;
+        rr += res * res;
+        double ri = lambda * res / nn;
+        for (int64_t q = 0; q < row.n; ++q) {
+          delta[row.j[q]] += row.l[q] * ri;
+          cnt[row.j[q]] += 1.0;
+        }
+      }
+      for (int64_t j = 0; j < M; ++j)
+        if (cnt[j] > 0.0) {
+          sum[j] += x[j] + delta[j] / cnt[j]; /* x_s,j */
+          touch[j] += 1.0;
+        }
+    }
+    for (int64_t j = 0; j < M; ++j)
+      if (touch[j] > 0.0) x[j] = sum[j] / touch[j];
+    if (resid) resid[sw] = rr;
+  }
+  free(delta);
+  free(cnt);
+  free(sum);
+  free(touch);
+  free(row.j);
+  free(row.l);
+  return 0;
+}

@@ -178,6 +178,20 @@ pct_status pct_create(pct_ctx** out, const pct_grid* grid, const pct_config* cfg
       break;
     }
     c->launches += 1;
+    if (c->cfg.flags & PCT_FLAG_CARP) {
+      if (cudaMalloc((void**)&c->carp_sum, M * sizeof(float)) != cudaSuccess ||
+          cudaMalloc((void**)&c->carp_touch, M * sizeof(float)) != cudaSuccess) {
+        (void)cudaGetLastError();
+        st = fail(PCT_ERR_NO_MEMORY, "CARP buffers");
+        break;
+      }
+      if ((e = cudaMemsetAsync(c->carp_sum, 0, M * sizeof(float), c->stream)) != cudaSuccess ||
+          (e = cudaMemsetAsync(c->carp_touch, 0, M * sizeof(float), c->stream)) != cudaSuccess ||
+          (e = cudaStreamSynchronize(c->stream)) != cudaSuccess) {
+        st = fail(PCT_ERR_CUDA, "CARP buffers: %s", cudaGetErrorString(e));
+        break;
+      }
+    }
     if (c->cfg.flags & PCT_FLAG_PROFILE) {
       c->ev = new cudaEvent_t[3 * c->cfg.n_blocks]();
       for (int i = 0; i < 3 * c->cfg.n_blocks && e == cudaSuccess; ++i) e = cudaEventCreate(&c->ev[i]);
@@ -208,6 +222,8 @@ pct_status pct_destroy(pct_ctx* c) {
   cudaFree(c->cnt);
   cudaFree(c->first_bad);
   cudaFree(c->acc);
+  cudaFree(c->carp_sum);
+  cudaFree(c->carp_touch);
   if (c->ev) {
     for (int i = 0; i < 3 * c->cfg.n_blocks; ++i) cudaEventDestroy(c->ev[i]);
     delete[] c->ev;
@@ -434,6 +450,7 @@ static pct_status build_sweep_graph(pct_ctx* c) {
   cudaError_t err = cudaSuccess;
   const int B = c->cfg.n_blocks;
   const int clamp = (c->cfg.flags & PCT_FLAG_CLAMP) != 0;
+  const bool carp = (c->cfg.flags & PCT_FLAG_CARP) != 0;
   for (int b = 0; b < B && err == cudaSuccess; ++b) {
     const int64_t lo = block_lo(c, b), hi = block_lo(c, b + 1);
     if (c->ev) err = cudaEventRecordWithFlags(c->ev[3 * b], s, cudaEventRecordExternal);
@@ -441,10 +458,17 @@ static pct_status build_sweep_graph(pct_ctx* c) {
       err = pct::launch_drop_fused(c->geo, c->rec, c->tab32, lo, hi - lo, c->x, c->delta, c->cfg.lambda,
                                    c->cfg.flags, c->cfg.cta_threads, s);
     if (err == cudaSuccess && c->ev) err = cudaEventRecordWithFlags(c->ev[3 * b + 1], s, cudaEventRecordExternal);
-    if (err == cudaSuccess)
-      err = pct::launch_drop_apply(c->x, c->delta, c->inv_s + (size_t)b * c->M, c->M, clamp, c->cfg.clamp_min, s);
+    if (err == cudaSuccess) {
+      if (carp)  // every string projects from the same x: x changes only after the last string
+        err = pct::launch_carp_accum(c->x, c->delta, c->inv_s + (size_t)b * c->M, c->carp_sum, c->carp_touch, c->M,
+                                     s);
+      else
+        err = pct::launch_drop_apply(c->x, c->delta, c->inv_s + (size_t)b * c->M, c->M, clamp, c->cfg.clamp_min, s);
+    }
     if (err == cudaSuccess && c->ev) err = cudaEventRecordWithFlags(c->ev[3 * b + 2], s, cudaEventRecordExternal);
   }
+  if (carp && err == cudaSuccess)
+    err = pct::launch_carp_apply(c->x, c->carp_sum, c->carp_touch, c->M, clamp, c->cfg.clamp_min, s);
   cudaError_t e2 = cudaStreamEndCapture(s, &graph);
   if (err != cudaSuccess || e2 != cudaSuccess) {
     if (graph) cudaGraphDestroy(graph);
@@ -472,7 +496,7 @@ pct_status pct_iterate(pct_ctx* c, int32_t n_sweeps) {
     if (st != PCT_OK) return st;
   }
   for (int s = 0; s < n_sweeps; ++s) PCT_CK(cudaGraphLaunch(c->sweep, c->stream));
-  c->launches += (int64_t)n_sweeps * 2 * c->cfg.n_blocks;
+  c->launches += (int64_t)n_sweeps * (2 * c->cfg.n_blocks + ((c->cfg.flags & PCT_FLAG_CARP) ? 1 : 0));
   if (n_sweeps > 0) c->swept = true;
   return PCT_OK;
 }

@@ -30,6 +30,8 @@ struct pct_ctx {
   unsigned int* cnt = nullptr;
   unsigned long long* first_bad = nullptr;
   double* acc = nullptr;  // residual accumulator
+  float* carp_sum = nullptr;    // CARP: sum of string estimates per voxel
+  float* carp_touch = nullptr;  // CARP: number of strings touching each voxel
   cudaGraphExec_t sweep = nullptr;
   cudaEvent_t* ev = nullptr;  // 3 per block (profiling): fused start, fused end, apply end
   bool swept = false;

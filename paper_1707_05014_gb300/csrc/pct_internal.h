@@ -56,6 +56,12 @@ cudaError_t launch_drop_fused(const Geo& g, const Rec& r, const float4* tab, int
                               const float* x, float* delta, float lambda, int flags, int threads, cudaStream_t s);
 cudaError_t launch_drop_apply(float* x, float* delta, const float* inv_s, int64_t M, int clamp, float clamp_min,
                               cudaStream_t s);
+// CARP: sum += x + delta * inv_s and touch += 1 where inv_s > 0, delta = 0;
+// then x = sum / touch where touch > 0 and sum = touch = 0.
+cudaError_t launch_carp_accum(const float* x, float* delta, const float* inv_s, float* sum, float* touch, int64_t M,
+                              cudaStream_t s);
+cudaError_t launch_carp_apply(float* x, float* sum, float* touch, int64_t M, int clamp, float clamp_min,
+                              cudaStream_t s);
 // y[p] = a_i.x for histories first+p (load order through `where`, if given).
 cudaError_t launch_project(const Geo& g, const Rec& r, const float4* tab, int64_t first, int64_t count,
                            const int64_t* where, const float* x, int flags, float* y, cudaStream_t s);

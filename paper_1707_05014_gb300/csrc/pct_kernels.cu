@@ -123,6 +123,36 @@ __global__ void drop_apply_kernel(float* __restrict__ x, float* __restrict__ del
   apply_voxel(x, delta, inv_s, j, clamp, clamp_min);
 }
 
+// CARP (Sec. 2.2): string s's estimate x_s,j = x0_j + delta_j / s_j where the
+// string touches j; accumulate its sum and the number of touching strings.
+__global__ void carp_accum_kernel(const float* __restrict__ x, float* __restrict__ delta,
+                                  const float* __restrict__ inv_s, float* __restrict__ sum, float* __restrict__ touch,
+                                  int64_t M) {
+  int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= M) return;
+  const float w = inv_s[j];
+  if (w > 0.f) {
+    sum[j] += __fmaf_rn(delta[j], w, x[j]);
+    touch[j] += 1.f;
+  }
+  delta[j] = 0.f;
+}
+
+// Component average: x_j = sum_j / touch_j where any string touched j.
+__global__ void carp_apply_kernel(float* __restrict__ x, float* __restrict__ sum, float* __restrict__ touch,
+                                  int64_t M, int clamp, float clamp_min) {
+  int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= M) return;
+  const float t = touch[j];
+  if (t > 0.f) {
+    float xv = sum[j] / t;
+    if (clamp) xv = fmaxf(xv, clamp_min);
+    x[j] = xv;
+  }
+  sum[j] = 0.f;
+  touch[j] = 0.f;
+}
+
 __global__ void row_count_kernel(Geo g, Rec r, const float4* __restrict__ tab_g, int64_t first, int64_t count,
                                  const int64_t* __restrict__ where, int64_t* __restrict__ row_ptr) {
   extern __shared__ float4 tab[];
@@ -358,6 +388,18 @@ cudaError_t launch_residual(const Geo& g, const Rec& r, const float4* tab, int64
 cudaError_t launch_drop_apply(float* x, float* delta, const float* inv_s, int64_t M, int clamp, float clamp_min,
                               cudaStream_t s) {
   drop_apply_kernel<<<grid_for(M, 256), 256, 0, s>>>(x, delta, inv_s, M, clamp, clamp_min);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_carp_accum(const float* x, float* delta, const float* inv_s, float* sum, float* touch, int64_t M,
+                              cudaStream_t s) {
+  carp_accum_kernel<<<grid_for(M, 256), 256, 0, s>>>(x, delta, inv_s, sum, touch, M);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_carp_apply(float* x, float* sum, float* touch, int64_t M, int clamp, float clamp_min,
+                              cudaStream_t s) {
+  carp_apply_kernel<<<grid_for(M, 256), 256, 0, s>>>(x, sum, touch, M, clamp, clamp_min);
   return cudaGetLastError();
 }
 

@@ -27,6 +27,7 @@ FLAG_CLAMP = 1
 FLAG_NO_KAHAN = 2
 FLAG_PROFILE = 4
 FLAG_NO_SORT = 8
+FLAG_CARP = 16
 LOAD_HOST = 0
 LOAD_DEVICE_COPY = 1
 LOAD_DEVICE_BORROW = 2

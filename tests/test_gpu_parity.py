@@ -201,3 +201,17 @@ def test_projection_and_residual_match_oracle(pct, oracle, kahan):
     assert abs(rr - ro) <= 1e-4 * ro
     # a 1/7 sample estimates the same sum (stored order is grouped by angle)
     assert abs(7 * rr7 - ro) <= 0.1 * ro
+
+
+@pytest.mark.parametrize("strings,sweeps", [(10, 5), (3, 2)])
+def test_carp_parity(pct, oracle, strings, sweeps):
+    # CARP (Sec. 2.2): strings from a common x, component averaging
+    wl = S.tiny_workload(60_000, seed=71)
+    rec = S.make_histories(wl)
+    with pct.Context(wl.grid, n_blocks=strings, flags=pct.FLAG_CARP) as ctx:
+        ctx.load(rec)
+        ctx.iterate(sweeps)
+        x = ctx.get_rsp().astype(np.float64)
+    xo = oracle.carp(wl.grid, rec, strings, sweeps, mode=oracle.MODE_FP32)
+    err = np.abs(x - xo) / np.maximum(np.abs(xo), 1.0)
+    assert err.max() <= 1e-3, err.max()

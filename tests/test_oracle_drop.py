@@ -97,3 +97,42 @@ def test_noise_free_tiny_workload_converges(oracle):
     e10 = S.mean_rsp_error(oracle.drop(g, rec, 100, 10), xt, g)
     assert e10 < e5
     assert e10 < 0.01
+
+
+def test_carp_single_string_is_drop_single_block(oracle):
+    g, rec = _tiny()
+    a = oracle.drop(g, rec, n_blocks=1, n_sweeps=5, lam=0.7)
+    b = oracle.carp(g, rec, n_strings=1, n_sweeps=5, lam=0.7)
+    assert np.abs(a - b).max() <= 1e-12 * max(1.0, np.abs(a).max())
+
+
+def test_carp_is_the_component_average_of_string_projections(oracle):
+    # one sweep of CARP from x0 equals, voxel by voxel, the mean of the
+    # single-string DROP results over the strings that touch the voxel
+    g, rec = _tiny()
+    S_ = 4
+    x0 = np.linspace(0.1, 1.0, g.m)
+    got = oracle.carp(g, rec, n_strings=S_, n_sweeps=1, x0=x0)
+    rp, vox, _ = oracle.rows(g, rec)
+    num = np.zeros(g.m)
+    den = np.zeros(g.m)
+    for s in range(S_):
+        lo, hi = s * 200 // S_, (s + 1) * 200 // S_
+        xs = oracle.drop(g, S.subset(rec, slice(lo, hi)), n_blocks=1, n_sweeps=1, x0=x0)
+        touched = np.zeros(g.m, dtype=bool)
+        touched[vox[rp[lo]:rp[hi]]] = True
+        num[touched] += xs[touched]
+        den[touched] += 1
+    ref = np.where(den > 0, num / np.maximum(den, 1), x0)
+    assert np.abs(got - ref).max() <= 1e-12
+
+
+def test_carp_consistent_data_residual_decreases(oracle):
+    wl = S.tiny_workload(4000, seed=4)
+    g = wl.grid
+    rec = S.make_histories(wl)
+    xt = S.voxelize(wl.phantom(), g)
+    rec["wepl"] = oracle.project(g, rec, xt).astype(np.float32)
+    x, res = oracle.carp(g, rec, 5, 30, lam=1.0, return_resid=True)
+    assert np.all(np.diff(res[1:]) < 0)
+    assert res[-1] < 2e-2 * res[0]
