@@ -181,6 +181,19 @@ def run_reference(args):
     return 0
 
 
+def max_over_ranks(ms: float, device=None) -> float:
+    """The slowest rank's time (the job's time): all-reduce MAX when a process
+    group is up, else the local value."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(ms)
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_batched(args):
     """Batched variant: 32 independent reconstructions of uneven size advanced by
     one persistent launch per sweep (pct_batch_*), autotuned; the same sweep
@@ -496,10 +509,7 @@ def run_ours(args):
     ms = e0.elapsed_time(e1)
     clk = clocks.stop()
     launches = ctx.launches - launches0
-    t = torch.tensor([ms], device=f"cuda:{local}")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms = float(t.item())
+    ms = max_over_ranks(ms, device=f"cuda:{local}")
     value = wl.n * args.steps * world / (ms / 1e3)
 
     # roofline of the dominant kernel (fused MLP + projection): ALU-bound
