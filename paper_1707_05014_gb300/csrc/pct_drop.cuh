@@ -20,9 +20,9 @@ __device__ __forceinline__ float ld_weak(const float* p) {
 
 // MLP nodes -> walk -> compensated a_i.x and |a_i|^2 -> relaxed residual ->
 // scatter-add into delta. The walk keeps the row (voxel, chord) in
-// thread-local memory so the scatter replays it instead of walking again; a
-// row longer than kRowCap runs (none for valid records on the supported
-// grids) is walked a second time instead. flags & 2: plain instead of
+// thread-local memory; the dot product and the scatter replay it. A row
+// longer than kRowCap runs (none for valid records on the supported grids) is
+// walked again for each of them instead. flags & 2: plain instead of
 // compensated summation.
 //
 // kCoherent: x may change while the kernel runs (the batched persistent
@@ -35,26 +35,46 @@ __device__ __forceinline__ void drop_history(const Geo& g, const float4* __restr
                                              int flags) {
   auto xload = [&](int j) { return kCoherent ? ld_weak(x + j) : __ldg(x + j); };
   const RecV v = load_rec(r, i);
+  // The walk only records the row; the gather of x and the scatter run as two
+  // replays of the recorded row, outside the walk's divergent crossing loop.
   uint2 row[kRowCap];
   int nrow = 0;
+  walk_proton(g, tab, v, [&](int j, float l) {
+    if (nrow < kRowCap) row[nrow] = make_uint2((unsigned)j, __float_as_uint(l));
+    ++nrow;
+  });
   float y = 0.f, c = 0.f, nn = 0.f;
-  if (flags & 2) {
-    walk_proton(g, tab, v, [&](int j, float l) {
-      y = __fmaf_rn(l, xload(j), y);
-      nn = __fmaf_rn(l, l, nn);
-      if (nrow < kRowCap) row[nrow] = make_uint2((unsigned)j, __float_as_uint(l));
-      ++nrow;
-    });
+  if (nrow <= kRowCap) {
+    if (flags & 2) {
+      for (int q = 0; q < nrow; ++q) {
+        const uint2 e = row[q];
+        const float l = __uint_as_float(e.y);
+        y = __fmaf_rn(l, xload((int)e.x), y);
+        nn = __fmaf_rn(l, l, nn);
+      }
+    } else {
+      // Kahan-compensated sum of l * x_j: the true sum is y - c
+      for (int q = 0; q < nrow; ++q) {
+        const uint2 e = row[q];
+        const float l = __uint_as_float(e.y);
+        const float term = __fsub_rn(__fmul_rn(l, xload((int)e.x)), c);
+        const float t = __fadd_rn(y, term);
+        c = __fsub_rn(__fsub_rn(t, y), term);
+        y = t;
+        nn = __fmaf_rn(l, l, nn);
+      }
+    }
   } else {
-    // Kahan-compensated sum of l * x_j: the true sum is y - c
     walk_proton(g, tab, v, [&](int j, float l) {
-      const float term = __fsub_rn(__fmul_rn(l, xload(j)), c);
-      const float t = __fadd_rn(y, term);
-      c = __fsub_rn(__fsub_rn(t, y), term);
-      y = t;
+      if (flags & 2) {
+        y = __fmaf_rn(l, xload(j), y);
+      } else {
+        const float term = __fsub_rn(__fmul_rn(l, xload(j)), c);
+        const float t = __fadd_rn(y, term);
+        c = __fsub_rn(__fsub_rn(t, y), term);
+        y = t;
+      }
       nn = __fmaf_rn(l, l, nn);
-      if (nrow < kRowCap) row[nrow] = make_uint2((unsigned)j, __float_as_uint(l));
-      ++nrow;
     });
   }
   if (!(nn > 0.f)) return;

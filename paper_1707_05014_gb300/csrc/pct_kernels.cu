@@ -56,7 +56,7 @@ __global__ void counts_to_float_kernel(const unsigned int* __restrict__ cnt, flo
 }
 
 // One thread per proton (see drop_history).
-__global__ void __launch_bounds__(128) drop_fused_kernel(Geo g, Rec r, const float4* __restrict__ tab_g,
+__global__ void __launch_bounds__(128, 9) drop_fused_kernel(Geo g, Rec r, const float4* __restrict__ tab_g,
                                                           int64_t first, int64_t count, const float* __restrict__ x,
                                                           float* __restrict__ delta, float lambda, int flags) {
   extern __shared__ float4 tab[];
