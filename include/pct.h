@@ -67,6 +67,16 @@ typedef struct pct_config {
   float clamp_min;          /* lower clamp of x after each block (with flag)   */
   int32_t threads_per_proton; /* 1 (reserved for 2, 4, 8)                      */
   int32_t cta_threads;      /* threads per CTA of the fused kernel; 0 = 128    */
+  /* Total-variation superiorization (Sec. 4.2), off when tvs_beta0 <= 0:
+   * before every DROP block (with PCT_FLAG_CARP: before every CARP iteration)
+   * x is perturbed once along -grad TV_eps(x) / rms, with step
+   * tvs_beta0 * tvs_alpha^l (l counts every trial of the run), keeping the
+   * first of up to tvs_tries trials that does not raise TV_eps. TV_eps sums
+   * sqrt(dx^2 + dy^2 + dz^2 + eps^2) over forward differences. */
+  float tvs_beta0;          /* step in RSP units, e.g. 0.02                     */
+  float tvs_alpha;          /* step decay per trial; <= 0: 0.99                 */
+  float tvs_eps;            /* TV smoothing; <= 0: 1e-4                         */
+  int32_t tvs_tries;        /* trials per perturbation; <= 0: 4                 */
 } pct_config;
 
 #define PCT_FLAG_CLAMP 1    /* x_j = max(x_j, clamp_min) after each block      */
@@ -171,7 +181,8 @@ PCT_API pct_status pct_residual(pct_ctx *ctx, int64_t stride, double *sum_sq);
  * written to DEVICE memory `out`. */
 PCT_API pct_status pct_block_counts(pct_ctx *ctx, int32_t block, float *out);
 
-/* Set the initial image x0 (M floats; device memory if on_device, else host). */
+/* Set the initial image x0 (M floats; device memory if on_device, else host).
+ * Does not reset the TVS trial counter (pct_load_histories does). */
 PCT_API pct_status pct_set_x0(pct_ctx *ctx, const float *x0, int on_device);
 
 /* Run n_sweeps DROP iterations (Sec. 2.1, Fig. 1): for each block b in
@@ -234,7 +245,7 @@ typedef struct pct_batch_config {
 
 /* Group n loaded contexts (same device) for batched sweeps. cfg may be NULL
  * (defaults). The contexts must outlive the batch and must not be reloaded
- * while it exists. */
+ * while it exists. DROP contexts without TVS only. */
 PCT_API pct_status pct_batch_create(pct_batch **out, pct_ctx *const *ctxs, int32_t n, const pct_batch_config *cfg);
 PCT_API pct_status pct_batch_destroy(pct_batch *batch);
 
@@ -305,7 +316,8 @@ PCT_API pct_status pct_net_train_step(pct_net *net, const float *x1, const float
  * order. x: DEVICE array of nx*ny*nz floats, read and updated in place:
  * x_j += lambda/s_j * sum_i a_ij (b_i - a_i.x)/|a_i|^2. cfg: lambda,
  * node_step_mm, flags (PCT_FLAG_CLAMP, PCT_FLAG_NO_KAHAN) and clamp_min are
- * used; n_blocks, threads_per_proton and cta_threads are ignored. stream: a
+ * used; n_blocks, threads_per_proton, cta_threads and the TVS fields are
+ * ignored. stream: a
  * cudaStream_t (NULL = the legacy default stream).
  *
  * Scratch: a fixed 16.1 MiB device array inside the library (its update

@@ -14,6 +14,7 @@ Schulte et al. 2008 that Sec. 2 cites):
 * ``block_counts``-- s_j of one DROP block.
 * ``drop``        -- DROP sweeps, Sec. 2.1 / Fig. 1.
 * ``carp``        -- CARP sweeps, Sec. 2.2 / Fig. 2 (strings + component averaging).
+* ``solve_tvs``   -- DROP / CARP with total-variation superiorization, Sec. 4.2.
 
 Pins (tests/test_oracle_*.py): table identities (translation / straight-line
 invariance, depth reversal), the constant-scattering special case against the
@@ -89,6 +90,12 @@ def lib():
         L.or_rows.restype = ctypes.c_int64
         L.or_project.argtypes = [gp, dp, rp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, dp, dp]
         L.or_block_counts.argtypes = [gp, dp, rp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp]
+        L.or_tv_value.argtypes = [gp, dp, ctypes.c_double]
+        L.or_tv_value.restype = ctypes.c_double
+        L.or_tv_grad.argtypes = [gp, dp, ctypes.c_double, dp]
+        L.or_solve_tvs.argtypes = [gp, dp, rp, ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                   ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                   ctypes.c_int, dp]
         L.or_carp.argtypes = [gp, dp, rp, ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int, dp,
                               dp]
         L.or_drop.argtypes = [gp, dp, rp, ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int,
@@ -254,3 +261,36 @@ def carp(g, rec, n_strings: int, n_sweeps: int, lam: float = 1.0, x0: Optional[n
     if rc != 0:
         raise MemoryError("oracle carp: allocation failed")
     return (x, resid[:n_sweeps]) if return_resid else x
+
+
+def tv_value(g, x: np.ndarray, eps: float = 1e-4) -> float:
+    """TV_eps of an image (forward differences, Neumann far boundary)."""
+    xx = np.ascontiguousarray(x, dtype=np.float64)
+    gg = _grid(g)
+    return lib().or_tv_value(ctypes.byref(gg), _ptr(xx, ctypes.c_double), float(eps))
+
+
+def tv_grad(g, x: np.ndarray, eps: float = 1e-4) -> np.ndarray:
+    xx = np.ascontiguousarray(x, dtype=np.float64)
+    out = np.zeros_like(xx)
+    gg = _grid(g)
+    lib().or_tv_grad(ctypes.byref(gg), _ptr(xx, ctypes.c_double), float(eps), _ptr(out, ctypes.c_double))
+    return out
+
+
+def solve_tvs(g, rec, n_blocks: int, n_sweeps: int, lam: float = 1.0, carp: bool = False, beta0: float = 0.02,
+              alpha: float = 0.99, eps: float = 1e-4, tries: int = 4, x0: Optional[np.ndarray] = None,
+              mode: int = MODE_FP32, table=None, flags: int = 0, node_step: float = 0.0) -> np.ndarray:
+    """DROP (TVS before every block) or CARP (TVS before every iteration) with
+    total-variation superiorization (Sec. 4.2)."""
+    h = _RecHolder(rec)
+    tab = _tab(g, table, flags, node_step)
+    gg = _grid(g, node_step)
+    M = g.nx * g.ny * g.nz
+    x = np.zeros(M) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+    rc = lib().or_solve_tvs(ctypes.byref(gg), _ptr(tab, ctypes.c_double), ctypes.byref(h.s), h.n, n_blocks,
+                            float(lam), n_sweeps, mode, 1 if carp else 0, float(beta0), float(alpha), float(eps),
+                            int(tries), _ptr(x, ctypes.c_double))
+    if rc != 0:
+        raise MemoryError("oracle tvs: allocation failed")
+    return x

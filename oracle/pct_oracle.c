@@ -627,3 +627,123 @@ int or_carp(const or_grid *g, const double *tab, const or_rec *r, int64_t n, int
   free(row.l);
   return 0;
 }
+
+/* ------------------------------------------------------------------ */
+/* TVS: total-variation superiorization (Sec. 4.2)                     */
+/* ------------------------------------------------------------------ */
+
+/*
+ * Reading (the paper names TVS and where it acts, not its form; this follows
+ * Penfold et al. 2010): TV_eps(x) = sum over voxels of
+ * sqrt(dx^2 + dy^2 + dz^2 + eps^2), forward differences, a difference across
+ * the far boundary taken as 0. One perturbation per application: g = grad
+ * TV, v = -g / rms(g) (rms over voxels, so beta is in RSP units), then for up
+ * to `tries` trials x' = x + beta_l v with beta_l = beta0 alpha^l and l
+ * counting every trial of the run; the first x' with TV(x') <= TV(x) is taken.
+ */
+typedef struct {
+  double beta0, alpha, eps;
+  int tries;
+  long long ell; /* trials so far (state) */
+} or_tvs;
+
+static double or_tv_term(const or_grid *g, const double *x, int64_t i, int64_t j, int64_t k, double eps) {
+  int64_t nx = g->nx, ny = g->ny, nz = g->nz;
+  int64_t v = i + nx * (j + ny * k);
+  double dx = i + 1 < nx ? x[v + 1] - x[v] : 0.0;
+  double dy = j + 1 < ny ? x[v + nx] - x[v] : 0.0;
+  double dz = k + 1 < nz ? x[v + nx * ny] - x[v] : 0.0;
+  return sqrt(dx * dx + dy * dy + dz * dz + eps * eps);
+}
+
+double or_tv_value(const or_grid *g, const double *x, double eps) {
+  double s = 0.0;
+  for (int64_t k = 0; k < g->nz; ++k)
+    for (int64_t j = 0; j < g->ny; ++j)
+      for (int64_t i = 0; i < g->nx; ++i) s += or_tv_term(g, x, i, j, k, eps);
+  return s;
+}
+
+/* gradient of TV_eps, written as the sum of the derivatives of every term */
+int or_tv_grad(const or_grid *g, const double *x, double eps, double *grad) {
+  int64_t nx = g->nx, ny = g->ny, nz = g->nz, M = nx * ny * nz;
+  memset(grad, 0, M * sizeof(double));
+  for (int64_t k = 0; k < nz; ++k)
+    for (int64_t j = 0; j < ny; ++j)
+      for (int64_t i = 0; i < nx; ++i) {
+        int64_t v = i + nx * (j + ny * k);
+        double t = or_tv_term(g, x, i, j, k, eps);
+        if (i + 1 < nx) {
+          double d = x[v + 1] - x[v];
+          grad[v + 1] += d / t;
+          grad[v] -= d / t;
+        }
+        if (j + 1 < ny) {
+          double d = x[v + nx] - x[v];
+          grad[v + nx] += d / t;
+          grad[v] -= d / t;
+        }
+        if (k + 1 < nz) {
+          double d = x[v + nx * ny] - x[v];
+          grad[v + nx * ny] += d / t;
+          grad[v] -= d / t;
+        }
+      }
+  return 0;
+}
+
+/* One superiorization perturbation of x in place. Returns 1 if accepted. */
+int or_tvs_apply(const or_grid *g, or_tvs *p, double *x) {
+  int64_t M = (int64_t)g->nx * g->ny * g->nz;
+  double *gr = (double *)malloc(M * sizeof(double));
+  double *xp = (double *)malloc(M * sizeof(double));
+  int accepted = 0;
+  if (!gr || !xp) {
+    free(gr);
+    free(xp);
+    return -1;
+  }
+  or_tv_grad(g, x, p->eps, gr);
+  double n2 = 0.0;
+  for (int64_t v = 0; v < M; ++v) n2 += gr[v] * gr[v];
+  double rms = sqrt(n2 / M);
+  double tv0 = or_tv_value(g, x, p->eps);
+  for (int t = 0; t < p->tries && rms > 0.0; ++t) {
+    double beta = p->beta0 * pow(p->alpha, (double)p->ell);
+    p->ell++;
+    for (int64_t v = 0; v < M; ++v) xp[v] = x[v] - beta * gr[v] / rms;
+    if (or_tv_value(g, xp, p->eps) <= tv0) {
+      memcpy(x, xp, M * sizeof(double));
+      accepted = 1;
+      break;
+    }
+  }
+  free(gr);
+  free(xp);
+  return accepted;
+}
+
+/*
+ * DROP (or_drop) with a TVS perturbation of the image entering every block
+ * (Sec. 4.2: "applied to the initial solution that enters each block"), or
+ * CARP (carp != 0) with one perturbation at the start of every iteration.
+ */
+int or_solve_tvs(const or_grid *g, const double *tab, const or_rec *r, int64_t n, int n_blocks, double lambda,
+                 int n_sweeps, int mode, int carp, double beta0, double alpha, double eps, int tries, double *x) {
+  or_tvs p = {beta0, alpha, eps, tries, 0};
+  for (int sw = 0; sw < n_sweeps; ++sw) {
+    if (carp) {
+      if (or_tvs_apply(g, &p, x) < 0) return -1;
+      if (or_carp(g, tab, r, n, n_blocks, lambda, 1, mode, x, NULL) != 0) return -1;
+    } else {
+      for (int b = 0; b < n_blocks; ++b) {
+        int64_t lo = (int64_t)b * n / n_blocks, hi = (int64_t)(b + 1) * n / n_blocks;
+        or_rec rb = {r->t0 + lo, r->v0 + lo, r->st0 + lo, r->sv0 + lo, r->t2 + lo, r->v2 + lo,
+                     r->st2 + lo, r->sv2 + lo, r->wepl + lo, r->cphi + lo, r->sphi + lo};
+        if (or_tvs_apply(g, &p, x) < 0) return -1;
+        if (or_drop(g, tab, &rb, hi - lo, 1, lambda, 1, mode, 0, 0.0, x, NULL) != 0) return -1;
+      }
+    }
+  }
+  return 0;
+}

@@ -93,6 +93,13 @@ pct_status pct_create(pct_ctx** out, const pct_grid* grid, const pct_config* cfg
   c->grid = g;
   c->cfg = *cfg;
   if (c->cfg.cta_threads <= 0) c->cfg.cta_threads = 128;
+  if (c->cfg.tvs_alpha <= 0.f) c->cfg.tvs_alpha = 0.99f;
+  if (c->cfg.tvs_eps <= 0.f) c->cfg.tvs_eps = 1e-4f;
+  if (c->cfg.tvs_tries <= 0) c->cfg.tvs_tries = 4;
+  if (!(c->cfg.tvs_beta0 >= 0.f) || c->cfg.tvs_alpha > 1.f) {
+    delete c;
+    return fail(PCT_ERR_INVALID_ARG, "TVS needs beta0 >= 0 and 0 < alpha <= 1");
+  }
 
   // Geometry in FP64, then rounded once to FP32 for the kernels.
   const double X = g.nx * g.hx, Y = g.ny * g.hy, Z = g.nz * g.hz;
@@ -192,6 +199,22 @@ pct_status pct_create(pct_ctx** out, const pct_grid* grid, const pct_config* cfg
         break;
       }
     }
+    if (c->cfg.tvs_beta0 > 0.f) {
+      if (cudaMalloc((void**)&c->tv_g, M * sizeof(float)) != cudaSuccess ||
+          cudaMalloc((void**)&c->tv_xp, M * sizeof(float)) != cudaSuccess ||
+          cudaMalloc((void**)&c->tv_acc, 3 * sizeof(double)) != cudaSuccess ||
+          cudaMalloc((void**)&c->tv_state, sizeof(pct::TvState)) != cudaSuccess) {
+        (void)cudaGetLastError();
+        st = fail(PCT_ERR_NO_MEMORY, "TVS buffers");
+        break;
+      }
+      if ((e = cudaMemsetAsync(c->tv_acc, 0, 3 * sizeof(double), c->stream)) != cudaSuccess ||
+          (e = cudaMemsetAsync(c->tv_state, 0, sizeof(pct::TvState), c->stream)) != cudaSuccess ||
+          (e = cudaStreamSynchronize(c->stream)) != cudaSuccess) {
+        st = fail(PCT_ERR_CUDA, "TVS buffers: %s", cudaGetErrorString(e));
+        break;
+      }
+    }
     if (c->cfg.flags & PCT_FLAG_PROFILE) {
       c->ev = new cudaEvent_t[3 * c->cfg.n_blocks]();
       for (int i = 0; i < 3 * c->cfg.n_blocks && e == cudaSuccess; ++i) e = cudaEventCreate(&c->ev[i]);
@@ -224,6 +247,10 @@ pct_status pct_destroy(pct_ctx* c) {
   cudaFree(c->acc);
   cudaFree(c->carp_sum);
   cudaFree(c->carp_touch);
+  cudaFree(c->tv_g);
+  cudaFree(c->tv_xp);
+  cudaFree(c->tv_acc);
+  cudaFree(c->tv_state);
   if (c->ev) {
     for (int i = 0; i < 3 * c->cfg.n_blocks; ++i) cudaEventDestroy(c->ev[i]);
     delete[] c->ev;
@@ -369,6 +396,7 @@ pct_status pct_load_histories(pct_ctx* c, const pct_histories* h, int flags, int
   }
   PCT_CK(cudaMemsetAsync(c->x, 0, (size_t)c->M * sizeof(float), c->stream));
   PCT_CK(cudaMemsetAsync(c->delta, 0, (size_t)c->M * sizeof(float), c->stream));
+  if (c->tv_state) PCT_CK(cudaMemsetAsync(c->tv_state, 0, sizeof(pct::TvState), c->stream));
   pct_status st = sync_and_check(c);  // scratch is freed after the stream is idle
   if (st != PCT_OK) return st;
   c->loaded = true;
@@ -451,9 +479,16 @@ static pct_status build_sweep_graph(pct_ctx* c) {
   const int B = c->cfg.n_blocks;
   const int clamp = (c->cfg.flags & PCT_FLAG_CLAMP) != 0;
   const bool carp = (c->cfg.flags & PCT_FLAG_CARP) != 0;
+  const bool tvs = c->cfg.tvs_beta0 > 0.f;
+  const pct::TvsParams tp{c->cfg.tvs_beta0, c->cfg.tvs_alpha, c->cfg.tvs_eps, c->cfg.tvs_tries};
+  if (tvs && carp)
+    err = pct::launch_tvs(c->x, c->grid.nx, c->grid.ny, c->grid.nz, tp, c->tv_g, c->tv_xp, c->tv_acc, c->tv_state, s);
   for (int b = 0; b < B && err == cudaSuccess; ++b) {
     const int64_t lo = block_lo(c, b), hi = block_lo(c, b + 1);
-    if (c->ev) err = cudaEventRecordWithFlags(c->ev[3 * b], s, cudaEventRecordExternal);
+    if (tvs && !carp)
+      err = pct::launch_tvs(c->x, c->grid.nx, c->grid.ny, c->grid.nz, tp, c->tv_g, c->tv_xp, c->tv_acc, c->tv_state,
+                            s);
+    if (err == cudaSuccess && c->ev) err = cudaEventRecordWithFlags(c->ev[3 * b], s, cudaEventRecordExternal);
     if (err == cudaSuccess)
       err = pct::launch_drop_fused(c->geo, c->rec, c->tab32, lo, hi - lo, c->x, c->delta, c->cfg.lambda,
                                    c->cfg.flags, c->cfg.cta_threads, s);

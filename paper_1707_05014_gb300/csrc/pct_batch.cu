@@ -332,6 +332,7 @@ pct_status pct_batch_create(pct_batch** out, pct_ctx* const* ctxs, int32_t n, co
     if (!ctxs[r]->loaded) return bfail(PCT_ERR_STATE, "every context must have histories loaded");
     if (ctxs[r]->device != ctxs[0]->device) return bfail(PCT_ERR_INVALID_ARG, "contexts on different devices");
     if (ctxs[r]->cfg.flags & PCT_FLAG_CARP) return bfail(PCT_ERR_INVALID_ARG, "CARP contexts are not batched");
+    if (ctxs[r]->cfg.tvs_beta0 > 0.f) return bfail(PCT_ERR_INVALID_ARG, "TVS contexts are not batched");
   }
   pct_batch* b = new pct_batch();
   b->device = ctxs[0]->device;

@@ -32,6 +32,10 @@ struct pct_ctx {
   double* acc = nullptr;  // residual accumulator
   float* carp_sum = nullptr;    // CARP: sum of string estimates per voxel
   float* carp_touch = nullptr;  // CARP: number of strings touching each voxel
+  float* tv_g = nullptr;        // TVS: gradient
+  float* tv_xp = nullptr;       // TVS: trial image
+  double* tv_acc = nullptr;     // TVS: |g|^2, TV(x), TV(x')
+  pct::TvState* tv_state = nullptr;
   cudaGraphExec_t sweep = nullptr;
   cudaEvent_t* ev = nullptr;  // 3 per block (profiling): fused start, fused end, apply end
   bool swept = false;

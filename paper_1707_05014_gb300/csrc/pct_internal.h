@@ -36,6 +36,17 @@ struct Rec {
   const float *t0, *v0, *st0, *sv0, *t2, *v2, *st2, *sv2, *wepl, *cphi, *sphi;
 };
 
+// Total-variation superiorization parameters and device state.
+struct TvsParams {
+  float beta0, alpha, eps;
+  int tries;
+};
+struct TvState {
+  long long ell;  // trials so far
+  int accepted;   // a trial of the current application was taken
+  int pad;
+};
+
 // Launchers (pct_kernels.cu / pct_table.cu). All enqueue on `s` and return
 // the launch error (cudaSuccess when queued).
 cudaError_t launch_mlp_table(double R, double du, int K, double* tab64, float4* tab32, cudaStream_t s);
@@ -62,6 +73,11 @@ cudaError_t launch_carp_accum(const float* x, float* delta, const float* inv_s, 
                               cudaStream_t s);
 cudaError_t launch_carp_apply(float* x, float* sum, float* touch, int64_t M, int clamp, float clamp_min,
                               cudaStream_t s);
+// One TVS perturbation of x (gradient, up to p.tries trials, commit); g, xp:
+// M floats of scratch; acc: 3 doubles and st: the state, both zero on entry
+// and left zero (st->ell keeps counting).
+cudaError_t launch_tvs(float* x, int nx, int ny, int nz, const TvsParams& p, float* g, float* xp, double* acc,
+                       TvState* st, cudaStream_t s);
 // y[p] = a_i.x for histories first+p (load order through `where`, if given).
 cudaError_t launch_project(const Geo& g, const Rec& r, const float4* tab, int64_t first, int64_t count,
                            const int64_t* where, const float* x, int flags, float* y, cudaStream_t s);

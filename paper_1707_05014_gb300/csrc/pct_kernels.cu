@@ -153,6 +153,116 @@ __global__ void carp_apply_kernel(float* __restrict__ x, float* __restrict__ sum
   touch[j] = 0.f;
 }
 
+// ---- total-variation superiorization (TVS, Sec. 4.2) ----------------------
+// TV_eps(x) = sum_v sqrt(dx^2 + dy^2 + dz^2 + eps^2), forward differences, 0
+// across the far boundary. All decisions stay on the device (graph-safe).
+
+__device__ __forceinline__ float tv_term(const float* __restrict__ x, int i, int j, int k, int nx, int ny, int nz,
+                                         float eps) {
+  const int64_t v = i + (int64_t)nx * (j + (int64_t)ny * k);
+  const float xv = x[v];
+  const float dx = i + 1 < nx ? x[v + 1] - xv : 0.f;
+  const float dy = j + 1 < ny ? x[v + nx] - xv : 0.f;
+  const float dz = k + 1 < nz ? x[v + (int64_t)nx * ny] - xv : 0.f;
+  return sqrtf(dx * dx + dy * dy + dz * dz + eps * eps);
+}
+
+__device__ __forceinline__ void block_add2(double a, double b, double* out) {
+  __shared__ double sa[8], sb[8];
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, o);
+    b += __shfl_down_sync(0xffffffffu, b, o);
+  }
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    sa[w] = a;
+    sb[w] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double ta = 0.0, tb = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
+      ta += sa[q];
+      tb += sb[q];
+    }
+    atomicAdd(out, ta);  // out[0] accumulates a, out[1] b
+    atomicAdd(out + 1, tb);
+  }
+}
+
+// g = grad TV_eps(x); acc[0] += |g|^2, acc[1] += TV(x)
+__global__ void __launch_bounds__(256) tv_grad_kernel(const float* __restrict__ x, int nx, int ny, int nz, float eps,
+                                                      float* __restrict__ g, double* acc) {
+  const int64_t M = (int64_t)nx * ny * nz;
+  const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double gg = 0.0, tv = 0.0;
+  if (v < M) {
+    const int i = (int)(v % nx), j = (int)((v / nx) % ny), k = (int)(v / ((int64_t)nx * ny));
+    const float xv = x[v];
+    const float t = tv_term(x, i, j, k, nx, ny, nz, eps);
+    float gr = 0.f;
+    if (i + 1 < nx) gr -= (x[v + 1] - xv) / t;
+    if (j + 1 < ny) gr -= (x[v + nx] - xv) / t;
+    if (k + 1 < nz) gr -= (x[v + (int64_t)nx * ny] - xv) / t;
+    if (i > 0) gr += (xv - x[v - 1]) / tv_term(x, i - 1, j, k, nx, ny, nz, eps);
+    if (j > 0) gr += (xv - x[v - nx]) / tv_term(x, i, j - 1, k, nx, ny, nz, eps);
+    if (k > 0) gr += (xv - x[v - (int64_t)nx * ny]) / tv_term(x, i, j, k - 1, nx, ny, nz, eps);
+    g[v] = gr;
+    gg = (double)gr * gr;
+    tv = t;
+  }
+  block_add2(gg, tv, acc);
+}
+
+// trial x' = x - beta_l g / rms(g), beta_l = beta0 alpha^l (skipped once accepted)
+__global__ void tv_trial_kernel(const float* __restrict__ x, const float* __restrict__ g, float* __restrict__ xp,
+                                int64_t M, const double* __restrict__ acc, const TvState* __restrict__ st,
+                                float beta0, float alpha) {
+  if (st->accepted) return;
+  const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= M) return;
+  const double rms = sqrt(acc[0] / (double)M);
+  if (!(rms > 0.0)) return;
+  const float beta = (float)((double)beta0 * pow((double)alpha, (double)st->ell));
+  xp[v] = x[v] - beta * (float)((double)g[v] / rms);
+}
+
+// acc[2] += TV(x') (skipped once accepted)
+__global__ void __launch_bounds__(256) tv_value_kernel(const float* __restrict__ xp, int nx, int ny, int nz, float eps,
+                                                       double* acc, const TvState* __restrict__ st) {
+  if (st->accepted) return;
+  const int64_t M = (int64_t)nx * ny * nz;
+  const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double tv = 0.0;
+  if (v < M) {
+    const int i = (int)(v % nx), j = (int)((v / nx) % ny), k = (int)(v / ((int64_t)nx * ny));
+    tv = tv_term(xp, i, j, k, nx, ny, nz, eps);
+  }
+  for (int o = 16; o > 0; o >>= 1) tv += __shfl_down_sync(0xffffffffu, tv, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(acc + 2, tv);
+}
+
+// one thread: count the trial, accept if TV(x') <= TV(x)
+__global__ void tv_decide_kernel(double* acc, TvState* st) {
+  if (!st->accepted && acc[0] > 0.0) {
+    st->ell += 1;
+    if (acc[2] <= acc[1]) st->accepted = 1;
+  }
+  acc[2] = 0.0;
+}
+
+// x = x' if a trial was accepted; reset the per-application state
+__global__ void tv_commit_kernel(float* __restrict__ x, const float* __restrict__ xp, int64_t M, TvState* st,
+                                 double* acc) {
+  const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v < M && st->accepted) x[v] = xp[v];
+}
+
+__global__ void tv_reset_kernel(double* acc, TvState* st) {
+  acc[0] = acc[1] = acc[2] = 0.0;
+  st->accepted = 0;
+}
+
 __global__ void row_count_kernel(Geo g, Rec r, const float4* __restrict__ tab_g, int64_t first, int64_t count,
                                  const int64_t* __restrict__ where, int64_t* __restrict__ row_ptr) {
   extern __shared__ float4 tab[];
@@ -400,6 +510,21 @@ cudaError_t launch_carp_accum(const float* x, float* delta, const float* inv_s, 
 cudaError_t launch_carp_apply(float* x, float* sum, float* touch, int64_t M, int clamp, float clamp_min,
                               cudaStream_t s) {
   carp_apply_kernel<<<grid_for(M, 256), 256, 0, s>>>(x, sum, touch, M, clamp, clamp_min);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tvs(float* x, int nx, int ny, int nz, const TvsParams& p, float* g, float* xp, double* acc,
+                       TvState* st, cudaStream_t s) {
+  const int64_t M = (int64_t)nx * ny * nz;
+  const unsigned b = grid_for(M, 256);
+  tv_grad_kernel<<<b, 256, 0, s>>>(x, nx, ny, nz, p.eps, g, acc);
+  for (int t = 0; t < p.tries; ++t) {
+    tv_trial_kernel<<<b, 256, 0, s>>>(x, g, xp, M, acc, st, p.beta0, p.alpha);
+    tv_value_kernel<<<b, 256, 0, s>>>(xp, nx, ny, nz, p.eps, acc, st);
+    tv_decide_kernel<<<1, 1, 0, s>>>(acc, st);
+  }
+  tv_commit_kernel<<<b, 256, 0, s>>>(x, xp, M, st, acc);
+  tv_reset_kernel<<<1, 1, 0, s>>>(acc, st);
   return cudaGetLastError();
 }
 

@@ -215,3 +215,23 @@ def test_carp_parity(pct, oracle, strings, sweeps):
     xo = oracle.carp(wl.grid, rec, strings, sweeps, mode=oracle.MODE_FP32)
     err = np.abs(x - xo) / np.maximum(np.abs(xo), 1.0)
     assert err.max() <= 1e-3, err.max()
+
+
+@pytest.mark.parametrize("carp", [False, True])
+def test_tvs_parity(pct, oracle, carp):
+    # total-variation superiorization (Sec. 4.2) before every DROP block or
+    # every CARP iteration, against the oracle's reading
+    wl = S.tiny_workload(30_000, seed=95)
+    rec = S.make_histories(wl)
+    flags = pct.FLAG_CARP if carp else 0
+    with pct.Context(wl.grid, n_blocks=4, flags=flags, tvs_beta0=0.05, tvs_alpha=0.99, tvs_eps=1e-4,
+                     tvs_tries=4) as ctx:
+        ctx.load(rec)
+        ctx.iterate(3)
+        x = ctx.get_rsp().astype(np.float64)
+    xo = oracle.solve_tvs(wl.grid, rec, 4, 3, carp=carp, beta0=0.05, alpha=0.99, eps=1e-4, tries=4,
+                          mode=oracle.MODE_FP32)
+    err = np.abs(x - xo) / np.maximum(np.abs(xo), 1.0)
+    assert err.max() <= 1e-3, err.max()
+    plain = oracle.carp(wl.grid, rec, 4, 3) if carp else oracle.drop(wl.grid, rec, 4, 3)
+    assert oracle.tv_value(wl.grid, x) < oracle.tv_value(wl.grid, plain)
