@@ -455,6 +455,46 @@ def run_warmstart(args):
     return 0
 
 
+def run_table2(args):
+    """Table 2 style accuracy study on the synthetic insert phantom: DROP and
+    CARP (both with TVS, as in Sec. 4.2), ROI mean / std / %error per insert."""
+    import numpy as np
+    import torch
+
+    from paper_1707_05014_gb300 import build as B
+    from paper_1707_05014_gb300 import pct as P
+    from paper_1707_05014_gb300 import synthetic as S
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    B.build()
+    g = S.Grid(160, 160, 32, 1.25, 1.25, 1.25)
+    wl = S.Workload(f"catphan_{args.t2_n}", g, args.t2_n, 404, 0, g.radius, 18.0, args.t2_blocks, args.t2_sweeps,
+                    "catphan")
+    rec = S.make_histories_device(wl, device=f"cuda:{local}")
+    out = {}
+    for name, flags in (("DROP", 0), ("CARP", P.FLAG_CARP)):
+        with P.Context(g, n_blocks=wl.n_blocks, flags=flags, tvs_beta0=args.t2_tvs, carp_strings=args.t2_strings,
+                       device=local) as ctx:
+            ctx.load(rec)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            st = torch.cuda.current_stream()
+            e0.record(st)
+            ctx.iterate(wl.n_sweeps)
+            e1.record(st)
+            x = ctx.get_rsp().astype(np.float64)
+            out[name] = {"rows": S.roi_stats(x, g), "seconds": e0.elapsed_time(e1) / 1e3}
+    line = {"metric": "ROI RSP accuracy (Table 2 format)", "unit": "RSP", "data": "synthetic",
+            "config": {"workload": wl.name, "grid": "160x160x32 @ 1.25 mm", "histories": wl.n, "blocks": wl.n_blocks,
+                       "carp_strings": args.t2_strings,
+                       "iterations": wl.n_sweeps, "tvs_beta0": args.t2_tvs,
+                       "phantom": "150 mm RSP-1.0 cylinder, seven 12 mm inserts at Table 2's true RSPs"},
+            "results": out}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -602,7 +642,12 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=1_000_000)
     ap.add_argument("--ref-sample", type=int, default=200_000)
     ap.add_argument("--no-sort", action="store_true", help="keep each block in load order (A/B of the ordering)")
-    ap.add_argument("--workload", default="head", choices=["head", "batched", "precision", "warmstart"])
+    ap.add_argument("--workload", default="head", choices=["head", "batched", "precision", "warmstart", "table2"])
+    ap.add_argument("--t2-n", type=int, default=200_000_000)
+    ap.add_argument("--t2-blocks", type=int, default=600, help="DROP blocks; CARP: blocks split over the strings")
+    ap.add_argument("--t2-strings", type=int, default=60)
+    ap.add_argument("--t2-sweeps", type=int, default=10)
+    ap.add_argument("--t2-tvs", type=float, default=0.02)
     ap.add_argument("--ws-pairs", type=int, default=200)
     ap.add_argument("--ws-train-n", type=int, default=50_000_000)
     ap.add_argument("--ws-train-sweeps", type=int, default=3)
@@ -623,6 +668,8 @@ def main():
         return run_precision(args)
     if args.workload == "warmstart":
         return run_warmstart(args)
+    if args.workload == "table2":
+        return run_table2(args)
     return run_ours(args)
 
 

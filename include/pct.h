@@ -77,6 +77,9 @@ typedef struct pct_config {
   float tvs_alpha;          /* step decay per trial; <= 0: 0.99                 */
   float tvs_eps;            /* TV smoothing; <= 0: 1e-4                         */
   int32_t tvs_tries;        /* trials per perturbation; <= 0: 4                 */
+  int32_t carp_strings;     /* PCT_FLAG_CARP: number of strings S; string s holds
+                               blocks [s B/S, (s+1) B/S); <= 0 or > B: one block
+                               per string                                      */
 } pct_config;
 
 #define PCT_FLAG_CLAMP 1    /* x_j = max(x_j, clamp_min) after each block      */
@@ -84,11 +87,12 @@ typedef struct pct_config {
 #define PCT_FLAG_PROFILE 4  /* record CUDA events around every fused launch
                                (read with pct_last_sweep_times)               */
 #define PCT_FLAG_CARP 16    /* pct_iterate runs CARP (Sec. 2.2, Fig. 2) instead of
-                               DROP: the n_blocks blocks are CARP strings; each
-                               string projects from the same x (its estimate
-                               x_s = x + lambda S_s^-1 sum_i a_i r_i), and x
-                               becomes the component average of the string
-                               estimates over the strings touching each voxel.
+                               DROP: carp_strings strings of consecutive blocks;
+                               every string sweeps its blocks with the DROP
+                               block update on a copy of the same starting x
+                               (the blocked form of a string's row sweep), and
+                               x becomes the component average of the string
+                               results over the strings touching each voxel.
                                Not accepted by pct_batch_create.             */
 #define PCT_FLAG_NO_SORT 8  /* keep each block in load order (default: each
                                block is stored ordered by gantry angle and

@@ -96,8 +96,8 @@ def lib():
         L.or_solve_tvs.argtypes = [gp, dp, rp, ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                    ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                    ctypes.c_int, dp]
-        L.or_carp.argtypes = [gp, dp, rp, ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int, dp,
-                              dp]
+        L.or_carp.argtypes = [gp, dp, rp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                              ctypes.c_int, dp, dp]
         L.or_drop.argtypes = [gp, dp, rp, ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                               ctypes.c_int, ctypes.c_double, dp, dp]
     return _lib
@@ -247,17 +247,20 @@ def drop(g, rec, n_blocks: int, n_sweeps: int, lam: float = 1.0, x0: Optional[np
 
 
 def carp(g, rec, n_strings: int, n_sweeps: int, lam: float = 1.0, x0: Optional[np.ndarray] = None,
-         mode: int = MODE_FP32, table=None, flags: int = 0, node_step: float = 0.0, return_resid: bool = False):
-    """CARP reconstruction (Sec. 2.2): strings from a common x0, component
-    averaging. Returns x (float64, M)."""
+         mode: int = MODE_FP32, table=None, flags: int = 0, node_step: float = 0.0, return_resid: bool = False,
+         n_blocks: Optional[int] = None):
+    """CARP reconstruction (Sec. 2.2): strings of consecutive DROP blocks
+    (n_blocks, default one block per string) swept from a common x0, then
+    component averaging. Returns x (float64, M)."""
+    n_blocks = n_strings if n_blocks is None else n_blocks
     h = _RecHolder(rec)
     tab = _tab(g, table, flags, node_step)
     gg = _grid(g, node_step)
     M = g.nx * g.ny * g.nz
     x = np.zeros(M) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
     resid = np.zeros(max(n_sweeps, 1))
-    rc = lib().or_carp(ctypes.byref(gg), _ptr(tab, ctypes.c_double), ctypes.byref(h.s), h.n, n_strings, float(lam),
-                       n_sweeps, mode, _ptr(x, ctypes.c_double), _ptr(resid, ctypes.c_double))
+    rc = lib().or_carp(ctypes.byref(gg), _ptr(tab, ctypes.c_double), ctypes.byref(h.s), h.n, n_blocks, n_strings,
+                       float(lam), n_sweeps, mode, _ptr(x, ctypes.c_double), _ptr(resid, ctypes.c_double))
     if rc != 0:
         raise MemoryError("oracle carp: allocation failed")
     return (x, resid[:n_sweeps]) if return_resid else x
@@ -278,18 +281,19 @@ def tv_grad(g, x: np.ndarray, eps: float = 1e-4) -> np.ndarray:
     return out
 
 
-def solve_tvs(g, rec, n_blocks: int, n_sweeps: int, lam: float = 1.0, carp: bool = False, beta0: float = 0.02,
+def solve_tvs(g, rec, n_blocks: int, n_sweeps: int, lam: float = 1.0, carp: int = 0, beta0: float = 0.02,
               alpha: float = 0.99, eps: float = 1e-4, tries: int = 4, x0: Optional[np.ndarray] = None,
               mode: int = MODE_FP32, table=None, flags: int = 0, node_step: float = 0.0) -> np.ndarray:
-    """DROP (TVS before every block) or CARP (TVS before every iteration) with
-    total-variation superiorization (Sec. 4.2)."""
+    """DROP (TVS before every block) or, with carp = number of strings > 0,
+    CARP (TVS before every iteration), with total-variation superiorization
+    (Sec. 4.2)."""
     h = _RecHolder(rec)
     tab = _tab(g, table, flags, node_step)
     gg = _grid(g, node_step)
     M = g.nx * g.ny * g.nz
     x = np.zeros(M) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
     rc = lib().or_solve_tvs(ctypes.byref(gg), _ptr(tab, ctypes.c_double), ctypes.byref(h.s), h.n, n_blocks,
-                            float(lam), n_sweeps, mode, 1 if carp else 0, float(beta0), float(alpha), float(eps),
+                            float(lam), n_sweeps, mode, int(carp), float(beta0), float(alpha), float(eps),
                             int(tries), _ptr(x, ctypes.c_double))
     if rc != 0:
         raise MemoryError("oracle tvs: allocation failed")

@@ -567,51 +567,66 @@ int or_drop(const or_grid *g, const double *tab, const or_rec *r, int64_t n, int
 /* ------------------------------------------------------------------ */
 
 /*
- * Every string (block) s starts from the same x0. Reading: a string's own
- * estimate is one simultaneous relaxed projection over its rows,
- *   x_s = x0 + lambda S_s^-1 sum_{i in s} a_i (b_i - a_i.x0)/|a_i|^2,
- * and the new x is the component average over the strings whose rows touch
- * voxel j:  x_j = (1/|T_j|) sum_{s in T_j} x_s,j  (x_j unchanged if T_j is
- * empty). Repeated n_sweeps times (the fixed stopping rule of Sec. 2.1-2.2).
+ * CARP with the strings formed by consecutive DROP blocks: string s holds
+ * blocks [s B/S, (s+1) B/S) (block b: histories [b N/B, (b+1) N/B)). Every
+ * string starts from the same x0 and sweeps its own rows sequentially, block
+ * by block, with the DROP block update (the blocked form of the Kaczmarz
+ * sweep of Gordon 2005): x_s = DROP(x0, blocks of s). The new x is the
+ * component average over the strings whose rows touch voxel j,
+ * x_j = (1/|T_j|) sum_{s in T_j} x_s,j (x_j unchanged if T_j is empty).
+ * Repeated n_sweeps times. With one block per string each x_s is a single
+ * simultaneous projection from x0.
  */
-int or_carp(const or_grid *g, const double *tab, const or_rec *r, int64_t n, int n_strings, double lambda,
-            int n_sweeps, int mode, double *x, double *resid) {
+int or_carp(const or_grid *g, const double *tab, const or_rec *r, int64_t n, int n_blocks, int n_strings,
+            double lambda, int n_sweeps, int mode, double *x, double *resid) {
   or_geom o;
   or_geometry(g, &o);
   int64_t M = (int64_t)g->nx * g->ny * g->nz;
+  double *xs = (double *)calloc(M, sizeof(double));
   double *delta = (double *)calloc(M, sizeof(double));
   double *cnt = (double *)calloc(M, sizeof(double));
   double *sum = (double *)calloc(M, sizeof(double));
   double *touch = (double *)calloc(M, sizeof(double));
+  char *hit = (char *)calloc(M, 1);
   or_row row = {0};
-  if (!delta || !cnt || !sum || !touch) return -1;
+  if (!xs || !delta || !cnt || !sum || !touch || !hit) return -1;
   for (int sw = 0; sw < n_sweeps; ++sw) {
     double rr = 0.0;
     memset(sum, 0, M * sizeof(double));
     memset(touch, 0, M * sizeof(double));
-    for (int b = 0; b < n_strings; ++b) {
-      int64_t lo = (int64_t)b * n / n_strings, hi = (int64_t)(b + 1) * n / n_strings;
-      memset(delta, 0, M * sizeof(double));
-      memset(cnt, 0, M * sizeof(double));
-      for (int64_t i = lo; i < hi; ++i) {
-        or_walk_row(g, &o, tab, r, i, mode, &row);
-        double ax = 0.0, nn = 0.0;
-        for (int64_t q = 0; q < row.n; ++q) {
-          ax += row.l[q] * x[row.j[q]];
-          nn += row.l[q] * row.l[q];
+    for (int st = 0; st < n_strings; ++st) {
+      memcpy(xs, x, M * sizeof(double));
+      memset(hit, 0, M);
+      int b0 = (int)((int64_t)st * n_blocks / n_strings), b1 = (int)((int64_t)(st + 1) * n_blocks / n_strings);
+      for (int b = b0; b < b1; ++b) {
+        int64_t lo = (int64_t)b * n / n_blocks, hi = (int64_t)(b + 1) * n / n_blocks;
+        memset(delta, 0, M * sizeof(double));
+        memset(cnt, 0, M * sizeof(double));
+        for (int64_t i = lo; i < hi; ++i) {
+          or_walk_row(g, &o, tab, r, i, mode, &row);
+          double ax = 0.0, nn = 0.0;
+          for (int64_t q = 0; q < row.n; ++q) {
+            ax += row.l[q] * xs[row.j[q]];
+            nn += row.l[q] * row.l[q];
+          }
+          if (nn <= 0.0) continue;
+          double res = (double)r->wepl[i] - ax;
+          rr += res * res;
+          double ri = lambda * res / nn;
+          for (int64_t q = 0; q < row.n; ++q) {
+            delta[row.j[q]] += row.l[q] * ri;
+            cnt[row.j[q]] += 1.0;
+          }
         }
-        if (nn <= 0.0) continue;
-        double res = (double)r->wepl[i] - ax;
-        rr += res * res;
-        double ri = lambda * res / nn;
-        for (int64_t q = 0; q < row.n; ++q) {
-          delta[row.j[q]] += row.l[q] * ri;
-          cnt[row.j[q]] += 1.0;
-        }
+        for (int64_t j = 0; j < M; ++j)
+          if (cnt[j] > 0.0) {
+            xs[j] += delta[j] / cnt[j];
+            hit[j] = 1;
+          }
       }
       for (int64_t j = 0; j < M; ++j)
-        if (cnt[j] > 0.0) {
-          sum[j] += x[j] + delta[j] / cnt[j]; /* x_s,j */
+        if (hit[j]) {
+          sum[j] += xs[j];
           touch[j] += 1.0;
         }
     }
@@ -619,10 +634,12 @@ int or_carp(const or_grid *g, const double *tab, const or_rec *r, int64_t n, int
       if (touch[j] > 0.0) x[j] = sum[j] / touch[j];
     if (resid) resid[sw] = rr;
   }
+  free(xs);
   free(delta);
   free(cnt);
   free(sum);
   free(touch);
+  free(hit);
   free(row.j);
   free(row.l);
   return 0;
@@ -726,15 +743,16 @@ int or_tvs_apply(const or_grid *g, or_tvs *p, double *x) {
 /*
  * DROP (or_drop) with a TVS perturbation of the image entering every block
  * (Sec. 4.2: "applied to the initial solution that enters each block"), or
- * CARP (carp != 0) with one perturbation at the start of every iteration.
+ * CARP with `carp` strings (carp > 0) with one perturbation at the start of
+ * every iteration.
  */
 int or_solve_tvs(const or_grid *g, const double *tab, const or_rec *r, int64_t n, int n_blocks, double lambda,
                  int n_sweeps, int mode, int carp, double beta0, double alpha, double eps, int tries, double *x) {
   or_tvs p = {beta0, alpha, eps, tries, 0};
   for (int sw = 0; sw < n_sweeps; ++sw) {
-    if (carp) {
+    if (carp > 0) {
       if (or_tvs_apply(g, &p, x) < 0) return -1;
-      if (or_carp(g, tab, r, n, n_blocks, lambda, 1, mode, x, NULL) != 0) return -1;
+      if (or_carp(g, tab, r, n, n_blocks, carp, lambda, 1, mode, x, NULL) != 0) return -1;
     } else {
       for (int b = 0; b < n_blocks; ++b) {
         int64_t lo = (int64_t)b * n / n_blocks, hi = (int64_t)(b + 1) * n / n_blocks;

@@ -96,6 +96,7 @@ pct_status pct_create(pct_ctx** out, const pct_grid* grid, const pct_config* cfg
   if (c->cfg.tvs_alpha <= 0.f) c->cfg.tvs_alpha = 0.99f;
   if (c->cfg.tvs_eps <= 0.f) c->cfg.tvs_eps = 1e-4f;
   if (c->cfg.tvs_tries <= 0) c->cfg.tvs_tries = 4;
+  if (c->cfg.carp_strings <= 0 || c->cfg.carp_strings > c->cfg.n_blocks) c->cfg.carp_strings = c->cfg.n_blocks;
   if (!(c->cfg.tvs_beta0 >= 0.f) || c->cfg.tvs_alpha > 1.f) {
     delete c;
     return fail(PCT_ERR_INVALID_ARG, "TVS needs beta0 >= 0 and 0 < alpha <= 1");
@@ -187,7 +188,8 @@ pct_status pct_create(pct_ctx** out, const pct_grid* grid, const pct_config* cfg
     c->launches += 1;
     if (c->cfg.flags & PCT_FLAG_CARP) {
       if (cudaMalloc((void**)&c->carp_sum, M * sizeof(float)) != cudaSuccess ||
-          cudaMalloc((void**)&c->carp_touch, M * sizeof(float)) != cudaSuccess) {
+          cudaMalloc((void**)&c->carp_touch, M * sizeof(float)) != cudaSuccess ||
+          cudaMalloc((void**)&c->carp_x0, M * sizeof(float)) != cudaSuccess) {
         (void)cudaGetLastError();
         st = fail(PCT_ERR_NO_MEMORY, "CARP buffers");
         break;
@@ -247,6 +249,7 @@ pct_status pct_destroy(pct_ctx* c) {
   cudaFree(c->acc);
   cudaFree(c->carp_sum);
   cudaFree(c->carp_touch);
+  cudaFree(c->carp_x0);
   cudaFree(c->tv_g);
   cudaFree(c->tv_xp);
   cudaFree(c->tv_acc);
@@ -481,29 +484,36 @@ static pct_status build_sweep_graph(pct_ctx* c) {
   const bool carp = (c->cfg.flags & PCT_FLAG_CARP) != 0;
   const bool tvs = c->cfg.tvs_beta0 > 0.f;
   const pct::TvsParams tp{c->cfg.tvs_beta0, c->cfg.tvs_alpha, c->cfg.tvs_eps, c->cfg.tvs_tries};
+  const size_t xbytes = (size_t)c->M * sizeof(float);
   if (tvs && carp)
     err = pct::launch_tvs(c->x, c->grid.nx, c->grid.ny, c->grid.nz, tp, c->tv_g, c->tv_xp, c->tv_acc, c->tv_state, s);
-  for (int b = 0; b < B && err == cudaSuccess; ++b) {
-    const int64_t lo = block_lo(c, b), hi = block_lo(c, b + 1);
-    if (tvs && !carp)
-      err = pct::launch_tvs(c->x, c->grid.nx, c->grid.ny, c->grid.nz, tp, c->tv_g, c->tv_xp, c->tv_acc, c->tv_state,
-                            s);
-    if (err == cudaSuccess && c->ev) err = cudaEventRecordWithFlags(c->ev[3 * b], s, cudaEventRecordExternal);
-    if (err == cudaSuccess)
-      err = pct::launch_drop_fused(c->geo, c->rec, c->tab32, lo, hi - lo, c->x, c->delta, c->cfg.lambda,
-                                   c->cfg.flags, c->cfg.cta_threads, s);
-    if (err == cudaSuccess && c->ev) err = cudaEventRecordWithFlags(c->ev[3 * b + 1], s, cudaEventRecordExternal);
-    if (err == cudaSuccess) {
-      if (carp)  // every string projects from the same x: x changes only after the last string
-        err = pct::launch_carp_accum(c->x, c->delta, c->inv_s + (size_t)b * c->M, c->carp_sum, c->carp_touch, c->M,
-                                     s);
-      else
-        err = pct::launch_drop_apply(c->x, c->delta, c->inv_s + (size_t)b * c->M, c->M, clamp, c->cfg.clamp_min, s);
+  if (carp && err == cudaSuccess) err = cudaMemcpyAsync(c->carp_x0, c->x, xbytes, cudaMemcpyDeviceToDevice, s);
+  const int S = carp ? c->cfg.carp_strings : 1;
+  for (int st = 0; st < S && err == cudaSuccess; ++st) {
+    // CARP: string st sweeps blocks [st B/S, (st+1) B/S) on a copy of the
+    // iteration's starting image; DROP: one "string" of all blocks on x
+    const int b0 = carp ? (int)((int64_t)st * B / S) : 0, b1 = carp ? (int)((int64_t)(st + 1) * B / S) : B;
+    if (carp && st > 0) err = cudaMemcpyAsync(c->x, c->carp_x0, xbytes, cudaMemcpyDeviceToDevice, s);
+    for (int b = b0; b < b1 && err == cudaSuccess; ++b) {
+      const int64_t lo = block_lo(c, b), hi = block_lo(c, b + 1);
+      if (tvs && !carp)
+        err = pct::launch_tvs(c->x, c->grid.nx, c->grid.ny, c->grid.nz, tp, c->tv_g, c->tv_xp, c->tv_acc,
+                              c->tv_state, s);
+      if (err == cudaSuccess && c->ev) err = cudaEventRecordWithFlags(c->ev[3 * b], s, cudaEventRecordExternal);
+      if (err == cudaSuccess)
+        err = pct::launch_drop_fused(c->geo, c->rec, c->tab32, lo, hi - lo, c->x, c->delta, c->cfg.lambda,
+                                     c->cfg.flags, c->cfg.cta_threads, s);
+      if (err == cudaSuccess && c->ev) err = cudaEventRecordWithFlags(c->ev[3 * b + 1], s, cudaEventRecordExternal);
+      if (err == cudaSuccess)
+        err = pct::launch_drop_apply(c->x, c->delta, c->inv_s + (size_t)b * c->M, c->M, carp ? 0 : clamp,
+                                     c->cfg.clamp_min, s);
+      if (err == cudaSuccess && c->ev) err = cudaEventRecordWithFlags(c->ev[3 * b + 2], s, cudaEventRecordExternal);
     }
-    if (err == cudaSuccess && c->ev) err = cudaEventRecordWithFlags(c->ev[3 * b + 2], s, cudaEventRecordExternal);
+    if (carp && err == cudaSuccess)
+      err = pct::launch_carp_collect(c->x, c->inv_s + (size_t)b0 * c->M, b1 - b0, c->M, c->carp_sum, c->carp_touch, s);
   }
   if (carp && err == cudaSuccess)
-    err = pct::launch_carp_apply(c->x, c->carp_sum, c->carp_touch, c->M, clamp, c->cfg.clamp_min, s);
+    err = pct::launch_carp_finish(c->x, c->carp_x0, c->carp_sum, c->carp_touch, c->M, clamp, c->cfg.clamp_min, s);
   cudaError_t e2 = cudaStreamEndCapture(s, &graph);
   if (err != cudaSuccess || e2 != cudaSuccess) {
     if (graph) cudaGraphDestroy(graph);
@@ -531,7 +541,7 @@ pct_status pct_iterate(pct_ctx* c, int32_t n_sweeps) {
     if (st != PCT_OK) return st;
   }
   for (int s = 0; s < n_sweeps; ++s) PCT_CK(cudaGraphLaunch(c->sweep, c->stream));
-  c->launches += (int64_t)n_sweeps * (2 * c->cfg.n_blocks + ((c->cfg.flags & PCT_FLAG_CARP) ? 1 : 0));
+  c->launches += (int64_t)n_sweeps * (2 * c->cfg.n_blocks + ((c->cfg.flags & PCT_FLAG_CARP) ? c->cfg.carp_strings + 1 : 0));
   if (n_sweeps > 0) c->swept = true;
   return PCT_OK;
 }

@@ -32,6 +32,7 @@ struct pct_ctx {
   double* acc = nullptr;  // residual accumulator
   float* carp_sum = nullptr;    // CARP: sum of string estimates per voxel
   float* carp_touch = nullptr;  // CARP: number of strings touching each voxel
+  float* carp_x0 = nullptr;     // CARP: the iteration's starting image
   float* tv_g = nullptr;        // TVS: gradient
   float* tv_xp = nullptr;       // TVS: trial image
   double* tv_acc = nullptr;     // TVS: |g|^2, TV(x), TV(x')

@@ -67,12 +67,13 @@ cudaError_t launch_drop_fused(const Geo& g, const Rec& r, const float4* tab, int
                               const float* x, float* delta, float lambda, int flags, int threads, cudaStream_t s);
 cudaError_t launch_drop_apply(float* x, float* delta, const float* inv_s, int64_t M, int clamp, float clamp_min,
                               cudaStream_t s);
-// CARP: sum += x + delta * inv_s and touch += 1 where inv_s > 0, delta = 0;
-// then x = sum / touch where touch > 0 and sum = touch = 0.
-cudaError_t launch_carp_accum(const float* x, float* delta, const float* inv_s, float* sum, float* touch, int64_t M,
-                              cudaStream_t s);
-cudaError_t launch_carp_apply(float* x, float* sum, float* touch, int64_t M, int clamp, float clamp_min,
-                              cudaStream_t s);
+// CARP: add a string's swept copy xs to sum / touch where any of its nb
+// blocks (inv_s: nb x M) touches the voxel; then x = sum / touch where
+// touched, else x0, and sum = touch = 0.
+cudaError_t launch_carp_collect(const float* xs, const float* inv_s, int nb, int64_t M, float* sum, float* touch,
+                                cudaStream_t s);
+cudaError_t launch_carp_finish(float* x, const float* x0, float* sum, float* touch, int64_t M, int clamp,
+                               float clamp_min, cudaStream_t s);
 // One TVS perturbation of x (gradient, up to p.tries trials, commit); g, xp:
 // M floats of scratch; acc: 3 doubles and st: the state, both zero on entry
 // and left zero (st->ell keeps counting).

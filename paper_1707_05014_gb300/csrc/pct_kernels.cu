@@ -123,32 +123,31 @@ __global__ void drop_apply_kernel(float* __restrict__ x, float* __restrict__ del
   apply_voxel(x, delta, inv_s, j, clamp, clamp_min);
 }
 
-// CARP (Sec. 2.2): string s's estimate x_s,j = x0_j + delta_j / s_j where the
-// string touches j; accumulate its sum and the number of touching strings.
-__global__ void carp_accum_kernel(const float* __restrict__ x, float* __restrict__ delta,
-                                  const float* __restrict__ inv_s, float* __restrict__ sum, float* __restrict__ touch,
-                                  int64_t M) {
+// CARP (Sec. 2.2): after string s has swept its blocks on the working copy
+// x_s, add it to the per-voxel sum where the string touched the voxel (any of
+// its blocks has s_j > 0).
+__global__ void carp_collect_kernel(const float* __restrict__ xs, const float* __restrict__ inv_s, int nb, int64_t M,
+                                    float* __restrict__ sum, float* __restrict__ touch) {
   int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= M) return;
-  const float w = inv_s[j];
-  if (w > 0.f) {
-    sum[j] += __fmaf_rn(delta[j], w, x[j]);
+  bool hit = false;
+  for (int b = 0; b < nb && !hit; ++b) hit = inv_s[(int64_t)b * M + j] > 0.f;
+  if (hit) {
+    sum[j] += xs[j];
     touch[j] += 1.f;
   }
-  delta[j] = 0.f;
 }
 
-// Component average: x_j = sum_j / touch_j where any string touched j.
-__global__ void carp_apply_kernel(float* __restrict__ x, float* __restrict__ sum, float* __restrict__ touch,
-                                  int64_t M, int clamp, float clamp_min) {
+// Component average: x_j = sum_j / touch_j where any string touched j, else
+// the iteration's starting value; sum = touch = 0.
+__global__ void carp_finish_kernel(float* __restrict__ x, const float* __restrict__ x0, float* __restrict__ sum,
+                                   float* __restrict__ touch, int64_t M, int clamp, float clamp_min) {
   int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= M) return;
   const float t = touch[j];
-  if (t > 0.f) {
-    float xv = sum[j] / t;
-    if (clamp) xv = fmaxf(xv, clamp_min);
-    x[j] = xv;
-  }
+  float xv = t > 0.f ? sum[j] / t : x0[j];
+  if (clamp) xv = fmaxf(xv, clamp_min);
+  x[j] = xv;
   sum[j] = 0.f;
   touch[j] = 0.f;
 }
@@ -501,15 +500,15 @@ cudaError_t launch_drop_apply(float* x, float* delta, const float* inv_s, int64_
   return cudaGetLastError();
 }
 
-cudaError_t launch_carp_accum(const float* x, float* delta, const float* inv_s, float* sum, float* touch, int64_t M,
-                              cudaStream_t s) {
-  carp_accum_kernel<<<grid_for(M, 256), 256, 0, s>>>(x, delta, inv_s, sum, touch, M);
+cudaError_t launch_carp_collect(const float* xs, const float* inv_s, int nb, int64_t M, float* sum, float* touch,
+                                cudaStream_t s) {
+  carp_collect_kernel<<<grid_for(M, 256), 256, 0, s>>>(xs, inv_s, nb, M, sum, touch);
   return cudaGetLastError();
 }
 
-cudaError_t launch_carp_apply(float* x, float* sum, float* touch, int64_t M, int clamp, float clamp_min,
-                              cudaStream_t s) {
-  carp_apply_kernel<<<grid_for(M, 256), 256, 0, s>>>(x, sum, touch, M, clamp, clamp_min);
+cudaError_t launch_carp_finish(float* x, const float* x0, float* sum, float* touch, int64_t M, int clamp,
+                               float clamp_min, cudaStream_t s) {
+  carp_finish_kernel<<<grid_for(M, 256), 256, 0, s>>>(x, x0, sum, touch, M, clamp, clamp_min);
   return cudaGetLastError();
 }
 

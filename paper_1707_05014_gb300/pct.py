@@ -48,7 +48,7 @@ class _Config(ctypes.Structure):
     _fields_ = [("n_blocks", ctypes.c_int32), ("lam", ctypes.c_float), ("node_step_mm", ctypes.c_double),
                 ("flags", ctypes.c_int32), ("clamp_min", ctypes.c_float), ("threads_per_proton", ctypes.c_int32),
                 ("cta_threads", ctypes.c_int32), ("tvs_beta0", ctypes.c_float), ("tvs_alpha", ctypes.c_float),
-                ("tvs_eps", ctypes.c_float), ("tvs_tries", ctypes.c_int32)]
+                ("tvs_eps", ctypes.c_float), ("tvs_tries", ctypes.c_int32), ("carp_strings", ctypes.c_int32)]
 
 
 class _Hist(ctypes.Structure):
@@ -161,13 +161,13 @@ class Context:
 
     def __init__(self, grid, n_blocks: int = 10, lam: float = 1.0, node_step: float = 0.0, flags: int = 0,
                  clamp_min: float = 0.0, device: int = 0, cta_threads: int = 128, tvs_beta0: float = 0.0,
-                 tvs_alpha: float = 0.99, tvs_eps: float = 1e-4, tvs_tries: int = 4):
+                 tvs_alpha: float = 0.99, tvs_eps: float = 1e-4, tvs_tries: int = 4, carp_strings: int = 0):
         L = load_library()
         self._L = L
         self.grid = grid
         g = _Grid(int(grid.nx), int(grid.ny), int(grid.nz), float(grid.hx), float(grid.hy), float(grid.hz))
         c = _Config(int(n_blocks), float(lam), float(node_step), int(flags), float(clamp_min), 1, int(cta_threads),
-                    float(tvs_beta0), float(tvs_alpha), float(tvs_eps), int(tvs_tries))
+                    float(tvs_beta0), float(tvs_alpha), float(tvs_eps), int(tvs_tries), int(carp_strings))
         h = ctypes.c_void_p()
         _check(L.pct_create(ctypes.byref(h), ctypes.byref(g), ctypes.byref(c), int(device)))
         self._h = h

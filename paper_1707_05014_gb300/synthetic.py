@@ -144,6 +144,50 @@ def head_phantom(seed: int = 0, jitter: float = 0.0) -> Phantom:
     return Phantom(RSP_AIR, tuple(parts))
 
 
+# Inserts with the "true" RSPs of Table 2 (Sec. 4.2); the layout (a ring of
+# 12 mm cylinders at 50 mm from the axis of a 150 mm water-equivalent
+# cylinder) is this build's own, the paper's Fig. 3 being an image only.
+CATPHAN_INSERTS = (("Teflon", 1.790), ("PMP", 0.883), ("LDPE", 0.979), ("Polystyrene", 1.024),
+                   ("Delrin", 1.359), ("Air 1", 0.00113), ("Air 2", 0.00113))
+CATPHAN_BODY = 1.0
+CATPHAN_RADIUS = 75.0
+INSERT_RADIUS = 6.0
+INSERT_RING = 50.0
+
+
+def insert_centres():
+    n = len(CATPHAN_INSERTS)
+    return [(INSERT_RING * math.cos(2 * math.pi * k / n), INSERT_RING * math.sin(2 * math.pi * k / n))
+            for k in range(n)]
+
+
+def catphan_phantom() -> Phantom:
+    """Cylinder of RSP 1.0 (r = 75 mm, axis z) with seven r = 6 mm cylindrical
+    inserts at the true RSPs of Table 2, in air."""
+    parts = [Quadric("cylz", (0.0, 0.0, 0.0), (CATPHAN_RADIUS, CATPHAN_RADIUS, 1.0), CATPHAN_BODY - RSP_AIR)]
+    for (name, rsp), (cx, cy) in zip(CATPHAN_INSERTS, insert_centres()):
+        parts.append(Quadric("cylz", (cx, cy, 0.0), (INSERT_RADIUS, INSERT_RADIUS, 1.0), rsp - CATPHAN_BODY))
+    return Phantom(RSP_AIR, tuple(parts))
+
+
+def roi_stats(x: np.ndarray, grid: Grid, margin_mm: float = 2.0, z_margin_mm: float = 5.0):
+    """Table 2 style ROI analysis: for each insert, the voxels whose centres lie
+    in a cylinder of radius (6 mm - margin) around the insert axis and more than
+    z_margin from the grid's top and bottom (away from partial volume). Returns
+    rows (name, true, mean, std, %error)."""
+    c = grid.voxel_centres()
+    zmax = 0.5 * grid.nz * grid.hz - z_margin_mm
+    rows = []
+    for (name, rsp), (cx, cy) in zip(CATPHAN_INSERTS, insert_centres()):
+        m = ((c[:, 0] - cx) ** 2 + (c[:, 1] - cy) ** 2 <= (INSERT_RADIUS - margin_mm) ** 2) & (np.abs(c[:, 2]) <= zmax)
+        v = x[m]
+        mean = float(v.mean())
+        err = 100.0 * (mean - rsp) / rsp if rsp > 0.01 else None
+        rows.append({"material": name, "true": rsp, "mean": mean, "std": float(v.std()), "pct_error": err,
+                     "voxels": int(m.sum())})
+    return rows
+
+
 def voxelize(ph: Phantom, grid: Grid, ss: int = 3) -> np.ndarray:
     """Voxel-average RSP by ss^3 supersampling; float64 array of length M."""
     out = np.zeros(grid.m, dtype=np.float64)
@@ -265,6 +309,8 @@ class Workload:
             return water_cylinder(25.0)
         if self.phantom_kind == "head":
             return head_phantom(self.seed, self.jitter)
+        if self.phantom_kind == "catphan":
+            return catphan_phantom()
         raise ValueError(self.phantom_kind)
 
 

@@ -203,16 +203,17 @@ def test_projection_and_residual_match_oracle(pct, oracle, kahan):
     assert abs(7 * rr7 - ro) <= 0.1 * ro
 
 
-@pytest.mark.parametrize("strings,sweeps", [(10, 5), (3, 2)])
-def test_carp_parity(pct, oracle, strings, sweeps):
-    # CARP (Sec. 2.2): strings from a common x, component averaging
+@pytest.mark.parametrize("strings,blocks,sweeps", [(10, 10, 5), (3, 3, 2), (4, 12, 3), (3, 7, 2)])
+def test_carp_parity(pct, oracle, strings, blocks, sweeps):
+    # CARP (Sec. 2.2): strings of DROP blocks swept from a common x, then
+    # component averaging
     wl = S.tiny_workload(60_000, seed=71)
     rec = S.make_histories(wl)
-    with pct.Context(wl.grid, n_blocks=strings, flags=pct.FLAG_CARP) as ctx:
+    with pct.Context(wl.grid, n_blocks=blocks, flags=pct.FLAG_CARP, carp_strings=strings) as ctx:
         ctx.load(rec)
         ctx.iterate(sweeps)
         x = ctx.get_rsp().astype(np.float64)
-    xo = oracle.carp(wl.grid, rec, strings, sweeps, mode=oracle.MODE_FP32)
+    xo = oracle.carp(wl.grid, rec, strings, sweeps, mode=oracle.MODE_FP32, n_blocks=blocks)
     err = np.abs(x - xo) / np.maximum(np.abs(xo), 1.0)
     assert err.max() <= 1e-3, err.max()
 
@@ -225,13 +226,13 @@ def test_tvs_parity(pct, oracle, carp):
     rec = S.make_histories(wl)
     flags = pct.FLAG_CARP if carp else 0
     with pct.Context(wl.grid, n_blocks=4, flags=flags, tvs_beta0=0.05, tvs_alpha=0.99, tvs_eps=1e-4,
-                     tvs_tries=4) as ctx:
+                     tvs_tries=4, carp_strings=2) as ctx:
         ctx.load(rec)
         ctx.iterate(3)
         x = ctx.get_rsp().astype(np.float64)
-    xo = oracle.solve_tvs(wl.grid, rec, 4, 3, carp=carp, beta0=0.05, alpha=0.99, eps=1e-4, tries=4,
+    xo = oracle.solve_tvs(wl.grid, rec, 4, 3, carp=2 if carp else 0, beta0=0.05, alpha=0.99, eps=1e-4, tries=4,
                           mode=oracle.MODE_FP32)
     err = np.abs(x - xo) / np.maximum(np.abs(xo), 1.0)
     assert err.max() <= 1e-3, err.max()
-    plain = oracle.carp(wl.grid, rec, 4, 3) if carp else oracle.drop(wl.grid, rec, 4, 3)
+    plain = oracle.carp(wl.grid, rec, 2, 3, n_blocks=4) if carp else oracle.drop(wl.grid, rec, 4, 3)
     assert oracle.tv_value(wl.grid, x) < oracle.tv_value(wl.grid, plain)

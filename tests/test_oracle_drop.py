@@ -106,19 +106,21 @@ def test_carp_single_string_is_drop_single_block(oracle):
     assert np.abs(a - b).max() <= 1e-12 * max(1.0, np.abs(a).max())
 
 
-def test_carp_is_the_component_average_of_string_projections(oracle):
-    # one sweep of CARP from x0 equals, voxel by voxel, the mean of the
-    # single-string DROP results over the strings that touch the voxel
+@pytest.mark.parametrize("per_string", [1, 3])
+def test_carp_is_the_component_average_of_string_sweeps(oracle, per_string):
+    # one sweep of CARP from x0 equals, voxel by voxel, the mean of the strings'
+    # own DROP sweeps (over their blocks) across the strings that touch the voxel
     g, rec = _tiny()
     S_ = 4
+    B = S_ * per_string
     x0 = np.linspace(0.1, 1.0, g.m)
-    got = oracle.carp(g, rec, n_strings=S_, n_sweeps=1, x0=x0)
+    got = oracle.carp(g, rec, n_strings=S_, n_sweeps=1, x0=x0, n_blocks=B)
     rp, vox, _ = oracle.rows(g, rec)
     num = np.zeros(g.m)
     den = np.zeros(g.m)
     for s in range(S_):
-        lo, hi = s * 200 // S_, (s + 1) * 200 // S_
-        xs = oracle.drop(g, S.subset(rec, slice(lo, hi)), n_blocks=1, n_sweeps=1, x0=x0)
+        lo, hi = (s * per_string) * 200 // B, ((s + 1) * per_string) * 200 // B
+        xs = oracle.drop(g, S.subset(rec, slice(lo, hi)), n_blocks=per_string, n_sweeps=1, x0=x0)
         touched = np.zeros(g.m, dtype=bool)
         touched[vox[rp[lo]:rp[hi]]] = True
         num[touched] += xs[touched]

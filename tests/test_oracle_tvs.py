@@ -29,7 +29,7 @@ def test_tvs_never_raises_tv_and_reduces_to_plain_solvers(oracle):
     wl = S.tiny_workload(6000, seed=91)
     g = wl.grid
     rec = S.make_histories(wl)
-    for carp in (False, True):
+    for carp in (0, 3):
         plain = oracle.carp(g, rec, 3, 2) if carp else oracle.drop(g, rec, 3, 2)
         same = oracle.solve_tvs(g, rec, 3, 2, carp=carp, beta0=0.0)
         assert np.abs(same - plain).max() <= 1e-12 * max(1.0, np.abs(plain).max())
