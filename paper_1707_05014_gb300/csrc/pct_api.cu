@@ -145,13 +145,8 @@ pct_status pct_create(pct_ctx** out, const pct_grid* grid, const pct_config* cfg
   G.hnx = 0.5f * (float)g.nx;
   G.hny = 0.5f * (float)g.ny;
   G.hnz = 0.5f * (float)g.nz;
-  G.lx = (float)(g.hx / (double)pct::kQOne);
-  G.ly = (float)(g.hy / (double)pct::kQOne);
-  G.lz = (float)(g.hz / (double)pct::kQOne);
   G.bx = (float)(0.5 * X);
   G.by = (float)(0.5 * Y);
-  G.bz = (float)(0.5 * Z);
-  G.R = (float)c->R;
 
   pct_status st = PCT_OK;
   do {

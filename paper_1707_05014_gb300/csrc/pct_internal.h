@@ -26,9 +26,7 @@ struct Geo {
   float hx, hy, hz;     // voxel size (mm)
   float ihx, ihy, ihz;  // 1/h rounded from FP64
   float hnx, hny, hnz;  // n/2
-  float lx, ly, lz;     // h * 2^-20: mm per Q20 unit
-  float bx, by, bz;     // half box extents (mm)
-  float R;              // plane half distance (mm)
+  float bx, by;         // half box extents in x and y (mm)
 };
 
 // Structure-of-arrays history records (device pointers).

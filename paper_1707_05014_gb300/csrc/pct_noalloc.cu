@@ -134,13 +134,8 @@ extern "C" pct_status pct_drop_block_noalloc(const pct_grid* grid, const pct_con
   g.hnx = 0.5f * (float)gr.nx;
   g.hny = 0.5f * (float)gr.ny;
   g.hnz = 0.5f * (float)gr.nz;
-  g.lx = (float)(gr.hx / (double)pct::kQOne);
-  g.ly = (float)(gr.hy / (double)pct::kQOne);
-  g.lz = (float)(gr.hz / (double)pct::kQOne);
   g.bx = (float)(0.5 * X);
   g.by = (float)(0.5 * Y);
-  g.bz = (float)(0.5 * Z);
-  g.R = (float)R;
   const Rec r{src[0], src[1], src[2], src[3], src[4], src[5], src[6], src[7], src[8], src[9], src[10]};
 
   // scratch address of the current device (first call on a device)
