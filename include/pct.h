@@ -66,7 +66,8 @@ typedef struct pct_config {
   int32_t flags;            /* PCT_FLAG_*                                      */
   float clamp_min;          /* lower clamp of x after each block (with flag)   */
   int32_t threads_per_proton; /* 1 (reserved for 2, 4, 8)                      */
-  int32_t cta_threads;      /* threads per CTA of the fused kernel; 0 = 128    */
+  int32_t cta_threads;      /* threads per CTA of the load-time count kernel;
+                             * 0 = 128 (the fused kernel always runs 128)    */
   /* Total-variation superiorization (Sec. 4.2), off when tvs_beta0 <= 0:
    * before every DROP block (with PCT_FLAG_CARP: before every CARP iteration)
    * x is perturbed once along -grad TV_eps(x) / rms, with step
