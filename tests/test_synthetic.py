@@ -2,10 +2,36 @@
 analysis, straight-line WEPL against a brute-force line integral, and the
 device generator against the host recipe."""
 import math
+import os
 
 import numpy as np
 
 from paper_1707_05014_gb300 import synthetic as S
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _table2_true_rsp():
+    """Sec. 4.2, Table 2: the inserts' true RSPs (tests/golden/table2_true_rsp.txt)."""
+    out = []
+    with open(os.path.join(GOLDEN, "table2_true_rsp.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                name, rsp = line.rstrip("\n").split("\t")
+                out.append((name, float(rsp)))
+    return out
+
+
+def test_insert_phantom_carries_table2_true_rsps():
+    # the phantom's materials are the paper's, in the paper's order
+    assert list(S.CATPHAN_INSERTS) == _table2_true_rsp()
+    # and the voxelised image holds exactly those values at each insert axis
+    g = S.Grid(160, 160, 32, 1.25, 1.25, 1.25)
+    x = S.voxelize(S.catphan_phantom(), g, ss=1).reshape(g.nz, g.ny, g.nx)
+    for (name, rsp), (cx, cy) in zip(_table2_true_rsp(), S.insert_centres()):
+        ix = int((cx + 0.5 * g.nx * g.hx) // g.hx)
+        iy = int((cy + 0.5 * g.ny * g.hy) // g.hy)
+        assert abs(x[g.nz // 2, iy, ix] - rsp) < 1e-12, name
 
 
 def test_roi_stats_on_the_true_image_are_exact():
