@@ -56,7 +56,8 @@ def build(force: bool = False) -> str:
 
 class _Grid(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("hx", ctypes.c_double),
-                ("hy", ctypes.c_double), ("hz", ctypes.c_double), ("node_step", ctypes.c_double)]
+                ("hy", ctypes.c_double), ("hz", ctypes.c_double), ("node_step", ctypes.c_double),
+                ("hull", ctypes.POINTER(ctypes.c_uint8))]
 
 
 class _Rec(ctypes.Structure):
@@ -83,6 +84,10 @@ def lib():
         L.or_moment.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int]
         L.or_moment.restype = ctypes.c_double
         L.or_mlp_table.argtypes = [gp, ctypes.c_int, dp]
+        L.or_mlp_table_n.argtypes = [gp, ctypes.c_int, ctypes.c_int, dp]
+        L.or_hull_ranges.argtypes = [gp, dp, rp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, i32p]
+        L.or_carve_hull.argtypes = [gp, dp, rp, ctypes.c_int64, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                    ctypes.POINTER(ctypes.c_uint8)]
         L.or_nodes.argtypes = [gp, dp, rp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, i32p]
         L.or_polyline.argtypes = [gp, dp, rp, ctypes.c_int64, ctypes.c_int, i32p]
         L.or_rows.argtypes = [gp, dp, rp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, i64p, i32p, dp,
@@ -103,8 +108,17 @@ def lib():
     return _lib
 
 
-def _grid(g, node_step: float = 0.0) -> _Grid:
-    return _Grid(int(g.nx), int(g.ny), int(g.nz), float(g.hx), float(g.hy), float(g.hz), float(node_step))
+def _grid(g, node_step: float = 0.0, hull=None) -> _Grid:
+    """C grid descriptor; ``hull`` (M values, nonzero = inside the object) is
+    kept alive on the returned structure."""
+    gg = _Grid(int(g.nx), int(g.ny), int(g.nz), float(g.hx), float(g.hy), float(g.hz), float(node_step), None)
+    if hull is not None:
+        h = np.ascontiguousarray(np.asarray(hull).reshape(-1) != 0, dtype=np.uint8)
+        if h.size != g.nx * g.ny * g.nz:
+            raise ValueError("hull mask must hold one value per voxel")
+        gg.hull = h.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+        gg._keep = h
+    return gg
 
 
 def _ptr(a: np.ndarray, ct):
@@ -154,6 +168,43 @@ def mlp_table(g, flags: int = 0, node_step: float = 0.0) -> np.ndarray:
     return out
 
 
+def mlp_table_n(g, n: int, flags: int = 0, node_step: float = 0.0) -> np.ndarray:
+    """(n+1, 4) float64: the MLP table of a hull n node intervals thick (nodes
+    m = 0..n from the hull entry); n = K is the slab between the planes."""
+    out = np.zeros((n + 1, 4))
+    gg = _grid(g, node_step)
+    if lib().or_mlp_table_n(ctypes.byref(gg), int(flags), int(n), _ptr(out, ctypes.c_double)) != n:
+        raise ValueError("n outside [1, K]")
+    return out
+
+
+def hull_ranges(g, rec, hull, first: int = 0, count: Optional[int] = None, mode: int = MODE_FP32,
+                node_step: float = 0.0) -> np.ndarray:
+    """(count, 2) int32: hull entry and exit node of each proton ((0, K) for a
+    proton that misses the hull)."""
+    h = _RecHolder(rec)
+    count = h.n - first if count is None else count
+    tab = _tab(g, None, 0, node_step)
+    out = np.zeros((count, 2), dtype=np.int32)
+    gg = _grid(g, node_step, hull)
+    lib().or_hull_ranges(ctypes.byref(gg), _ptr(tab, ctypes.c_double), ctypes.byref(h.s), first, count, mode,
+                         _ptr(out, ctypes.c_int32))
+    return out
+
+
+def carve_hull(g, rec, wepl_max: float, dilate: int = 0, mode: int = MODE_FP32, node_step: float = 0.0) -> np.ndarray:
+    """Space-carved hull (M uint8): voxels on the rows of protons with WEPL <=
+    wepl_max are outside; the rest, grown by ``dilate`` 6-neighbour steps, is
+    the hull."""
+    h = _RecHolder(rec)
+    tab = _tab(g, None, 0, node_step)
+    out = np.zeros(g.nx * g.ny * g.nz, dtype=np.uint8)
+    gg = _grid(g, node_step)
+    lib().or_carve_hull(ctypes.byref(gg), _ptr(tab, ctypes.c_double), ctypes.byref(h.s), h.n, float(wepl_max),
+                        int(dilate), mode, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)))
+    return out
+
+
 def _tab(g, table, flags, node_step):
     if table is None:
         table = mlp_table(g, flags, node_step)
@@ -161,37 +212,37 @@ def _tab(g, table, flags, node_step):
 
 
 def nodes(g, rec, first: int = 0, count: Optional[int] = None, mode: int = MODE_FP32, table=None, flags: int = 0,
-          node_step: float = 0.0) -> np.ndarray:
+          node_step: float = 0.0, hull=None) -> np.ndarray:
     """(count, K+1, 3) int32 Q20 grid coordinates of the interior nodes."""
     h = _RecHolder(rec)
     count = h.n - first if count is None else count
     tab = _tab(g, table, flags, node_step)
     out = np.zeros((count, tab.shape[0], 3), dtype=np.int32)
-    gg = _grid(g, node_step)
+    gg = _grid(g, node_step, hull)
     lib().or_nodes(ctypes.byref(gg), _ptr(tab, ctypes.c_double), ctypes.byref(h.s), first, count, mode,
                    _ptr(out, ctypes.c_int32))
     return out
 
 
-def polyline(g, rec, i: int, mode: int = MODE_FP32, table=None, flags: int = 0, node_step: float = 0.0):
+def polyline(g, rec, i: int, mode: int = MODE_FP32, table=None, flags: int = 0, node_step: float = 0.0, hull=None):
     """(K + 2E + 1, 3) int32 Q20 nodes of proton i, extensions included."""
     h = _RecHolder(rec)
     tab = _tab(g, table, flags, node_step)
     _, _, K, E = geom_info(g, node_step)
     out = np.zeros((K + 2 * E + 1, 3), dtype=np.int32)
-    gg = _grid(g, node_step)
+    gg = _grid(g, node_step, hull)
     lib().or_polyline(ctypes.byref(gg), _ptr(tab, ctypes.c_double), ctypes.byref(h.s), int(i), mode,
                       _ptr(out, ctypes.c_int32))
     return out
 
 
 def rows(g, rec, first: int = 0, count: Optional[int] = None, mode: int = MODE_FP32, table=None, flags: int = 0,
-         node_step: float = 0.0):
+         node_step: float = 0.0, hull=None):
     """CSR rows: (row_ptr int64 [count+1], vox int32, len float64 mm)."""
     h = _RecHolder(rec)
     count = h.n - first if count is None else count
     tab = _tab(g, table, flags, node_step)
-    gg = _grid(g, node_step)
+    gg = _grid(g, node_step, hull)
     rp = np.zeros(count + 1, dtype=np.int64)
     cap = max(1, 64 * count)
     while True:
@@ -205,11 +256,11 @@ def rows(g, rec, first: int = 0, count: Optional[int] = None, mode: int = MODE_F
 
 
 def project(g, rec, x: np.ndarray, first: int = 0, count: Optional[int] = None, mode: int = MODE_FP32, table=None,
-            flags: int = 0, node_step: float = 0.0) -> np.ndarray:
+            flags: int = 0, node_step: float = 0.0, hull=None) -> np.ndarray:
     h = _RecHolder(rec)
     count = h.n - first if count is None else count
     tab = _tab(g, table, flags, node_step)
-    gg = _grid(g, node_step)
+    gg = _grid(g, node_step, hull)
     xx = np.ascontiguousarray(x, dtype=np.float64)
     y = np.zeros(count)
     lib().or_project(ctypes.byref(gg), _ptr(tab, ctypes.c_double), ctypes.byref(h.s), first, count, mode,
@@ -218,10 +269,10 @@ def project(g, rec, x: np.ndarray, first: int = 0, count: Optional[int] = None, 
 
 
 def block_counts(g, rec, n_blocks: int, b: int, mode: int = MODE_FP32, table=None, flags: int = 0,
-                 node_step: float = 0.0) -> np.ndarray:
+                 node_step: float = 0.0, hull=None) -> np.ndarray:
     h = _RecHolder(rec)
     tab = _tab(g, table, flags, node_step)
-    gg = _grid(g, node_step)
+    gg = _grid(g, node_step, hull)
     out = np.zeros(g.nx * g.ny * g.nz)
     lib().or_block_counts(ctypes.byref(gg), _ptr(tab, ctypes.c_double), ctypes.byref(h.s), h.n, n_blocks, b, mode,
                           _ptr(out, ctypes.c_double))
@@ -229,12 +280,12 @@ def block_counts(g, rec, n_blocks: int, b: int, mode: int = MODE_FP32, table=Non
 
 
 def drop(g, rec, n_blocks: int, n_sweeps: int, lam: float = 1.0, x0: Optional[np.ndarray] = None,
-         mode: int = MODE_FP32, table=None, flags: int = 0, node_step: float = 0.0, clamp_min: Optional[float] = None,
+         mode: int = MODE_FP32, table=None, flags: int = 0, node_step: float = 0.0, hull=None, clamp_min: Optional[float] = None,
          return_resid: bool = False):
     """DROP reconstruction (Sec. 2.1). Returns x (float64, M)."""
     h = _RecHolder(rec)
     tab = _tab(g, table, flags, node_step)
-    gg = _grid(g, node_step)
+    gg = _grid(g, node_step, hull)
     M = g.nx * g.ny * g.nz
     x = np.zeros(M) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
     resid = np.zeros(max(n_sweeps, 1))
@@ -247,7 +298,7 @@ def drop(g, rec, n_blocks: int, n_sweeps: int, lam: float = 1.0, x0: Optional[np
 
 
 def carp(g, rec, n_strings: int, n_sweeps: int, lam: float = 1.0, x0: Optional[np.ndarray] = None,
-         mode: int = MODE_FP32, table=None, flags: int = 0, node_step: float = 0.0, return_resid: bool = False,
+         mode: int = MODE_FP32, table=None, flags: int = 0, node_step: float = 0.0, hull=None, return_resid: bool = False,
          n_blocks: Optional[int] = None):
     """CARP reconstruction (Sec. 2.2): strings of consecutive DROP blocks
     (n_blocks, default one block per string) swept from a common x0, then
@@ -255,7 +306,7 @@ def carp(g, rec, n_strings: int, n_sweeps: int, lam: float = 1.0, x0: Optional[n
     n_blocks = n_strings if n_blocks is None else n_blocks
     h = _RecHolder(rec)
     tab = _tab(g, table, flags, node_step)
-    gg = _grid(g, node_step)
+    gg = _grid(g, node_step, hull)
     M = g.nx * g.ny * g.nz
     x = np.zeros(M) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
     resid = np.zeros(max(n_sweeps, 1))
@@ -283,13 +334,13 @@ def tv_grad(g, x: np.ndarray, eps: float = 1e-4) -> np.ndarray:
 
 def solve_tvs(g, rec, n_blocks: int, n_sweeps: int, lam: float = 1.0, carp: int = 0, beta0: float = 0.02,
               alpha: float = 0.99, eps: float = 1e-4, tries: int = 4, x0: Optional[np.ndarray] = None,
-              mode: int = MODE_FP32, table=None, flags: int = 0, node_step: float = 0.0) -> np.ndarray:
+              mode: int = MODE_FP32, table=None, flags: int = 0, node_step: float = 0.0, hull=None) -> np.ndarray:
     """DROP (TVS before every block) or, with carp = number of strings > 0,
     CARP (TVS before every iteration), with total-variation superiorization
     (Sec. 4.2)."""
     h = _RecHolder(rec)
     tab = _tab(g, table, flags, node_step)
-    gg = _grid(g, node_step)
+    gg = _grid(g, node_step, hull)
     M = g.nx * g.ny * g.nz
     x = np.zeros(M) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
     rc = lib().or_solve_tvs(ctypes.byref(gg), _ptr(tab, ctypes.c_double), ctypes.byref(h.s), h.n, n_blocks,

@@ -58,7 +58,8 @@
 typedef struct {
   int nx, ny, nz;
   double hx, hy, hz;
-  double node_step; /* <= 0: min(h)/2 */
+  double node_step;     /* <= 0: min(h)/2 */
+  const uint8_t *hull;  /* object hull, one byte per voxel (nonzero = inside); NULL: none */
 } or_grid;
 
 typedef struct {
@@ -181,25 +182,23 @@ static void mul2(const double a[2][2], const double b[2][2], double o[2][2]) {
 }
 
 /*
- * MLP coefficient table: for each interior node k = 0..K (depth u_k) the
+ * MLP coefficients of the nodes m = 0..n, spaced du (mm), of a water layer of
+ * thickness W (cm) that the proton enters at m = 0 and leaves at m = n: the
  * first rows of H^-1 S1^-1 R0 -> (c1, c2) and of H^-1 R1^T S2^-1 -> (c3, c4),
- * so that t_k = c1 t0 + c2 st0 + c3 t2 + c4 st2 (positions in mm, c2/c4 in
- * mm). Nodes k = 0 and k = K take the measured values exactly. out: (K+1)*4.
+ * so that t_m = c1 t_in + c2 s_in + c3 t_out + c4 s_out (positions in mm,
+ * c2/c4 in mm). The end nodes take the measured values exactly. out: (n+1)*4.
  */
-int or_mlp_table(const or_grid *g, int flags, double *out) {
-  or_geom o;
-  or_geometry(g, &o);
-  const double W = 2.0 * o.R / 10.0; /* slab thickness, cm */
-  for (int k = 0; k <= o.K; ++k) {
+static void or_table_fill(double W, double du, int n, int flags, double *out) {
+  for (int k = 0; k <= n; ++k) {
     double *c = out + 4 * k;
-    if (k == 0 || k == o.K) {
+    if (k == 0 || k == n) {
       c[0] = (k == 0);
       c[1] = 0.0;
-      c[2] = (k == o.K);
+      c[2] = (k == n);
       c[3] = 0.0;
       continue;
     }
-    double w1 = k * o.du / 10.0; /* node depth, cm */
+    double w1 = k * du / 10.0; /* node depth, cm */
     double k1 = or_highland(w1, flags), k2 = or_highland(W - w1, flags);
     double S1[2][2] = {{k1 * or_moment(0, w1, w1, 2, flags), k1 * or_moment(0, w1, w1, 1, flags)},
                        {k1 * or_moment(0, w1, w1, 1, flags), k1 * or_moment(0, w1, w1, 0, flags)}};
@@ -224,7 +223,49 @@ int or_mlp_table(const or_grid *g, int flags, double *out) {
     c[2] = Mb[0][0];
     c[3] = 10.0 * Mb[0][1];
   }
+}
+
+/* MLP table between the measurement planes (the whole slab, W = 2R): nodes
+ * k = 0..K at depth u_k. out: (K+1)*4. */
+int or_mlp_table(const or_grid *g, int flags, double *out) {
+  or_geom o;
+  or_geometry(g, &o);
+  or_table_fill(2.0 * o.R / 10.0, o.du, o.K, flags, out);
   return o.K;
+}
+
+/* Table of a hull of n node intervals (thickness n du; n = K is the slab). */
+static double or_layer_cm(const or_geom *o, int n) { return n == o->K ? 2.0 * o->R / 10.0 : n * o->du / 10.0; }
+
+int or_mlp_table_n(const or_grid *g, int flags, int n, double *out) {
+  or_geom o;
+  or_geometry(g, &o);
+  if (n < 1 || n > o.K) return -1;
+  or_table_fill(or_layer_cm(&o, n), o.du, n, flags, out);
+  return n;
+}
+
+/* Tables per hull thickness, computed on first use for the current geometry. */
+static double **or_fam = NULL;
+static int or_fam_K = -1;
+static double or_fam_du = 0.0, or_fam_R = 0.0;
+
+static const double *or_family(const or_geom *o, int n) {
+  if (or_fam_K != o->K || or_fam_du != o->du || or_fam_R != o->R) {
+    if (or_fam) {
+      for (int i = 0; i <= or_fam_K; ++i) free(or_fam[i]);
+      free(or_fam);
+    }
+    or_fam = (double **)calloc((size_t)o->K + 1, sizeof(double *));
+    or_fam_K = o->K;
+    or_fam_du = o->du;
+    or_fam_R = o->R;
+  }
+  if (!or_fam[n]) {
+    or_fam[n] = (double *)malloc(((size_t)n + 1) * 4 * sizeof(double));
+    or_table_fill(or_layer_cm(o, n), o->du, n, 0, or_fam[n]);
+  }
+  return or_fam[n];
 }
 
 /* ------------------------------------------------------------------ */
@@ -243,60 +284,151 @@ static int32_t or_quant_f(float q) {
   return (int32_t)lrintf(q * 1048576.0f);
 }
 
-/* Quantised node k of proton i in grid units (Q20). */
-static void or_node(const or_grid *g, const or_geom *o, const double *tab, const or_rec *r, int64_t i, int mode,
-                    int k, int32_t Q[3]) {
+/*
+ * Path of one proton: straight along the measured entry direction up to node
+ * iin, the MLP of the layer between nodes iin and iout (table tab, entries
+ * m = k - iin), straight along the measured exit direction from node iout.
+ * Without a hull iin = 0, iout = K (the measurement planes, the slab table).
+ * With one, iin is the first node k in [0, K] whose entry-ray point lies in a
+ * hull voxel and iout the last node whose exit-ray point does (a proton with
+ * no such pair keeps the slab).
+ */
+typedef struct {
+  int iin, iout;
+  const double *tab;
+} or_path;
+
+/* grid coordinates of the point (u, t, v) -> Q20 */
+static void or_quantise_d(const or_grid *g, const or_rec *r, int64_t i, double u, double t, double v, int32_t Q[3]) {
+  double cp = r->cphi[i], sp = r->sphi[i];
+  double x = u * cp - t * sp, y = u * sp + t * cp, z = v;
+  Q[0] = or_quant_d(x / g->hx + 0.5 * g->nx);
+  Q[1] = or_quant_d(y / g->hy + 0.5 * g->ny);
+  Q[2] = or_quant_d(z / g->hz + 0.5 * g->nz);
+}
+
+static void or_quantise_f(const or_grid *g, const or_rec *r, int64_t i, float u, float t, float v, int32_t Q[3]) {
+  float cp = r->cphi[i], sp = r->sphi[i];
+  float ts = t * sp, tc = t * cp;
+  float x = fmaf(u, cp, -ts);
+  float y = fmaf(u, sp, tc);
+  float ihx = (float)(1.0 / g->hx), ihy = (float)(1.0 / g->hy), ihz = (float)(1.0 / g->hz);
+  Q[0] = or_quant_f(fmaf(x, ihx, 0.5f * (float)g->nx));
+  Q[1] = or_quant_f(fmaf(y, ihy, 0.5f * (float)g->ny));
+  Q[2] = or_quant_f(fmaf(v, ihz, 0.5f * (float)g->nz));
+}
+
+/* Lateral/vertical position at node k of the entry ray (exit = 0) or the
+ * exit ray (exit = 1), both modes. */
+static void or_ray_d(const or_geom *o, const or_rec *r, int64_t i, int exit, int k, double *t, double *v) {
+  if (!exit) {
+    *t = (double)r->t0[i] + (double)r->st0[i] * (k * o->du);
+    *v = (double)r->v0[i] + (double)r->sv0[i] * (k * o->du);
+  } else {
+    *t = (double)r->t2[i] + (double)r->st2[i] * ((k - o->K) * o->du);
+    *v = (double)r->v2[i] + (double)r->sv2[i] * ((k - o->K) * o->du);
+  }
+}
+
+static void or_ray_f(const or_geom *o, const or_rec *r, int64_t i, int exit, int k, float *t, float *v) {
+  float du = (float)o->du;
+  if (!exit) {
+    float dk = (float)k * du;
+    *t = fmaf(r->st0[i], dk, r->t0[i]);
+    *v = fmaf(r->sv0[i], dk, r->v0[i]);
+  } else {
+    float dk = (float)(k - o->K) * du;
+    *t = fmaf(r->st2[i], dk, r->t2[i]);
+    *v = fmaf(r->sv2[i], dk, r->v2[i]);
+  }
+}
+
+/* Q20 point of node k on the entry or exit ray */
+static void or_ray_node(const or_grid *g, const or_geom *o, const or_rec *r, int64_t i, int mode, int exit, int k,
+                        int32_t Q[3]) {
   if (mode == OR_MODE_FP64) {
-    double t0 = r->t0[i], v0 = r->v0[i], st0 = r->st0[i], sv0 = r->sv0[i];
-    double t2 = r->t2[i], v2 = r->v2[i], st2 = r->st2[i], sv2 = r->sv2[i];
-    double cp = r->cphi[i], sp = r->sphi[i];
-    double u = o->u0 + k * o->du, t, v;
-    if (k < 0) {
-      t = t0 + st0 * (k * o->du);
-      v = v0 + sv0 * (k * o->du);
-    } else if (k > o->K) {
-      t = t2 + st2 * ((k - o->K) * o->du);
-      v = v2 + sv2 * ((k - o->K) * o->du);
-    } else {
-      const double *c = tab + 4 * k;
-      t = c[0] * t0 + c[1] * st0 + c[2] * t2 + c[3] * st2;
-      v = c[0] * v0 + c[1] * sv0 + c[2] * v2 + c[3] * sv2;
-    }
-    double x = u * cp - t * sp, y = u * sp + t * cp, z = v;
-    Q[0] = or_quant_d(x / g->hx + 0.5 * g->nx);
-    Q[1] = or_quant_d(y / g->hy + 0.5 * g->ny);
-    Q[2] = or_quant_d(z / g->hz + 0.5 * g->nz);
+    double t, v;
+    or_ray_d(o, r, i, exit, k, &t, &v);
+    or_quantise_d(g, r, i, o->u0 + k * o->du, t, v, Q);
+  } else {
+    float t, v;
+    or_ray_f(o, r, i, exit, k, &t, &v);
+    or_quantise_f(g, r, i, fmaf((float)k, (float)o->du, (float)o->u0), t, v, Q);
+  }
+}
+
+static int64_t or_floor_div(int64_t a);
+
+/* the voxel holding Q is inside the grid and the hull */
+static int or_in_hull(const or_grid *g, const int32_t Q[3]) {
+  int64_t ix = or_floor_div(Q[0]), iy = or_floor_div(Q[1]), iz = or_floor_div(Q[2]);
+  if (ix < 0 || ix >= g->nx || iy < 0 || iy >= g->ny || iz < 0 || iz >= g->nz) return 0;
+  return g->hull[ix + (int64_t)g->nx * (iy + (int64_t)g->ny * iz)] != 0;
+}
+
+static void or_path_of(const or_grid *g, const or_geom *o, const double *tab, const or_rec *r, int64_t i, int mode,
+                       or_path *p) {
+  p->iin = 0;
+  p->iout = o->K;
+  p->tab = tab;
+  if (!g->hull) return;
+  int32_t Q[3];
+  int iin = -1, iout = -1;
+  for (int k = 0; k <= o->K && iin < 0; ++k) {
+    or_ray_node(g, o, r, i, mode, 0, k, Q);
+    if (or_in_hull(g, Q)) iin = k;
+  }
+  for (int k = o->K; k >= 0 && iout < 0; --k) {
+    or_ray_node(g, o, r, i, mode, 1, k, Q);
+    if (or_in_hull(g, Q)) iout = k;
+  }
+  if (iin < 0 || iout < 0 || iout <= iin) return; /* misses the hull */
+  p->iin = iin;
+  p->iout = iout;
+  p->tab = iout - iin == o->K ? tab : or_family(o, iout - iin);
+}
+
+/* Quantised node k of proton i in grid units (Q20) on path p. */
+static void or_node(const or_grid *g, const or_geom *o, const or_path *p, const or_rec *r, int64_t i, int mode, int k,
+                    int32_t Q[3]) {
+  if (k <= p->iin || k >= p->iout) {
+    or_ray_node(g, o, r, i, mode, k >= p->iout, k, Q);
+    return;
+  }
+  const double *c = p->tab + 4 * (k - p->iin);
+  if (mode == OR_MODE_FP64) {
+    double tin, vin, tout, vout;
+    or_ray_d(o, r, i, 0, p->iin, &tin, &vin);
+    or_ray_d(o, r, i, 1, p->iout, &tout, &vout);
+    double t = c[0] * tin + c[1] * r->st0[i] + c[2] * tout + c[3] * r->st2[i];
+    double v = c[0] * vin + c[1] * r->sv0[i] + c[2] * vout + c[3] * r->sv2[i];
+    or_quantise_d(g, r, i, o->u0 + k * o->du, t, v, Q);
   } else {
     /* fixed single-precision order (the bit-exact contract) */
-    float t0 = r->t0[i], v0 = r->v0[i], st0 = r->st0[i], sv0 = r->sv0[i];
-    float t2 = r->t2[i], v2 = r->v2[i], st2 = r->st2[i], sv2 = r->sv2[i];
-    float cp = r->cphi[i], sp = r->sphi[i];
-    float du = (float)o->du, u0 = (float)o->u0;
-    float u = fmaf((float)k, du, u0), t, v;
-    if (k < 0) {
-      float dk = (float)k * du;
-      t = fmaf(st0, dk, t0);
-      v = fmaf(sv0, dk, v0);
-    } else if (k > o->K) {
-      float dk = (float)(k - o->K) * du;
-      t = fmaf(st2, dk, t2);
-      v = fmaf(sv2, dk, v2);
-    } else {
-      const double *c = tab + 4 * k;
-      float c1 = (float)c[0], c2 = (float)c[1], c3 = (float)c[2], c4 = (float)c[3];
-      float a = c1 * t0;
-      t = fmaf(c4, st2, fmaf(c3, t2, fmaf(c2, st0, a)));
-      float b = c1 * v0;
-      v = fmaf(c4, sv2, fmaf(c3, v2, fmaf(c2, sv0, b)));
-    }
-    float ts = t * sp, tc = t * cp;
-    float x = fmaf(u, cp, -ts);
-    float y = fmaf(u, sp, tc);
-    float ihx = (float)(1.0 / g->hx), ihy = (float)(1.0 / g->hy), ihz = (float)(1.0 / g->hz);
-    Q[0] = or_quant_f(fmaf(x, ihx, 0.5f * (float)g->nx));
-    Q[1] = or_quant_f(fmaf(y, ihy, 0.5f * (float)g->ny));
-    Q[2] = or_quant_f(fmaf(v, ihz, 0.5f * (float)g->nz));
+    float tin, vin, tout, vout;
+    or_ray_f(o, r, i, 0, p->iin, &tin, &vin);
+    or_ray_f(o, r, i, 1, p->iout, &tout, &vout);
+    float c1 = (float)c[0], c2 = (float)c[1], c3 = (float)c[2], c4 = (float)c[3];
+    float a = c1 * tin;
+    float t = fmaf(c4, r->st2[i], fmaf(c3, tout, fmaf(c2, r->st0[i], a)));
+    float b = c1 * vin;
+    float v = fmaf(c4, r->sv2[i], fmaf(c3, vout, fmaf(c2, r->sv0[i], b)));
+    or_quantise_f(g, r, i, fmaf((float)k, (float)o->du, (float)o->u0), t, v, Q);
   }
+}
+
+/* Hull entry/exit nodes of protons [first, first+count): out (count, 2). */
+int or_hull_ranges(const or_grid *g, const double *tab, const or_rec *r, int64_t first, int64_t count, int mode,
+                   int32_t *out) {
+  or_geom o;
+  or_geometry(g, &o);
+  for (int64_t p = 0; p < count; ++p) {
+    or_path pa;
+    or_path_of(g, &o, tab, r, first + p, mode, &pa);
+    out[2 * p] = pa.iin;
+    out[2 * p + 1] = pa.iout;
+  }
+  return 0;
 }
 
 /* Interior nodes k = 0..K of protons [first, first+count): out (count, K+1, 3) */
@@ -304,8 +436,11 @@ int or_nodes(const or_grid *g, const double *tab, const or_rec *r, int64_t first
              int32_t *out) {
   or_geom o;
   or_geometry(g, &o);
-  for (int64_t p = 0; p < count; ++p)
-    for (int k = 0; k <= o.K; ++k) or_node(g, &o, tab, r, first + p, mode, k, out + 3 * ((int64_t)p * (o.K + 1) + k));
+  for (int64_t p = 0; p < count; ++p) {
+    or_path pa;
+    or_path_of(g, &o, tab, r, first + p, mode, &pa);
+    for (int k = 0; k <= o.K; ++k) or_node(g, &o, &pa, r, first + p, mode, k, out + 3 * ((int64_t)p * (o.K + 1) + k));
+  }
   return 0;
 }
 
@@ -313,7 +448,9 @@ int or_nodes(const or_grid *g, const double *tab, const or_rec *r, int64_t first
 int or_polyline(const or_grid *g, const double *tab, const or_rec *r, int64_t i, int mode, int32_t *out) {
   or_geom o;
   or_geometry(g, &o);
-  for (int k = -o.E; k <= o.K + o.E; ++k) or_node(g, &o, tab, r, i, mode, k, out + 3 * (int64_t)(k + o.E));
+  or_path pa;
+  or_path_of(g, &o, tab, r, i, mode, &pa);
+  for (int k = -o.E; k <= o.K + o.E; ++k) or_node(g, &o, &pa, r, i, mode, k, out + 3 * (int64_t)(k + o.E));
   return o.K + 2 * o.E + 1;
 }
 
@@ -432,9 +569,11 @@ static void or_walk_row(const or_grid *g, const or_geom *o, const double *tab, c
   memset(&s, 0, sizeof s);
   row->n = 0;
   int32_t P[3], E[3];
-  or_node(g, o, tab, r, i, mode, -o->E, P);
+  or_path pa;
+  or_path_of(g, o, tab, r, i, mode, &pa);
+  or_node(g, o, &pa, r, i, mode, -o->E, P);
   for (int k = -o->E + 1; k <= o->K + o->E; ++k) {
-    or_node(g, o, tab, r, i, mode, k, E);
+    or_node(g, o, &pa, r, i, mode, k, E);
     or_segment(g, P, E, &s, row);
     P[0] = E[0];
     P[1] = E[1];
@@ -469,6 +608,46 @@ int64_t or_rows(const or_grid *g, const double *tab, const or_rec *r, int64_t fi
 }
 
 /* y_i = a_i . x for protons [first, first+count) (forward projection). */
+/*
+ * Space-carved object hull: every voxel on the row of a proton whose WEPL is
+ * at most wepl_max (it crossed air only) is outside the object; the hull is
+ * the rest of the grid, grown by `dilate` steps of the 6-neighbourhood.
+ * Rows are walked without a hull (g->hull is ignored). out: M bytes.
+ */
+int or_carve_hull(const or_grid *g, const double *tab, const or_rec *r, int64_t n, double wepl_max, int dilate,
+                  int mode, uint8_t *out) {
+  or_grid gp = *g;
+  gp.hull = NULL;
+  or_geom o;
+  or_geometry(&gp, &o);
+  const int64_t M = (int64_t)g->nx * g->ny * g->nz;
+  for (int64_t j = 0; j < M; ++j) out[j] = 1;
+  or_row row = {0};
+  for (int64_t i = 0; i < n; ++i) {
+    if (!(r->wepl[i] <= wepl_max)) continue;
+    or_walk_row(&gp, &o, tab, r, i, mode, &row);
+    for (int64_t q = 0; q < row.n; ++q) out[row.j[q]] = 0;
+  }
+  free(row.j);
+  free(row.l);
+  uint8_t *tmp = (uint8_t *)malloc((size_t)M);
+  for (int it = 0; it < dilate; ++it) {
+    memcpy(tmp, out, (size_t)M);
+    for (int64_t z = 0; z < g->nz; ++z)
+      for (int64_t y = 0; y < g->ny; ++y)
+        for (int64_t x = 0; x < g->nx; ++x) {
+          int64_t j = x + g->nx * (y + g->ny * z);
+          if (tmp[j]) continue;
+          int hit = (x > 0 && tmp[j - 1]) || (x + 1 < g->nx && tmp[j + 1]) || (y > 0 && tmp[j - g->nx]) ||
+                    (y + 1 < g->ny && tmp[j + g->nx]) || (z > 0 && tmp[j - (int64_t)g->nx * g->ny]) ||
+                    (z + 1 < g->nz && tmp[j + (int64_t)g->nx * g->ny]);
+          if (hit) out[j] = 1;
+        }
+  }
+  free(tmp);
+  return 0;
+}
+
 int or_project(const or_grid *g, const double *tab, const or_rec *r, int64_t first, int64_t count, int mode,
                const double *x, double *y) {
   or_geom o;
