@@ -170,6 +170,48 @@ PCT_API pct_status pct_load_histories(pct_ctx *ctx, const pct_histories *h, int 
 PCT_API pct_status pct_mlp_rows(pct_ctx *ctx, int64_t first, int64_t count, int64_t *row_ptr, int32_t *vox, float *len,
                         int64_t cap, int32_t *nodes, int64_t *needed);
 
+/* Object hull of the MLP. Sec. 2 cites the MLP of Schulte et al. 2008, which
+ * estimates the path inside the object and takes it straight outside. With a
+ * hull set, history i's path is its entry ray up to node iin, the MLP of the
+ * water layer between nodes iin and iout, then its exit ray. The layer has
+ * n = iout - iin node intervals; its FP64 table is built on the GPU for every
+ * n and rounded to FP32. The MLP starts from the ray positions at the hull
+ * and the measured slopes. iin is the first node k in [0, K] whose entry-ray
+ * point (t0 + st0 k du, at depth u_k) lies in a hull voxel; iout is the last
+ * node whose exit-ray point (t2 + st2 (k - K) du) does. A history with no such
+ * pair (iout <= iin) keeps the plane-to-plane MLP, like every history without
+ * a hull. The same fixed single-precision operation order as without a hull
+ * defines the rows bit for bit.
+ *
+ * pct_set_hull: mask = M bytes, nonzero = inside the object (device memory
+ * if on_device, else host); NULL removes the hull. Recomputes the ranges and
+ * the block weights of loaded histories; later loads use the hull too.
+ * Synchronises. Contexts with a hull are not accepted by pct_batch_create. */
+PCT_API pct_status pct_set_hull(pct_ctx *ctx, const uint8_t *mask, int on_device);
+
+/* Space-carved hull from the loaded histories: every voxel on the
+ * plane-to-plane row of a history with wepl <= wepl_max crossed only air and
+ * is outside; the hull is every other voxel, grown by `dilate` steps of the
+ * 6-neighbourhood (dilate >= 0; 1 restores boundary voxels that grazing
+ * histories carved). Then as pct_set_hull. Allocates 2 M bytes of scratch
+ * for the call. Synchronises. */
+PCT_API pct_status pct_carve_hull(pct_ctx *ctx, float wepl_max, int32_t dilate);
+
+/* Copy the current hull mask (M bytes) to host `out`. PCT_ERR_STATE without
+ * a hull. Synchronises. */
+PCT_API pct_status pct_get_hull(pct_ctx *ctx, uint8_t *out);
+
+/* Hull nodes (iin, iout) of histories [first, first+count) in load order,
+ * to host `out` (2 x count int32). PCT_ERR_STATE without a hull or
+ * histories. Synchronises. */
+PCT_API pct_status pct_hull_ranges(pct_ctx *ctx, int64_t first, int64_t count, int32_t *out);
+
+/* FP64 MLP table of a layer of n node intervals (1 <= n <= K; n = K is the
+ * slab between the planes, equal to pct_mlp_table), (n+1) x 4 doubles for
+ * nodes m = 0..n from the layer entry, computed on the GPU, to host `out`.
+ * Synchronises. */
+PCT_API pct_status pct_mlp_table_n(pct_ctx *ctx, int32_t n, double *out);
+
 /* Forward projection y[p] = a_i.x for histories i = first+p (load order) of
  * the loaded set, with the current x and the fused kernel's arithmetic
  * (compensated unless PCT_FLAG_NO_KAHAN). y: DEVICE, count floats.

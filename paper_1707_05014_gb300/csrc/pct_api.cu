@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/pct.h"
 #include "pct_ctx.h"
@@ -53,6 +54,8 @@ void free_records(pct_ctx* c) {
   c->inv_s = nullptr;
   if (c->where) cudaFree(c->where);
   c->where = nullptr;
+  if (c->hull_range) cudaFree(c->hull_range);
+  c->hull_range = nullptr;
   c->rec = Rec{};
   c->n = 0;
   c->loaded = false;
@@ -63,6 +66,20 @@ int64_t block_lo(const pct_ctx* c, int b) { return (int64_t)b * c->n / c->cfg.n_
 pct_status sync_and_check(pct_ctx* c) {
   PCT_CK(cudaStreamSynchronize(c->stream));
   PCT_CK(cudaGetLastError());
+  return PCT_OK;
+}
+
+// DROP block weights (Sec. 2.1): s_j = runs of block b in voxel j; inv_s
+// holds 1/s_j (0 where the block does not touch voxel j).
+pct_status block_weights(pct_ctx* c) {
+  for (int b = 0; b < c->cfg.n_blocks; ++b) {
+    const int64_t lo = block_lo(c, b), hi = block_lo(c, b + 1);
+    PCT_CK(cudaMemsetAsync(c->cnt, 0, (size_t)c->M * sizeof(unsigned int), c->stream));
+    PCT_CK(pct::launch_count(c->geo, c->rec, c->tab32, pct::hull_view(c), lo, hi - lo, c->cnt, c->cfg.cta_threads,
+                             c->stream));
+    PCT_CK(pct::launch_inv_counts(c->cnt, c->inv_s + (size_t)b * c->M, c->M, c->stream));
+    c->launches += 2;
+  }
   return PCT_OK;
 }
 
@@ -249,6 +266,8 @@ pct_status pct_destroy(pct_ctx* c) {
   cudaFree(c->tv_xp);
   cudaFree(c->tv_acc);
   cudaFree(c->tv_state);
+  cudaFree(c->hull_mask);
+  cudaFree(c->fam32);
   if (c->ev) {
     for (int i = 0; i < 3 * c->cfg.n_blocks; ++i) cudaEventDestroy(c->ev[i]);
     delete[] c->ev;
@@ -383,14 +402,16 @@ pct_status pct_load_histories(pct_ctx* c, const pct_histories* h, int flags, int
     return fail(PCT_ERR_INVALID_DATA, "history %lld failed validation", (long long)fb);
   }
 
-  // DROP block weights: s_j = runs of block b in voxel j; store 1/s_j
+  // hull ranges of the stored histories, then the DROP block weights
+  if (c->hull_mask) {
+    PCT_ALLOC(c->hull_range, (size_t)n * sizeof(int32_t));
+    PCT_CK(pct::launch_hull_ranges(c->geo, c->rec, n, c->hull_mask, c->hull_range, c->stream));
+    c->launches += 1;
+  }
   PCT_ALLOC(c->inv_s, (size_t)B * c->M * sizeof(float));
-  for (int b = 0; b < B; ++b) {
-    const int64_t lo = block_lo(c, b), hi = block_lo(c, b + 1);
-    PCT_CK(cudaMemsetAsync(c->cnt, 0, (size_t)c->M * sizeof(unsigned int), c->stream));
-    PCT_CK(pct::launch_count(c->geo, c->rec, c->tab32, lo, hi - lo, c->cnt, c->cfg.cta_threads, c->stream));
-    PCT_CK(pct::launch_inv_counts(c->cnt, c->inv_s + (size_t)b * c->M, c->M, c->stream));
-    c->launches += 2;
+  {
+    pct_status st = block_weights(c);
+    if (st != PCT_OK) return st;
   }
   PCT_CK(cudaMemsetAsync(c->x, 0, (size_t)c->M * sizeof(float), c->stream));
   PCT_CK(cudaMemsetAsync(c->delta, 0, (size_t)c->M * sizeof(float), c->stream));
@@ -398,6 +419,110 @@ pct_status pct_load_histories(pct_ctx* c, const pct_histories* h, int flags, int
   pct_status st = sync_and_check(c);  // scratch is freed after the stream is idle
   if (st != PCT_OK) return st;
   c->loaded = true;
+  return PCT_OK;
+}
+
+pct_status pct_set_hull(pct_ctx* c, const uint8_t* mask, int on_device) {
+  if (!c) return fail(PCT_ERR_INVALID_ARG, "ctx is NULL");
+  PCT_CK(cudaSetDevice(c->device));
+  PCT_CK(cudaStreamSynchronize(c->stream));
+  if (c->sweep) cudaGraphExecDestroy(c->sweep);  // the sweep's kernels change
+  c->sweep = nullptr;
+  if (!mask) {
+    cudaFree(c->hull_mask);
+    cudaFree(c->hull_range);
+    c->hull_mask = nullptr;
+    c->hull_range = nullptr;
+  } else {
+    if (!c->hull_mask) PCT_ALLOC(c->hull_mask, (size_t)c->M);
+    if (!c->fam32) {
+      PCT_ALLOC(c->fam32, (size_t)pct::family_offset(c->K + 1) * sizeof(float4));
+      PCT_CK(pct::launch_mlp_family(c->R, c->du, c->K, c->fam32, 0, nullptr, c->stream));
+      c->launches += 1;
+    }
+    PCT_CK(cudaMemcpyAsync(c->hull_mask, mask, (size_t)c->M,
+                           on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+    if (c->loaded) {
+      if (!c->hull_range) PCT_ALLOC(c->hull_range, (size_t)c->n * sizeof(int32_t));
+      PCT_CK(pct::launch_hull_ranges(c->geo, c->rec, c->n, c->hull_mask, c->hull_range, c->stream));
+      c->launches += 1;
+    }
+  }
+  if (c->loaded) {
+    pct_status st = block_weights(c);
+    if (st != PCT_OK) return st;
+  }
+  return sync_and_check(c);
+}
+
+pct_status pct_carve_hull(pct_ctx* c, float wepl_max, int32_t dilate) {
+  if (!c) return fail(PCT_ERR_INVALID_ARG, "ctx is NULL");
+  if (!c->loaded) return fail(PCT_ERR_STATE, "no histories loaded");
+  if (dilate < 0) return fail(PCT_ERR_INVALID_ARG, "dilate must be >= 0");
+  PCT_CK(cudaSetDevice(c->device));
+  uint8_t *out = nullptr, *tmp = nullptr;
+  cudaError_t e = cudaMalloc((void**)&out, (size_t)c->M);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&tmp, (size_t)c->M);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    cudaFree(out);
+    return fail(PCT_ERR_NO_MEMORY, "carving scratch (%lld bytes)", (long long)c->M);
+  }
+  e = pct::launch_carve_hull(c->geo, c->rec, c->tab32, c->n, wepl_max, dilate, out, tmp, c->stream);
+  c->launches += 1 + dilate;
+  pct_status st = e == cudaSuccess ? pct_set_hull(c, out, 1) : fail(PCT_ERR_CUDA, "carving: %s", cudaGetErrorString(e));
+  cudaStreamSynchronize(c->stream);
+  cudaFree(out);
+  cudaFree(tmp);
+  return st;
+}
+
+pct_status pct_get_hull(pct_ctx* c, uint8_t* out) {
+  if (!c || !out) return fail(PCT_ERR_INVALID_ARG, "ctx or out is NULL");
+  if (!c->hull_mask) return fail(PCT_ERR_STATE, "no hull set");
+  PCT_CK(cudaSetDevice(c->device));
+  PCT_CK(cudaMemcpyAsync(out, c->hull_mask, (size_t)c->M, cudaMemcpyDeviceToHost, c->stream));
+  return sync_and_check(c);
+}
+
+pct_status pct_hull_ranges(pct_ctx* c, int64_t first, int64_t count, int32_t* out) {
+  if (!c || (count > 0 && !out)) return fail(PCT_ERR_INVALID_ARG, "ctx or out is NULL");
+  if (!c->loaded) return fail(PCT_ERR_STATE, "no histories loaded");
+  if (!c->hull_mask) return fail(PCT_ERR_STATE, "no hull set");
+  if (first < 0 || count < 0 || first + count > c->n) return fail(PCT_ERR_INVALID_ARG, "range outside [0, n)");
+  PCT_CK(cudaSetDevice(c->device));
+  std::vector<int32_t> stored;
+  std::vector<int64_t> where;
+  stored.resize((size_t)c->n);
+  PCT_CK(cudaMemcpyAsync(stored.data(), c->hull_range, (size_t)c->n * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                         c->stream));
+  if (c->where) {
+    where.resize((size_t)c->n);
+    PCT_CK(cudaMemcpyAsync(where.data(), c->where, (size_t)c->n * sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
+  }
+  pct_status st = sync_and_check(c);
+  if (st != PCT_OK) return st;
+  for (int64_t p = 0; p < count; ++p) {
+    const int32_t v = stored[(size_t)(c->where ? where[(size_t)(first + p)] : first + p)];
+    out[2 * p] = v & 0xffff;
+    out[2 * p + 1] = v >> 16;
+  }
+  return PCT_OK;
+}
+
+pct_status pct_mlp_table_n(pct_ctx* c, int32_t n, double* out) {
+  if (!c || !out) return fail(PCT_ERR_INVALID_ARG, "ctx or out is NULL");
+  if (n < 1 || n > c->K) return fail(PCT_ERR_INVALID_ARG, "n must be in [1, K]");
+  PCT_CK(cudaSetDevice(c->device));
+  double* d = nullptr;
+  PCT_ALLOC(d, (size_t)(n + 1) * 4 * sizeof(double));
+  cudaError_t e = pct::launch_mlp_family(c->R, c->du, c->K, nullptr, n, d, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, d, (size_t)(n + 1) * 4 * sizeof(double), cudaMemcpyDeviceToHost,
+                                            c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  cudaFree(d);
+  c->launches += 1;
+  if (e != cudaSuccess) return fail(PCT_ERR_CUDA, "layer table: %s", cudaGetErrorString(e));
   return PCT_OK;
 }
 
@@ -409,7 +534,8 @@ pct_status pct_mlp_rows(pct_ctx* c, int64_t first, int64_t count, int64_t* row_p
   if (first < 0 || count < 0 || first + count > c->n) return fail(PCT_ERR_INVALID_ARG, "range outside [0, n)");
   if (cap < 0 || (cap > 0 && (!vox || !len))) return fail(PCT_ERR_INVALID_ARG, "bad row buffers");
   PCT_CK(cudaSetDevice(c->device));
-  PCT_CK(pct::launch_row_counts(c->geo, c->rec, c->tab32, first, count, c->where, row_ptr, c->stream));
+  PCT_CK(pct::launch_row_counts(c->geo, c->rec, c->tab32, pct::hull_view(c), first, count, c->where, row_ptr,
+                                c->stream));
   PCT_CK(pct::launch_scan_rows(row_ptr, count, c->stream));
   c->launches += 2;
   int64_t total = 0;
@@ -418,7 +544,8 @@ pct_status pct_mlp_rows(pct_ctx* c, int64_t first, int64_t count, int64_t* row_p
   if (needed) *needed = total;
   if (total > cap) return fail(PCT_ERR_CAPACITY, "rows need %lld runs, capacity %lld", (long long)total,
                                (long long)cap);
-  PCT_CK(pct::launch_row_fill(c->geo, c->rec, c->tab32, first, count, c->where, row_ptr, vox, len, nodes,
+  PCT_CK(pct::launch_row_fill(c->geo, c->rec, c->tab32, pct::hull_view(c), first, count, c->where, row_ptr, vox,
+                              len, nodes,
                               c->stream));
   c->launches += 1;
   return sync_and_check(c);
@@ -429,7 +556,8 @@ pct_status pct_project(pct_ctx* c, int64_t first, int64_t count, float* y) {
   if (!c->loaded) return fail(PCT_ERR_STATE, "no histories loaded");
   if (first < 0 || count < 0 || first + count > c->n) return fail(PCT_ERR_INVALID_ARG, "range outside [0, n)");
   PCT_CK(cudaSetDevice(c->device));
-  PCT_CK(pct::launch_project(c->geo, c->rec, c->tab32, first, count, c->where, c->x, c->cfg.flags, y, c->stream));
+  PCT_CK(pct::launch_project(c->geo, c->rec, c->tab32, pct::hull_view(c), first, count, c->where, c->x, c->cfg.flags,
+                             y, c->stream));
   c->launches += 1;
   return PCT_OK;
 }
@@ -440,7 +568,8 @@ pct_status pct_residual(pct_ctx* c, int64_t stride, double* sum_sq) {
   if (!c->loaded) return fail(PCT_ERR_STATE, "no histories loaded");
   PCT_CK(cudaSetDevice(c->device));
   PCT_CK(cudaMemsetAsync(c->acc, 0, sizeof(double), c->stream));
-  PCT_CK(pct::launch_residual(c->geo, c->rec, c->tab32, c->n, stride, c->x, c->cfg.flags, c->acc, c->stream));
+  PCT_CK(pct::launch_residual(c->geo, c->rec, c->tab32, pct::hull_view(c), c->n, stride, c->x, c->cfg.flags, c->acc,
+                              c->stream));
   c->launches += 1;
   PCT_CK(cudaMemcpyAsync(sum_sq, c->acc, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   return sync_and_check(c);
@@ -453,7 +582,8 @@ pct_status pct_block_counts(pct_ctx* c, int32_t block, float* out) {
   PCT_CK(cudaSetDevice(c->device));
   const int64_t lo = block_lo(c, block), hi = block_lo(c, block + 1);
   PCT_CK(cudaMemsetAsync(c->cnt, 0, (size_t)c->M * sizeof(unsigned int), c->stream));
-  PCT_CK(pct::launch_count(c->geo, c->rec, c->tab32, lo, hi - lo, c->cnt, c->cfg.cta_threads, c->stream));
+  PCT_CK(pct::launch_count(c->geo, c->rec, c->tab32, pct::hull_view(c), lo, hi - lo, c->cnt, c->cfg.cta_threads,
+                           c->stream));
   PCT_CK(pct::launch_counts_to_float(c->cnt, out, c->M, c->stream));
   c->launches += 2;
   return PCT_OK;
@@ -496,7 +626,8 @@ static pct_status build_sweep_graph(pct_ctx* c) {
                               c->tv_state, s);
       if (err == cudaSuccess && c->ev) err = cudaEventRecordWithFlags(c->ev[3 * b], s, cudaEventRecordExternal);
       if (err == cudaSuccess)
-        err = pct::launch_drop_fused(c->geo, c->rec, c->tab32, lo, hi - lo, c->x, c->delta, c->cfg.lambda,
+        err = pct::launch_drop_fused(c->geo, c->rec, c->tab32, pct::hull_view(c), lo, hi - lo, c->x, c->delta,
+                                     c->cfg.lambda,
                                      c->cfg.flags, c->cfg.cta_threads, s);
       if (err == cudaSuccess && c->ev) err = cudaEventRecordWithFlags(c->ev[3 * b + 1], s, cudaEventRecordExternal);
       if (err == cudaSuccess)

@@ -273,8 +273,8 @@ pct_status enqueue_branches(pct_batch* b, int n_sweeps, cudaStream_t s) {
     for (int sw = 0; sw < n_sweeps; ++sw)
       for (int blk = 0; blk < c->cfg.n_blocks; ++blk) {
         const int64_t lo = pct::block_first(c, blk), hi = pct::block_first(c, blk + 1);
-        PCT_BCK(pct::launch_drop_fused(c->geo, c->rec, c->tab32, lo, hi - lo, c->x, c->delta, c->cfg.lambda,
-                                       c->cfg.flags, c->cfg.cta_threads, bs));
+        PCT_BCK(pct::launch_drop_fused(c->geo, c->rec, c->tab32, pct::Hull{}, lo, hi - lo, c->x, c->delta,
+                                       c->cfg.lambda, c->cfg.flags, c->cfg.cta_threads, bs));
         PCT_BCK(pct::launch_drop_apply(c->x, c->delta, c->inv_s + (size_t)blk * c->M, c->M, clamp,
                                        c->cfg.clamp_min, bs));
         b->launches += 2;
@@ -333,6 +333,7 @@ pct_status pct_batch_create(pct_batch** out, pct_ctx* const* ctxs, int32_t n, co
     if (ctxs[r]->device != ctxs[0]->device) return bfail(PCT_ERR_INVALID_ARG, "contexts on different devices");
     if (ctxs[r]->cfg.flags & PCT_FLAG_CARP) return bfail(PCT_ERR_INVALID_ARG, "CARP contexts are not batched");
     if (ctxs[r]->cfg.tvs_beta0 > 0.f) return bfail(PCT_ERR_INVALID_ARG, "TVS contexts are not batched");
+    if (ctxs[r]->hull_mask) return bfail(PCT_ERR_INVALID_ARG, "contexts with an object hull are not batched");
   }
   pct_batch* b = new pct_batch();
   b->device = ctxs[0]->device;

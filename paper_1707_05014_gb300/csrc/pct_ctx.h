@@ -37,6 +37,9 @@ struct pct_ctx {
   float* tv_xp = nullptr;       // TVS: trial image
   double* tv_acc = nullptr;     // TVS: |g|^2, TV(x), TV(x')
   pct::TvState* tv_state = nullptr;
+  uint8_t* hull_mask = nullptr;   // object hull, M bytes (null: no hull)
+  int32_t* hull_range = nullptr;  // per stored history: iin | iout << 16 (with a hull and histories)
+  float4* fam32 = nullptr;        // MLP tables of every hull thickness (with a hull)
   cudaGraphExec_t sweep = nullptr;
   cudaEvent_t* ev = nullptr;  // 3 per block (profiling): fused start, fused end, apply end
   bool swept = false;
@@ -45,6 +48,8 @@ struct pct_ctx {
 };
 
 namespace pct {
+// The hull as the kernels see it (range null: no hull).
+inline Hull hull_view(const pct_ctx* c) { return Hull{c->hull_mask ? c->hull_range : nullptr, c->fam32}; }
 // First history of DROP block b: b * n / B (blocks are contiguous ranges).
 inline int64_t block_first(const pct_ctx* c, int b) { return (int64_t)b * c->n / c->cfg.n_blocks; }
 }  // namespace pct

@@ -29,17 +29,15 @@ __device__ __forceinline__ float ld_weak(const float* p) {
 // kernel applies block updates between work items), so x is read with plain
 // weak loads instead of the read-only path (which assumes data that never
 // changes during the launch).
-template <bool kCoherent = false>
-__device__ __forceinline__ void drop_history(const Geo& g, const float4* __restrict__ tab, const Rec& r, int64_t i,
-                                             const float* __restrict__ x, float* __restrict__ delta, float lambda,
-                                             int flags) {
+template <bool kCoherent, class Walk>
+__device__ __forceinline__ void drop_history_core(const RecV& v, Walk&& walk, const float* __restrict__ x,
+                                                  float* __restrict__ delta, float lambda, int flags) {
   auto xload = [&](int j) { return kCoherent ? ld_weak(x + j) : __ldg(x + j); };
-  const RecV v = load_rec(r, i);
   // The walk only records the row; the gather of x and the scatter run as two
   // replays of the recorded row, outside the walk's divergent crossing loop.
   uint2 row[kRowCap];
   int nrow = 0;
-  walk_proton(g, tab, v, [&](int j, float l) {
+  walk([&](int j, float l) {
     if (nrow < kRowCap) row[nrow] = make_uint2((unsigned)j, __float_as_uint(l));
     ++nrow;
   });
@@ -65,7 +63,7 @@ __device__ __forceinline__ void drop_history(const Geo& g, const float4* __restr
       }
     }
   } else {
-    walk_proton(g, tab, v, [&](int j, float l) {
+    walk([&](int j, float l) {
       if (flags & 2) {
         y = __fmaf_rn(l, xload(j), y);
       } else {
@@ -86,8 +84,26 @@ __device__ __forceinline__ void drop_history(const Geo& g, const float4* __restr
       atomicAdd(delta + e.x, __uint_as_float(e.y) * ri);
     }
   } else {
-    walk_proton(g, tab, v, [&](int j, float l) { atomicAdd(delta + j, l * ri); });
+    walk([&](int j, float l) { atomicAdd(delta + j, l * ri); });
   }
+}
+
+template <bool kCoherent = false>
+__device__ __forceinline__ void drop_history(const Geo& g, const float4* __restrict__ tab, const Rec& r, int64_t i,
+                                             const float* __restrict__ x, float* __restrict__ delta, float lambda,
+                                             int flags) {
+  const RecV v = load_rec(r, i);
+  drop_history_core<kCoherent>(v, [&](auto&& visit) { walk_proton(g, tab, v, visit); }, x, delta, lambda, flags);
+}
+
+// The same with an object hull (the MLP between the proton's hull nodes).
+__device__ __forceinline__ void drop_history_hull(const Geo& g, const Hull& hull, const Rec& r, int64_t i,
+                                                  const float* __restrict__ x, float* __restrict__ delta, float lambda,
+                                                  int flags) {
+  const RecV v = load_rec(r, i);
+  const int32_t range = __ldg(hull.range + i);
+  drop_history_core<false>(v, [&](auto&& visit) { walk_proton_hull(g, hull.fam, range, v, visit); }, x, delta, lambda,
+                           flags);
 }
 
 // x_j += delta_j / s_j (optionally clamped), delta_j = 0. kCoherent: x and

@@ -34,6 +34,19 @@ struct Rec {
   const float *t0, *v0, *st0, *sv0, *t2, *v2, *st2, *sv2, *wepl, *cphi, *sphi;
 };
 
+// Object hull of the MLP (device pointers; range == nullptr: no hull, every
+// proton's MLP spans the measurement planes). range[i] = iin | iout << 16 for
+// stored history i: its MLP runs between nodes iin and iout with the table of
+// a layer of n = iout - iin node intervals, fam + family_offset(n).
+struct Hull {
+  const int32_t* range;
+  const float4* fam;
+};
+
+// Start of the table of thickness n (entries m = 0..n) in the table family:
+// the tables of thickness 1 .. n-1 hold 2 + 3 + ... + n entries.
+__host__ __device__ constexpr int64_t family_offset(int n) { return (int64_t)(n - 1) * (n + 2) / 2; }
+
 // Total-variation superiorization parameters and device state.
 struct TvsParams {
   float beta0, alpha, eps;
@@ -48,6 +61,18 @@ struct TvState {
 // Launchers (pct_kernels.cu / pct_table.cu). All enqueue on `s` and return
 // the launch error (cudaSuccess when queued).
 cudaError_t launch_mlp_table(double R, double du, int K, double* tab64, float4* tab32, cudaStream_t s);
+// Table family of every hull thickness n = 1..K into fam (family_offset(K+1)
+// float4, may be null); with tab64 non-null also the FP64 table of n = n64
+// ((n64+1) x 4 doubles).
+cudaError_t launch_mlp_family(double R, double du, int K, float4* fam, int n64, double* tab64, cudaStream_t s);
+// range[i] for stored histories [0, n) against the hull mask (M bytes).
+cudaError_t launch_hull_ranges(const Geo& g, const Rec& r, int64_t n, const uint8_t* mask, int32_t* range,
+                               cudaStream_t s);
+// Space carving: out[j] = 0 for every voxel on the (hull-free) row of a stored
+// history with wepl <= wepl_max, else 1; then `dilate` 6-neighbour growth
+// steps (tmp: M bytes of scratch).
+cudaError_t launch_carve_hull(const Geo& g, const Rec& r, const float4* tab, int64_t n, float wepl_max, int dilate,
+                              uint8_t* out, uint8_t* tmp, cudaStream_t s);
 cudaError_t launch_validate(const Rec& r, int64_t n, int64_t base, float pos_limit, unsigned long long* first_bad,
                             cudaStream_t s);
 // Order n records of one block by (angle bin, entry lateral bin) into
@@ -57,11 +82,11 @@ cudaError_t launch_sort_block(const Rec& src, int64_t n, int64_t base, float lat
                               unsigned* key, unsigned* hist, unsigned* order, cudaStream_t s);
 // Copy n records into dst_rec[base ..) in input order (where as above).
 cudaError_t launch_copy_block(const Rec& src, int64_t n, int64_t base, Rec dst_rec, int64_t* where, cudaStream_t s);
-cudaError_t launch_count(const Geo& g, const Rec& r, const float4* tab, int64_t first, int64_t count,
+cudaError_t launch_count(const Geo& g, const Rec& r, const float4* tab, const Hull& hull, int64_t first, int64_t count,
                          unsigned int* cnt, int threads, cudaStream_t s);
 cudaError_t launch_inv_counts(const unsigned int* cnt, float* inv_s, int64_t M, cudaStream_t s);
 cudaError_t launch_counts_to_float(const unsigned int* cnt, float* out, int64_t M, cudaStream_t s);
-cudaError_t launch_drop_fused(const Geo& g, const Rec& r, const float4* tab, int64_t first, int64_t count,
+cudaError_t launch_drop_fused(const Geo& g, const Rec& r, const float4* tab, const Hull& hull, int64_t first, int64_t count,
                               const float* x, float* delta, float lambda, int flags, int threads, cudaStream_t s);
 cudaError_t launch_drop_apply(float* x, float* delta, const float* inv_s, int64_t M, int clamp, float clamp_min,
                               cudaStream_t s);
@@ -78,15 +103,15 @@ cudaError_t launch_carp_finish(float* x, const float* x0, float* sum, float* tou
 cudaError_t launch_tvs(float* x, int nx, int ny, int nz, const TvsParams& p, float* g, float* xp, double* acc,
                        TvState* st, cudaStream_t s);
 // y[p] = a_i.x for histories first+p (load order through `where`, if given).
-cudaError_t launch_project(const Geo& g, const Rec& r, const float4* tab, int64_t first, int64_t count,
+cudaError_t launch_project(const Geo& g, const Rec& r, const float4* tab, const Hull& hull, int64_t first, int64_t count,
                            const int64_t* where, const float* x, int flags, float* y, cudaStream_t s);
 // *acc += sum over stored histories i = 0, stride, ... < n of (b_i - a_i.x)^2.
-cudaError_t launch_residual(const Geo& g, const Rec& r, const float4* tab, int64_t n, int64_t stride, const float* x,
+cudaError_t launch_residual(const Geo& g, const Rec& r, const float4* tab, const Hull& hull, int64_t n, int64_t stride, const float* x,
                             int flags, double* acc, cudaStream_t s);
-cudaError_t launch_row_counts(const Geo& g, const Rec& r, const float4* tab, int64_t first, int64_t count,
+cudaError_t launch_row_counts(const Geo& g, const Rec& r, const float4* tab, const Hull& hull, int64_t first, int64_t count,
                               const int64_t* where, int64_t* row_ptr, cudaStream_t s);
 cudaError_t launch_scan_rows(int64_t* row_ptr, int64_t count, cudaStream_t s);
-cudaError_t launch_row_fill(const Geo& g, const Rec& r, const float4* tab, int64_t first, int64_t count,
+cudaError_t launch_row_fill(const Geo& g, const Rec& r, const float4* tab, const Hull& hull, int64_t first, int64_t count,
                             const int64_t* where, const int64_t* row_ptr, int32_t* vox, float* len, int32_t* nodes,
                             cudaStream_t s);
 

@@ -32,14 +32,14 @@ __global__ void validate_kernel(Rec r, int64_t n, int64_t base, float pos_limit,
   if (bad) atomicMin(first_bad, (unsigned long long)(base + i));
 }
 
-__global__ void count_kernel(Geo g, Rec r, const float4* __restrict__ tab_g, int64_t first, int64_t count,
-                             unsigned int* __restrict__ cnt) {
+__global__ void count_kernel(Geo g, Rec r, const float4* __restrict__ tab_g, Hull hull, int64_t first,
+                             int64_t count, unsigned int* __restrict__ cnt) {
   extern __shared__ float4 tab[];
   load_table(tab_g, tab, g.K + 1);
   int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= count) return;
   const RecV v = load_rec(r, first + p);
-  walk_proton(g, tab, v, [&](int j, float) { atomicAdd(cnt + j, 1u); });
+  walk_any(g, tab, hull, first + p, v, [&](int j, float) { atomicAdd(cnt + j, 1u); });
 }
 
 __global__ void inv_counts_kernel(const unsigned int* __restrict__ cnt, float* __restrict__ inv_s, int64_t M) {
@@ -66,16 +66,25 @@ __global__ void __launch_bounds__(128, 9) drop_fused_kernel(Geo g, Rec r, const 
   drop_history(g, tab, r, first + p, x, delta, lambda, flags);
 }
 
+// The same with an object hull (see walk_proton_hull).
+__global__ void __launch_bounds__(128, 9) drop_fused_hull_kernel(Geo g, Rec r, Hull hull, int64_t first, int64_t count,
+                                                               const float* __restrict__ x, float* __restrict__ delta,
+                                                               float lambda, int flags) {
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= count) return;
+  drop_history_hull(g, hull, r, first + p, x, delta, lambda, flags);
+}
+
 // Compensated a_i.x (or plain with flags & 2), the arithmetic of the fused
 // kernel's first pass. Returns y - c (Kahan: the true sum is y - c).
-__device__ __forceinline__ float project_history(const Geo& g, const float4* __restrict__ tab, const RecV& v,
-                                                 const float* __restrict__ x, int flags) {
+__device__ __forceinline__ float project_history(const Geo& g, const float4* __restrict__ tab, const Hull& hull,
+                                                 int64_t i, const RecV& v, const float* __restrict__ x, int flags) {
   float y = 0.f, c = 0.f;
   if (flags & 2) {
-    walk_proton(g, tab, v, [&](int j, float l) { y = __fmaf_rn(l, __ldg(x + j), y); });
+    walk_any(g, tab, hull, i, v, [&](int j, float l) { y = __fmaf_rn(l, __ldg(x + j), y); });
     return y;
   }
-  walk_proton(g, tab, v, [&](int j, float l) {
+  walk_any(g, tab, hull, i, v, [&](int j, float l) {
     const float term = __fsub_rn(__fmul_rn(l, __ldg(x + j)), c);
     const float t = __fadd_rn(y, term);
     c = __fsub_rn(__fsub_rn(t, y), term);
@@ -84,22 +93,23 @@ __device__ __forceinline__ float project_history(const Geo& g, const float4* __r
   return __fsub_rn(y, c);
 }
 
-__global__ void __launch_bounds__(128) project_kernel(Geo g, Rec r, const float4* __restrict__ tab_g, int64_t first,
-                                                      int64_t count, const int64_t* __restrict__ where,
+__global__ void __launch_bounds__(128) project_kernel(Geo g, Rec r, const float4* __restrict__ tab_g, Hull hull,
+                                                      int64_t first, int64_t count, const int64_t* __restrict__ where,
                                                       const float* __restrict__ x, int flags, float* __restrict__ y) {
   extern __shared__ float4 tab[];
   load_table(tab_g, tab, g.K + 1);
   int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= count) return;
-  const RecV v = load_rec(r, where ? where[first + p] : first + p);
-  y[p] = project_history(g, tab, v, x, flags);
+  const int64_t i = where ? where[first + p] : first + p;
+  const RecV v = load_rec(r, i);
+  y[p] = project_history(g, tab, hull, i, v, x, flags);
 }
 
 // sum over i = 0, stride, 2 stride, ... < n of (b_i - a_i.x)^2: per-CTA
 // double reduction, one double atomic per CTA.
-__global__ void __launch_bounds__(128) residual_kernel(Geo g, Rec r, const float4* __restrict__ tab_g, int64_t n,
-                                                       int64_t stride, const float* __restrict__ x, int flags,
-                                                       double* acc) {
+__global__ void __launch_bounds__(128) residual_kernel(Geo g, Rec r, const float4* __restrict__ tab_g, Hull hull,
+                                                       int64_t n, int64_t stride, const float* __restrict__ x,
+                                                       int flags, double* acc) {
   extern __shared__ float4 tab[];
   __shared__ double part[4];
   load_table(tab_g, tab, g.K + 1);
@@ -107,7 +117,7 @@ __global__ void __launch_bounds__(128) residual_kernel(Geo g, Rec r, const float
   double rr = 0.0;
   if (p < n) {
     const RecV v = load_rec(r, p);
-    const double res = (double)v.wepl - (double)project_history(g, tab, v, x, flags);
+    const double res = (double)v.wepl - (double)project_history(g, tab, hull, p, v, x, flags);
     rr = res * res;
   }
   for (int o = 16; o > 0; o >>= 1) rr += __shfl_down_sync(0xffffffffu, rr, o);
@@ -262,15 +272,16 @@ __global__ void tv_reset_kernel(double* acc, TvState* st) {
   st->accepted = 0;
 }
 
-__global__ void row_count_kernel(Geo g, Rec r, const float4* __restrict__ tab_g, int64_t first, int64_t count,
-                                 const int64_t* __restrict__ where, int64_t* __restrict__ row_ptr) {
+__global__ void row_count_kernel(Geo g, Rec r, const float4* __restrict__ tab_g, Hull hull, int64_t first,
+                                 int64_t count, const int64_t* __restrict__ where, int64_t* __restrict__ row_ptr) {
   extern __shared__ float4 tab[];
   load_table(tab_g, tab, g.K + 1);
   int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= count) return;
-  const RecV v = load_rec(r, where ? where[first + p] : first + p);
+  const int64_t i = where ? where[first + p] : first + p;
+  const RecV v = load_rec(r, i);
   int64_t n = 0;
-  walk_proton(g, tab, v, [&](int, float) { ++n; });
+  walk_any(g, tab, hull, i, v, [&](int, float) { ++n; });
   row_ptr[p + 1] = n;
 }
 
@@ -302,24 +313,26 @@ __global__ void __launch_bounds__(1024) scan_rows_kernel(int64_t* __restrict__ r
   }
 }
 
-__global__ void row_fill_kernel(Geo g, Rec r, const float4* __restrict__ tab_g, int64_t first, int64_t count,
-                                const int64_t* __restrict__ where, const int64_t* __restrict__ row_ptr,
+__global__ void row_fill_kernel(Geo g, Rec r, const float4* __restrict__ tab_g, Hull hull, int64_t first,
+                                int64_t count, const int64_t* __restrict__ where, const int64_t* __restrict__ row_ptr,
                                 int32_t* __restrict__ vox, float* __restrict__ len, int32_t* __restrict__ nodes) {
   extern __shared__ float4 tab[];
   load_table(tab_g, tab, g.K + 1);
   int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= count) return;
-  const RecV v = load_rec(r, where ? where[first + p] : first + p);
+  const int64_t i = where ? where[first + p] : first + p;
+  const RecV v = load_rec(r, i);
   int64_t o = row_ptr[p];
-  walk_proton(g, tab, v, [&](int j, float l) {
+  walk_any(g, tab, hull, i, v, [&](int j, float l) {
     vox[o] = j;
     len[o] = l;
     ++o;
   });
   if (nodes) {
     int32_t* out = nodes + (int64_t)p * (g.K + 1) * 3;
+    const int32_t range = hull.range ? hull.range[i] : 0;
     for (int k = 0; k <= g.K; ++k) {
-      const int3 Q = node_q(g, tab, v, k);
+      const int3 Q = hull.range ? node_q_hull(g, hull.fam, range, v, k) : node_q(g, tab, v, k);
       out[3 * k + 0] = Q.x;
       out[3 * k + 1] = Q.y;
       out[3 * k + 2] = Q.z;
@@ -327,6 +340,64 @@ __global__ void row_fill_kernel(Geo g, Rec r, const float4* __restrict__ tab_g, 
   }
 }
 
+
+// ---- object hull: per-history MLP range and space carving -----------------
+
+// range[i] = iin | iout << 16: iin = the first node k in [0, K] whose entry-ray
+// point lies in a hull voxel, iout = the last node whose exit-ray point does;
+// (0, K) when either is missing or iout <= iin (the proton misses the hull).
+__global__ void hull_range_kernel(Geo g, Rec r, int64_t n, const uint8_t* __restrict__ mask,
+                                  int32_t* __restrict__ range) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const RecV v = load_rec(r, i);
+  auto in_hull = [&](float t, float vv, int k) {
+    const int3 Q = quantise3(node_grid(g, v, __fmaf_rn((float)k, g.du, g.u0), t, vv));
+    const int ix = floor_q(Q.x), iy = floor_q(Q.y), iz = floor_q(Q.z);
+    if ((unsigned)ix >= (unsigned)g.nx || (unsigned)iy >= (unsigned)g.ny || (unsigned)iz >= (unsigned)g.nz) return false;
+    return mask[ix + (int64_t)g.nx * (iy + (int64_t)g.ny * iz)] != 0;
+  };
+  int iin = -1, iout = -1;
+  for (int k = 0; k <= g.K && iin < 0; ++k) {
+    const float dk = __fmul_rn((float)k, g.du);
+    if (in_hull(__fmaf_rn(v.st0, dk, v.t0), __fmaf_rn(v.sv0, dk, v.v0), k)) iin = k;
+  }
+  for (int k = g.K; k >= 0 && iout < 0; --k) {
+    const float dk = __fmul_rn((float)(k - g.K), g.du);
+    if (in_hull(__fmaf_rn(v.st2, dk, v.t2), __fmaf_rn(v.sv2, dk, v.v2), k)) iout = k;
+  }
+  if (iin < 0 || iout < 0 || iout <= iin) {
+    iin = 0;
+    iout = g.K;
+  }
+  range[i] = iin | (iout << 16);
+}
+
+// out[j] = 0 on the row of every history with wepl <= wepl_max (voxels its
+// hull-free path crosses are air); out starts at 1.
+__global__ void carve_kernel(Geo g, Rec r, const float4* __restrict__ tab_g, int64_t n, float wepl_max,
+                             uint8_t* __restrict__ out) {
+  extern __shared__ float4 tab[];
+  load_table(tab_g, tab, g.K + 1);
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (!(__ldg(r.wepl + i) <= wepl_max)) return;
+  const RecV v = load_rec(r, i);
+  walk_proton(g, tab, v, [&](int j, float) { out[j] = 0; });
+}
+
+// One 6-neighbour growth step of the hull: out = in, plus every voxel with a
+// face neighbour in `in`.
+__global__ void dilate_kernel(const uint8_t* __restrict__ in, uint8_t* __restrict__ out, int nx, int ny, int nz) {
+  const int64_t M = (int64_t)nx * ny * nz;
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= M) return;
+  const int x = (int)(j % nx), y = (int)((j / nx) % ny), z = (int)(j / ((int64_t)nx * ny));
+  const int64_t sxy = (int64_t)nx * ny;
+  const bool hit = in[j] || (x > 0 && in[j - 1]) || (x + 1 < nx && in[j + 1]) || (y > 0 && in[j - nx]) ||
+                   (y + 1 < ny && in[j + nx]) || (z > 0 && in[j - sxy]) || (z + 1 < nz && in[j + sxy]);
+  out[j] = hit ? 1 : 0;
+}
 
 // ---- load-time ordering of each block: (gantry-angle bin, entry lateral bin)
 // so that the 32 lanes of a warp trace nearly parallel paths (coherent face
@@ -452,10 +523,32 @@ cudaError_t launch_validate(const Rec& r, int64_t n, int64_t base, float pos_lim
   return cudaGetLastError();
 }
 
-cudaError_t launch_count(const Geo& g, const Rec& r, const float4* tab, int64_t first, int64_t count,
-                         unsigned int* cnt, int threads, cudaStream_t s) {
+cudaError_t launch_hull_ranges(const Geo& g, const Rec& r, int64_t n, const uint8_t* mask, int32_t* range,
+                               cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  hull_range_kernel<<<grid_for(n, 128), 128, 0, s>>>(g, r, n, mask, range);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_carve_hull(const Geo& g, const Rec& r, const float4* tab, int64_t n, float wepl_max, int dilate,
+                              uint8_t* out, uint8_t* tmp, cudaStream_t s) {
+  const int64_t M = (int64_t)g.nx * g.ny * g.nz;
+  cudaError_t e = cudaMemsetAsync(out, 1, (size_t)M, s);
+  if (e != cudaSuccess) return e;
+  if (n > 0) carve_kernel<<<grid_for(n, 128), 128, (g.K + 1) * sizeof(float4), s>>>(g, r, tab, n, wepl_max, out);
+  for (int it = 0; it < dilate; ++it) {
+    e = cudaMemcpyAsync(tmp, out, (size_t)M, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return e;
+    dilate_kernel<<<grid_for(M, 256), 256, 0, s>>>(tmp, out, g.nx, g.ny, g.nz);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_count(const Geo& g, const Rec& r, const float4* tab, const Hull& hull, int64_t first,
+                         int64_t count, unsigned int* cnt, int threads, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
-  count_kernel<<<grid_for(count, threads), threads, (g.K + 1) * sizeof(float4), s>>>(g, r, tab, first, count, cnt);
+  count_kernel<<<grid_for(count, threads), threads, (g.K + 1) * sizeof(float4), s>>>(g, r, tab, hull, first, count,
+                                                                                      cnt);
   return cudaGetLastError();
 }
 
@@ -469,28 +562,35 @@ cudaError_t launch_counts_to_float(const unsigned int* cnt, float* out, int64_t 
   return cudaGetLastError();
 }
 
-cudaError_t launch_drop_fused(const Geo& g, const Rec& r, const float4* tab, int64_t first, int64_t count,
-                              const float* x, float* delta, float lambda, int flags, int threads, cudaStream_t s) {
+cudaError_t launch_drop_fused(const Geo& g, const Rec& r, const float4* tab, const Hull& hull, int64_t first,
+                              int64_t count, const float* x, float* delta, float lambda, int flags, int threads,
+                              cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
   threads = 128;
+  if (hull.range) {
+    drop_fused_hull_kernel<<<grid_for(count, threads), threads, 0, s>>>(g, r, hull, first, count, x, delta, lambda,
+                                                                         flags);
+    return cudaGetLastError();
+  }
   drop_fused_kernel<<<grid_for(count, threads), threads, (g.K + 1) * sizeof(float4), s>>>(g, r, tab, first, count, x,
                                                                                            delta, lambda, flags);
   return cudaGetLastError();
 }
 
-cudaError_t launch_project(const Geo& g, const Rec& r, const float4* tab, int64_t first, int64_t count,
-                           const int64_t* where, const float* x, int flags, float* y, cudaStream_t s) {
+cudaError_t launch_project(const Geo& g, const Rec& r, const float4* tab, const Hull& hull, int64_t first,
+                           int64_t count, const int64_t* where, const float* x, int flags, float* y, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
-  project_kernel<<<grid_for(count, 128), 128, (g.K + 1) * sizeof(float4), s>>>(g, r, tab, first, count, where, x,
-                                                                                flags, y);
+  project_kernel<<<grid_for(count, 128), 128, (g.K + 1) * sizeof(float4), s>>>(g, r, tab, hull, first, count, where,
+                                                                                x, flags, y);
   return cudaGetLastError();
 }
 
-cudaError_t launch_residual(const Geo& g, const Rec& r, const float4* tab, int64_t n, int64_t stride, const float* x,
-                            int flags, double* acc, cudaStream_t s) {
+cudaError_t launch_residual(const Geo& g, const Rec& r, const float4* tab, const Hull& hull, int64_t n, int64_t stride,
+                            const float* x, int flags, double* acc, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   const int64_t m = (n + stride - 1) / stride;
-  residual_kernel<<<grid_for(m, 128), 128, (g.K + 1) * sizeof(float4), s>>>(g, r, tab, n, stride, x, flags, acc);
+  residual_kernel<<<grid_for(m, 128), 128, (g.K + 1) * sizeof(float4), s>>>(g, r, tab, hull, n, stride, x, flags,
+                                                                             acc);
   return cudaGetLastError();
 }
 
@@ -527,11 +627,11 @@ cudaError_t launch_tvs(float* x, int nx, int ny, int nz, const TvsParams& p, flo
   return cudaGetLastError();
 }
 
-cudaError_t launch_row_counts(const Geo& g, const Rec& r, const float4* tab, int64_t first, int64_t count,
-                              const int64_t* where, int64_t* row_ptr, cudaStream_t s) {
+cudaError_t launch_row_counts(const Geo& g, const Rec& r, const float4* tab, const Hull& hull, int64_t first,
+                              int64_t count, const int64_t* where, int64_t* row_ptr, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
-  row_count_kernel<<<grid_for(count, 128), 128, (g.K + 1) * sizeof(float4), s>>>(g, r, tab, first, count, where,
-                                                                                  row_ptr);
+  row_count_kernel<<<grid_for(count, 128), 128, (g.K + 1) * sizeof(float4), s>>>(g, r, tab, hull, first, count,
+                                                                                  where, row_ptr);
   return cudaGetLastError();
 }
 
@@ -540,12 +640,12 @@ cudaError_t launch_scan_rows(int64_t* row_ptr, int64_t count, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_row_fill(const Geo& g, const Rec& r, const float4* tab, int64_t first, int64_t count,
-                            const int64_t* where, const int64_t* row_ptr, int32_t* vox, float* len, int32_t* nodes,
-                            cudaStream_t s) {
+cudaError_t launch_row_fill(const Geo& g, const Rec& r, const float4* tab, const Hull& hull, int64_t first,
+                            int64_t count, const int64_t* where, const int64_t* row_ptr, int32_t* vox, float* len,
+                            int32_t* nodes, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
-  row_fill_kernel<<<grid_for(count, 128), 128, (g.K + 1) * sizeof(float4), s>>>(g, r, tab, first, count, where,
-                                                                                 row_ptr, vox, len, nodes);
+  row_fill_kernel<<<grid_for(count, 128), 128, (g.K + 1) * sizeof(float4), s>>>(g, r, tab, hull, first, count,
+                                                                                 where, row_ptr, vox, len, nodes);
   return cudaGetLastError();
 }
 

@@ -175,7 +175,7 @@ extern "C" pct_status pct_drop_block_noalloc(const pct_grid* grid, const pct_con
   // run counts s_j of this block (counted in the delta area), then 1/s_j
   unsigned* cnt = (unsigned*)delta;
   if ((e = cudaMemsetAsync(cnt, 0, (size_t)M * sizeof(unsigned), s)) != cudaSuccess ||
-      (e = pct::launch_count(g, r, tab32, 0, h->n, cnt, 128, s)) != cudaSuccess ||
+      (e = pct::launch_count(g, r, tab32, pct::Hull{}, 0, h->n, cnt, 128, s)) != cudaSuccess ||
       (e = pct::launch_inv_counts(cnt, inv_s, M, s)) != cudaSuccess ||
       (e = cudaMemsetAsync(delta, 0, (size_t)M * sizeof(float), s)) != cudaSuccess)
     return noalloc_fail(PCT_ERR_CUDA, "count pass", e);

@@ -354,4 +354,91 @@ __device__ __forceinline__ void walk_proton(const Geo& g, const float4* __restri
   emit_run(g, s, visit);
 }
 
+// Walk with an object hull (same runs contract as walk_proton): the path is
+// the entry ray up to node iin, the MLP of the layer between nodes iin and
+// iout (table T = fam + family_offset(iout - iin), node k uses T[k - iin],
+// from the ray positions at the hull, t_in = fma(st0, iin du, t0) and
+// t_out = fma(st2, (iout - K) du, t2), and the measured slopes), then the exit
+// ray from node iout:
+//   t_k = fma(c4, st2, fma(c3, t_out, fma(c2, st0, c1 * t_in)))   (same for v)
+// range = iin | iout << 16 (0 <= iin < iout <= K).
+template <class Visit>
+__device__ __forceinline__ void walk_proton_hull(const Geo& g, const float4* __restrict__ fam, int32_t range,
+                                                 const RecV& r, Visit&& visit) {
+  const int iin = range & 0xffff, iout = range >> 16;
+  const float4* __restrict__ T = fam + family_offset(iout - iin);
+  const float din = __fmul_rn((float)iin, g.du), dout = __fmul_rn((float)(iout - g.K), g.du);
+  const float tin = __fmaf_rn(r.st0, din, r.t0), vin = __fmaf_rn(r.sv0, din, r.v0);
+  const float tout = __fmaf_rn(r.st2, dout, r.t2), vout = __fmaf_rn(r.sv2, dout, r.v2);
+  int klo, khi;
+  node_range(g, r, klo, khi);
+  WalkState s;
+  {
+    // klo <= 0 <= iin: the first node is on the entry ray
+    const float dk = __fmul_rn((float)klo, g.du);
+    s.qP = node_grid(g, r, __fmaf_rn((float)klo, g.du, g.u0), __fmaf_rn(r.st0, dk, r.t0), __fmaf_rn(r.sv0, dk, r.v0));
+    s.P = quantise3(s.qP);
+  }
+  s.cx = floor_q(s.P.x);
+  s.cy = floor_q(s.P.y);
+  s.cz = floor_q(s.P.z);
+  s.run = 0.f;
+  s.pos = false;
+  int k = klo + 1;
+  // entry ray up to the hull entry
+  for (; k <= iin && k <= khi; ++k) {
+    const float kf = (float)k;
+    const float dk = __fmul_rn(kf, g.du);
+    const float t = __fmaf_rn(r.st0, dk, r.t0), v = __fmaf_rn(r.sv0, dk, r.v0);
+    walk_segment(g, s, node_grid(g, r, __fmaf_rn(kf, g.du, g.u0), t, v), visit);
+  }
+  // MLP inside the hull
+  const int kmid = min(khi, iout - 1);
+  for (; k <= kmid; ++k) {
+    const float4 c = __ldg(T + (k - iin));
+    const float t = __fmaf_rn(c.w, r.st2, __fmaf_rn(c.z, tout, __fmaf_rn(c.y, r.st0, __fmul_rn(c.x, tin))));
+    const float v = __fmaf_rn(c.w, r.sv2, __fmaf_rn(c.z, vout, __fmaf_rn(c.y, r.sv0, __fmul_rn(c.x, vin))));
+    walk_segment(g, s, node_grid(g, r, __fmaf_rn((float)k, g.du, g.u0), t, v), visit);
+  }
+  // exit ray from the hull exit
+  for (; k <= khi; ++k) {
+    const float dk = __fmul_rn((float)(k - g.K), g.du);
+    const float t = __fmaf_rn(r.st2, dk, r.t2), v = __fmaf_rn(r.sv2, dk, r.v2);
+    walk_segment(g, s, node_grid(g, r, __fmaf_rn((float)k, g.du, g.u0), t, v), visit);
+  }
+  emit_run(g, s, visit);
+}
+
+// Q20 grid coordinates of node k (0 <= k <= K) on the hull path.
+__device__ __forceinline__ int3 node_q_hull(const Geo& g, const float4* __restrict__ fam, int32_t range,
+                                            const RecV& r, int k) {
+  const int iin = range & 0xffff, iout = range >> 16;
+  float t, v;
+  if (k <= iin) {
+    const float dk = __fmul_rn((float)k, g.du);
+    t = __fmaf_rn(r.st0, dk, r.t0);
+    v = __fmaf_rn(r.sv0, dk, r.v0);
+  } else if (k >= iout) {
+    const float dk = __fmul_rn((float)(k - g.K), g.du);
+    t = __fmaf_rn(r.st2, dk, r.t2);
+    v = __fmaf_rn(r.sv2, dk, r.v2);
+  } else {
+    const float din = __fmul_rn((float)iin, g.du), dout = __fmul_rn((float)(iout - g.K), g.du);
+    const float tin = __fmaf_rn(r.st0, din, r.t0), vin = __fmaf_rn(r.sv0, din, r.v0);
+    const float tout = __fmaf_rn(r.st2, dout, r.t2), vout = __fmaf_rn(r.sv2, dout, r.v2);
+    const float4 c = __ldg(fam + family_offset(iout - iin) + (k - iin));
+    t = __fmaf_rn(c.w, r.st2, __fmaf_rn(c.z, tout, __fmaf_rn(c.y, r.st0, __fmul_rn(c.x, tin))));
+    v = __fmaf_rn(c.w, r.sv2, __fmaf_rn(c.z, vout, __fmaf_rn(c.y, r.sv0, __fmul_rn(c.x, vin))));
+  }
+  return quantise3(node_grid(g, r, __fmaf_rn((float)k, g.du, g.u0), t, v));
+}
+
+// Either walk: with a hull when hull.range is set (i = stored index).
+template <class Visit>
+__device__ __forceinline__ void walk_any(const Geo& g, const float4* __restrict__ tab, const Hull& hull, int64_t i,
+                                         const RecV& r, Visit&& visit) {
+  if (hull.range) walk_proton_hull(g, hull.fam, __ldg(hull.range + i), r, visit);
+  else walk_proton(g, tab, r, visit);
+}
+
 }  // namespace pct

@@ -68,6 +68,11 @@ _SIGS = {
     "pct_mlp_rows": [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
                      ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)],
     "pct_block_counts": [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p],
+    "pct_set_hull": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int],
+    "pct_carve_hull": [ctypes.c_void_p, ctypes.c_float, ctypes.c_int32],
+    "pct_get_hull": [ctypes.c_void_p, ctypes.c_void_p],
+    "pct_hull_ranges": [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p],
+    "pct_mlp_table_n": [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p],
     "pct_project": [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p],
     "pct_residual": [ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)],
     "pct_set_x0": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int],
@@ -261,6 +266,47 @@ class Context:
         n = int(need.value)
         out = (rp, vox[:n], ln[:n])
         return out + (nodes,) if with_nodes else out
+
+    def set_hull(self, mask) -> None:
+        """Object hull (M values, nonzero = inside; numpy or CUDA tensor), or
+        None to remove it."""
+        self._bind_stream()
+        if mask is None:
+            _check(self._L.pct_set_hull(self._h, None, 0))
+        elif _is_tensor(mask) and mask.is_cuda:
+            m = (mask.reshape(-1) != 0).to(_torch().uint8).contiguous()
+            _check(self._L.pct_set_hull(self._h, ctypes.c_void_p(m.data_ptr()), 1))
+        else:
+            m = np.ascontiguousarray(np.asarray(mask).reshape(-1) != 0, dtype=np.uint8)
+            if m.size != self.M:
+                raise ValueError("hull mask must hold one value per voxel")
+            _check(self._L.pct_set_hull(self._h, m.ctypes.data_as(ctypes.c_void_p), 0))
+
+    def carve_hull(self, wepl_max: float, dilate: int = 1) -> None:
+        """Space-carved hull from the loaded histories (see pct_carve_hull)."""
+        self._bind_stream()
+        _check(self._L.pct_carve_hull(self._h, float(wepl_max), int(dilate)))
+
+    def get_hull(self) -> np.ndarray:
+        out = np.zeros(self.M, dtype=np.uint8)
+        self._bind_stream()
+        _check(self._L.pct_get_hull(self._h, out.ctypes.data_as(ctypes.c_void_p)))
+        return out
+
+    def hull_ranges(self, first: int = 0, count: Optional[int] = None) -> np.ndarray:
+        """(count, 2) int32 hull entry/exit nodes of histories [first, first+count)."""
+        count = self.n - first if count is None else count
+        out = np.zeros((count, 2), dtype=np.int32)
+        self._bind_stream()
+        _check(self._L.pct_hull_ranges(self._h, int(first), int(count), out.ctypes.data_as(ctypes.c_void_p)))
+        return out
+
+    def mlp_table_n(self, n: int) -> np.ndarray:
+        """FP64 MLP table (n+1, 4) of a layer of n node intervals, from the GPU."""
+        out = np.zeros((n + 1, 4), dtype=np.float64)
+        self._bind_stream()
+        _check(self._L.pct_mlp_table_n(self._h, int(n), out.ctypes.data_as(ctypes.c_void_p)))
+        return out
 
     def project(self, first: int = 0, count: Optional[int] = None):
         """a_i.x for histories [first, first+count) (load order) as a CUDA tensor."""
