@@ -477,6 +477,8 @@ def run_table2(args):
         with P.Context(g, n_blocks=wl.n_blocks, flags=flags, tvs_beta0=args.t2_tvs, carp_strings=args.t2_strings,
                        device=local) as ctx:
             ctx.load(rec)
+            if args.hull:
+                ctx.carve_hull(args.hull_wepl, args.hull_dilate)
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             st = torch.cuda.current_stream()
@@ -488,6 +490,7 @@ def run_table2(args):
     line = {"metric": "ROI RSP accuracy (Table 2 format)", "unit": "RSP", "data": "synthetic",
             "config": {"workload": wl.name, "grid": "160x160x32 @ 1.25 mm", "histories": wl.n, "blocks": wl.n_blocks,
                        "carp_strings": args.t2_strings,
+                       "hull": (f"carved: WEPL <= {args.hull_wepl} mm, dilate {args.hull_dilate}") if args.hull else "none",
                        "iterations": wl.n_sweeps, "tvs_beta0": args.t2_tvs,
                        "phantom": "150 mm RSP-1.0 cylinder, seven 12 mm inserts at Table 2's true RSPs"},
             "results": out}
@@ -519,6 +522,10 @@ def run_ours(args):
     flags = P.FLAG_PROFILE | (P.FLAG_NO_SORT if args.no_sort else 0)
     ctx = P.Context(g, n_blocks=wl.n_blocks, flags=flags, device=local)
     ctx.load(rec, borrow=True)
+    hull = None
+    if args.hull:  # object hull carved from the data (untimed set-up, like the load)
+        ctx.carve_hull(args.hull_wepl, args.hull_dilate)
+        hull = ctx.get_hull()
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
         ctx.iterate(1)
@@ -559,6 +566,8 @@ def run_ours(args):
     ctx_rows = P.Context(g, n_blocks=1, device=local)  # runs per history on a sample (unit count)
     sample = {k: v[: min(wl.n, 200_000)] for k, v in rec.items()}
     ctx_rows.load(sample, borrow=True)
+    if hull is not None:
+        ctx_rows.set_hull(hull)
     rp = ctx_rows.rows(0, len(sample["t0"]))[0]
     runs_per_history = float(rp[-1].item()) / len(sample["t0"])
     ctx_rows.close()
@@ -569,7 +578,7 @@ def run_ours(args):
     cnt = ncu_counters()
     traffic = cnt["dram_bytes_per_history"] * per_block if cnt else None
     hbm_achieved = 44.0 * per_block / avg_fused_s / 1e9
-    roof = {"kernel": "drop_fused_kernel", "bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
+    roof = {"kernel": "drop_fused_hull_kernel" if args.hull else "drop_fused_kernel", "bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
             "frac": achieved / alu_peak, "traffic": traffic,
             "peak_source": f"{ALU_LANES_PER_SM} lanes x {N_SMS} SMs x {sm_mhz:.0f} MHz",
             "ops_per_history": ops_per_history, "runs_per_history": runs_per_history, "mlp_nodes": ctx.K + 1,
@@ -592,6 +601,8 @@ def run_ours(args):
             barrier()
             t0 = time.perf_counter()
             ctx2.load(host)
+            if args.hull:
+                ctx2.carve_hull(args.hull_wepl, args.hull_dilate)
             ctx2.iterate(args.e2e_sweeps)
             xs.append(ctx2.get_rsp())
             dt = time.perf_counter() - t0
@@ -601,7 +612,8 @@ def run_ours(args):
         e2e_val = wl.n * args.e2e_sweeps * world / statistics.mean(times)
         e2e = {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 44 * wl.n,
                "d2h_bytes_per_step": 4 * g.m, "sweeps_per_step": args.e2e_sweeps,
-               "includes": "H2D copy, validation, block counts, sweeps, D2H of x"}
+               "includes": "H2D copy, validation, block counts, " + ("hull carving, " if args.hull else "") +
+                           "sweeps, D2H of x"}
     else:
         ctx.close()
 
@@ -617,10 +629,12 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": wl.name, "grid": "160x160x64 @ 1.25 mm (1.64M voxels)",
+            "config": {"workload": wl.name + ("_hull" if args.hull else ""), "grid": "160x160x64 @ 1.25 mm (1.64M voxels)",
                        "histories_per_gpu": wl.n, "angles": 90, "n_blocks": wl.n_blocks,
                        "step": "one DROP sweep over all histories", "parallelism": f"replicas{world}",
-                       "l2": "records 2.2 GB per sweep > 129 MB L2 (no flush needed); x and delta L2-resident"},
+                       "l2": "records 2.2 GB per sweep > 129 MB L2 (no flush needed); x and delta L2-resident",
+                       "hull": (f"carved from the data: rows of histories with WEPL <= {args.hull_wepl} mm are air, "
+                                f"hull dilated by {args.hull_dilate} voxel") if args.hull else "none (MLP between the planes)"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
             "host_threads": _cpu_threads(),
         }
@@ -642,6 +656,9 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=1_000_000)
     ap.add_argument("--ref-sample", type=int, default=200_000)
     ap.add_argument("--no-sort", action="store_true", help="keep each block in load order (A/B of the ordering)")
+    ap.add_argument("--hull", action="store_true", help="head / table2: MLP inside a hull carved from the data")
+    ap.add_argument("--hull-wepl", type=float, default=1.0, help="carving: histories with WEPL <= this (mm) are air")
+    ap.add_argument("--hull-dilate", type=int, default=1, help="carving: 6-neighbour growth steps of the hull")
     ap.add_argument("--workload", default="head", choices=["head", "batched", "precision", "warmstart", "table2"])
     ap.add_argument("--t2-n", type=int, default=200_000_000)
     ap.add_argument("--t2-blocks", type=int, default=600, help="DROP blocks; CARP: blocks split over the strings")

@@ -66,8 +66,12 @@ __global__ void __launch_bounds__(128, 9) drop_fused_kernel(Geo g, Rec r, const 
   drop_history(g, tab, r, first + p, x, delta, lambda, flags);
 }
 
-// The same with an object hull (see walk_proton_hull).
-__global__ void __launch_bounds__(128, 9) drop_fused_hull_kernel(Geo g, Rec r, Hull hull, int64_t first, int64_t count,
+// The same with an object hull (see walk_proton_hull). PCT_HULL_MIN_CTAS:
+// resident 128-thread CTAs per SM its register allocation must allow.
+#ifndef PCT_HULL_MIN_CTAS
+#define PCT_HULL_MIN_CTAS 9
+#endif
+__global__ void __launch_bounds__(128, PCT_HULL_MIN_CTAS) drop_fused_hull_kernel(Geo g, Rec r, Hull hull, int64_t first, int64_t count,
                                                                const float* __restrict__ x, float* __restrict__ delta,
                                                                float lambda, int flags) {
   int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;

@@ -362,11 +362,19 @@ __device__ __forceinline__ void walk_proton(const Geo& g, const float4* __restri
 // ray from node iout:
 //   t_k = fma(c4, st2, fma(c3, t_out, fma(c2, st0, c1 * t_in)))   (same for v)
 // range = iin | iout << 16 (0 <= iin < iout <= K).
+//
+// The lanes of a warp enter and leave their hulls at different nodes, so the
+// three pieces run in one loop: every node uses the four-term form, with
+// (1, k du, 0, 0) on (t0, st0, -, -) for the entry ray and (0, 0, 1,
+// (k - K) du) on (-, -, t2, st2) for the exit ray. A product with 0 adds a
+// signed zero, which leaves every non-zero value unchanged and the grid
+// coordinates q (offset by n/2 > 0) identical, so the nodes are those of the
+// separate ray formulas bit for bit.
 template <class Visit>
 __device__ __forceinline__ void walk_proton_hull(const Geo& g, const float4* __restrict__ fam, int32_t range,
                                                  const RecV& r, Visit&& visit) {
   const int iin = range & 0xffff, iout = range >> 16;
-  const float4* __restrict__ T = fam + family_offset(iout - iin);
+  const float4* __restrict__ T = fam + family_offset(iout - iin) - iin;  // T[k] for iin < k < iout
   const float din = __fmul_rn((float)iin, g.du), dout = __fmul_rn((float)(iout - g.K), g.du);
   const float tin = __fmaf_rn(r.st0, din, r.t0), vin = __fmaf_rn(r.sv0, din, r.v0);
   const float tout = __fmaf_rn(r.st2, dout, r.t2), vout = __fmaf_rn(r.sv2, dout, r.v2);
@@ -384,26 +392,19 @@ __device__ __forceinline__ void walk_proton_hull(const Geo& g, const float4* __r
   s.cz = floor_q(s.P.z);
   s.run = 0.f;
   s.pos = false;
-  int k = klo + 1;
-  // entry ray up to the hull entry
-  for (; k <= iin && k <= khi; ++k) {
-    const float kf = (float)k;
-    const float dk = __fmul_rn(kf, g.du);
-    const float t = __fmaf_rn(r.st0, dk, r.t0), v = __fmaf_rn(r.sv0, dk, r.v0);
-    walk_segment(g, s, node_grid(g, r, __fmaf_rn(kf, g.du, g.u0), t, v), visit);
-  }
-  // MLP inside the hull
-  const int kmid = min(khi, iout - 1);
-  for (; k <= kmid; ++k) {
-    const float4 c = __ldg(T + (k - iin));
-    const float t = __fmaf_rn(c.w, r.st2, __fmaf_rn(c.z, tout, __fmaf_rn(c.y, r.st0, __fmul_rn(c.x, tin))));
-    const float v = __fmaf_rn(c.w, r.sv2, __fmaf_rn(c.z, vout, __fmaf_rn(c.y, r.sv0, __fmul_rn(c.x, vin))));
-    walk_segment(g, s, node_grid(g, r, __fmaf_rn((float)k, g.du, g.u0), t, v), visit);
-  }
-  // exit ray from the hull exit
-  for (; k <= khi; ++k) {
-    const float dk = __fmul_rn((float)(k - g.K), g.du);
-    const float t = __fmaf_rn(r.st2, dk, r.t2), v = __fmaf_rn(r.sv2, dk, r.v2);
+  for (int k = klo + 1; k <= khi; ++k) {
+    const bool exit = k >= iout, mlp = k > iin && !exit;
+    float4 c;
+    if (mlp) {
+      c = __ldg(T + k);
+    } else {
+      const float dk = __fmul_rn((float)(exit ? k - g.K : k), g.du);
+      c = exit ? make_float4(0.f, 0.f, 1.f, dk) : make_float4(1.f, dk, 0.f, 0.f);
+    }
+    const float at = mlp ? tin : r.t0, av = mlp ? vin : r.v0;
+    const float bt = exit ? r.t2 : tout, bv = exit ? r.v2 : vout;
+    const float t = __fmaf_rn(c.w, r.st2, __fmaf_rn(c.z, bt, __fmaf_rn(c.y, r.st0, __fmul_rn(c.x, at))));
+    const float v = __fmaf_rn(c.w, r.sv2, __fmaf_rn(c.z, bv, __fmaf_rn(c.y, r.sv0, __fmul_rn(c.x, av))));
     walk_segment(g, s, node_grid(g, r, __fmaf_rn((float)k, g.du, g.u0), t, v), visit);
   }
   emit_run(g, s, visit);
