@@ -578,6 +578,20 @@ def run_ours(args):
     cnt = ncu_counters()
     traffic = cnt["dram_bytes_per_history"] * per_block if cnt else None
     hbm_achieved = 44.0 * per_block / avg_fused_s / 1e9
+    # the library's own roof microbenchmarks: L2 atomics, L2 gathers, ALU issue
+    mr = P.measure_roofs(local)
+    per_s = per_block / avg_fused_s
+    measured = {
+        "l2_atomic": {"achieved": runs_per_history * per_s, "peak": mr["l2_red_per_s"], "unit": "atomics/s",
+                      "peak_coherent_lines": mr["l2_red_coherent_per_s"]},
+        "l2_gather": {"achieved": runs_per_history * per_s, "peak": mr["l2_gather_per_s"], "unit": "loads/s"},
+        "alu_issue": {"achieved": ops_per_history * per_s, "peak": mr["alu_ops_per_s"], "unit": "ops/s",
+                      "fma_chain_peak": mr["fma_ops_per_s"]},
+        "source": (f"pct_measure_roofs: random float atomics / 4 B gathers in an {mr['array_bytes'] >> 20} MB "
+                   f"array (L2 {mr['l2_bytes'] >> 20} MB), integer and FMA chains; {mr['sms']} SMs"),
+    }
+    for k in ("l2_atomic", "l2_gather", "alu_issue"):
+        measured[k]["frac"] = measured[k]["achieved"] / measured[k]["peak"]
     roof = {"kernel": "drop_fused_hull_kernel" if args.hull else "drop_fused_kernel", "bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
             "frac": achieved / alu_peak, "traffic": traffic,
             "peak_source": f"{ALU_LANES_PER_SM} lanes x {N_SMS} SMs x {sm_mhz:.0f} MHz",
@@ -585,7 +599,8 @@ def run_ours(args):
             "avg_launch_ms": avg_fused_s * 1e3, "histories_per_launch": per_block,
             "fused_share_of_step": sum(fused_ms) / ms,
             "hbm": {"achieved": hbm_achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                    "frac": hbm_achieved / peaks["hbm_gbs"], "peak_source": src, "algorithmic_bytes": "44 B/history"}}
+                    "frac": hbm_achieved / peaks["hbm_gbs"], "peak_source": src, "algorithmic_bytes": "44 B/history"},
+            "measured_roofs": measured}
 
     # end to end through the public API from pinned host buffers
     e2e = None

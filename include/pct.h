@@ -383,6 +383,28 @@ PCT_API pct_status pct_drop_block_noalloc(const pct_grid *grid, const pct_config
 /* Text for the last error of the calling thread ("" if none). */
 PCT_API const char *pct_last_error(void);
 
+/* Measured roofs of the resources the fused kernel uses (Sec. 2 / 2.1 give no
+ * hardware model; these are this library's own microbenchmarks). Each rate is
+ * the best of five timed launches (CUDA events) after a warm-up, with
+ * 8 CTAs of 256 threads per SM:
+ *   l2_red_per_s          float atomicAdd at random addresses of an
+ *                         array_bytes array (default 8 MB, L2-resident);
+ *   l2_red_coherent_per_s the same with the 32 lanes of a warp on one
+ *                         128-byte line per step;
+ *   l2_gather_per_s       random 4-byte loads from the same array;
+ *   alu_ops_per_s         integer shift/xor/add chains (4 source operations
+ *                         per step, 8 independent chains per thread);
+ *   fma_ops_per_s         FP32 FMA chains (8 independent chains per thread).
+ * l2_bytes and sms come from cudaDeviceProp. Allocates array_bytes (rounded
+ * down to a power of two, 4 KB .. 8 GB; <= 0: 8 MB) for the call, on
+ * `device`. Synchronises. */
+typedef struct pct_roofs {
+  double l2_red_per_s, l2_red_coherent_per_s, l2_gather_per_s, alu_ops_per_s, fma_ops_per_s;
+  int64_t array_bytes, l2_bytes;
+  int32_t sms;
+} pct_roofs;
+PCT_API pct_status pct_measure_roofs(int device, int64_t array_bytes, pct_roofs *out);
+
 #ifdef __cplusplus
 }
 #endif

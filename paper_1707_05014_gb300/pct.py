@@ -51,6 +51,13 @@ class _Config(ctypes.Structure):
                 ("tvs_eps", ctypes.c_float), ("tvs_tries", ctypes.c_int32), ("carp_strings", ctypes.c_int32)]
 
 
+class _Roofs(ctypes.Structure):
+    _fields_ = [("l2_red_per_s", ctypes.c_double), ("l2_red_coherent_per_s", ctypes.c_double),
+                ("l2_gather_per_s", ctypes.c_double), ("alu_ops_per_s", ctypes.c_double),
+                ("fma_ops_per_s", ctypes.c_double), ("array_bytes", ctypes.c_int64), ("l2_bytes", ctypes.c_int64),
+                ("sms", ctypes.c_int32)]
+
+
 class _Hist(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64)] + [(f, ctypes.c_void_p) for f in FIELDS]
 
@@ -69,6 +76,7 @@ _SIGS = {
                      ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)],
     "pct_block_counts": [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p],
     "pct_set_hull": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int],
+    "pct_measure_roofs": [ctypes.c_int, ctypes.c_int64, ctypes.c_void_p],
     "pct_carve_hull": [ctypes.c_void_p, ctypes.c_float, ctypes.c_int32],
     "pct_get_hull": [ctypes.c_void_p, ctypes.c_void_p],
     "pct_hull_ranges": [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p],
@@ -127,6 +135,14 @@ def load_library(path: str = LIB_PATH):
 def _check(code: int):
     if code != PCT_OK:
         raise PctError(code, load_library().pct_last_error().decode())
+
+
+def measure_roofs(device: int = 0, array_bytes: int = 8 << 20) -> Dict[str, float]:
+    """The library's roof microbenchmarks (pct_measure_roofs) as a dict."""
+    L = load_library()
+    r = _Roofs()
+    _check(L.pct_measure_roofs(int(device), int(array_bytes), ctypes.byref(r)))
+    return {f: getattr(r, f) for f, _ in _Roofs._fields_}
 
 
 def _torch():
