@@ -103,17 +103,21 @@ OPS_PER_MLP_NODE = 27  # t/v 8, rotation 4, grid 3, scale 3, rounding 3, floor 3
 OPS_PER_RUN = 11  # crossing fraction 3, accumulation 2, index 3, load/atomic 3
 
 
+# the sources the fused kernel is compiled from
+FUSED_SOURCES = ("pct_internal.h", "pct_walk.cuh", "pct_drop.cuh", "pct_kernels.cu")
+
+
 def kernel_source_hash() -> str:
-    """Hash of the CUDA sources: counters taken for another version are stale."""
+    """Hash of the fused kernel's CUDA sources: counters taken for another
+    version are stale."""
     import hashlib
 
     d = os.path.join(ROOT, "paper_1707_05014_gb300", "csrc")
     h = hashlib.sha256()
-    for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(f.encode())
-            with open(os.path.join(d, f), "rb") as fh:
-                h.update(fh.read())
+    for f in FUSED_SOURCES:
+        h.update(f.encode())
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 
