@@ -163,8 +163,9 @@ PCT_API pct_status pct_load_histories(pct_ctx *ctx, const pct_histories *h, int 
  * all DEVICE pointers: row_ptr (count+1 int64), vox (cap int32 voxel
  * indices), len (cap float chord lengths in mm, in path order; a run is a
  * maximal stretch in one voxel, zero-length runs never appear). `nodes`
- * (optional, may be NULL) receives count x (K+1) x 3 int32: the interior MLP
- * nodes in Q20 fixed point grid units. *needed receives the total number of
+ * (optional, may be NULL) receives count x (K+1) x 3 int32: the path's nodes
+ * k = 0..K between the planes (the MLP nodes; with a hull, the ray nodes
+ * outside it) in Q20 fixed point grid units. *needed receives the total number of
  * runs; if it exceeds cap, returns PCT_ERR_CAPACITY and writes no runs.
  * Synchronises. */
 PCT_API pct_status pct_mlp_rows(pct_ctx *ctx, int64_t first, int64_t count, int64_t *row_ptr, int32_t *vox, float *len,

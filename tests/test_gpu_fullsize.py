@@ -56,3 +56,29 @@ def test_full_sweep_projection_and_residual(full, oracle):
         y = ctx.project(s, 200).cpu().numpy().astype(np.float64)
         yo = oracle.project(g, S.subset(host, slice(200 * q, 200 * q + 200)), x, mode=oracle.MODE_FP32)
         assert np.all(np.abs(y - yo) <= 1e-5 * np.maximum(np.abs(yo), 1.0))
+
+
+def test_sampled_hull_rows_bit_exact_at_full_size(full, oracle):
+    # the same loaded 50M histories with the voxelised head as object hull:
+    # hull ranges, nodes and index lists of the samples match the oracle's
+    # hull path, and a sweep with the hull still fits the data
+    wl, ctx, starts, host = full
+    g = wl.grid
+    hull = (S.voxelize(wl.phantom(), g, ss=1) > 0.5).astype(np.uint8)
+    ctx.set_hull(hull)
+    try:
+        for q, s in enumerate(starts[::2]):
+            sub = S.subset(host, slice(400 * q, 400 * q + 200))
+            rng = ctx.hull_ranges(s, 200)
+            assert np.array_equal(rng, oracle.hull_ranges(g, sub, hull, mode=oracle.MODE_FP32))
+            rp, vox, ln, nodes = (t.cpu().numpy() for t in ctx.rows(s, 200, with_nodes=True))
+            assert np.array_equal(nodes, oracle.nodes(g, sub, mode=oracle.MODE_FP32, hull=hull))
+            orp, ovox, oln = oracle.rows(g, sub, mode=oracle.MODE_FP32, hull=hull)
+            assert np.array_equal(rp, orp) and np.array_equal(vox, ovox)
+            assert np.all(np.abs(ln - oln) <= 1e-5 * np.maximum(oln, g.hx))
+        ctx.set_x0(np.zeros(g.m, np.float32))
+        r0 = ctx.residual(64)
+        ctx.iterate(1)
+        assert ctx.residual(64) < 0.5 * r0
+    finally:
+        ctx.set_hull(None)
