@@ -6,7 +6,6 @@
 #include <string.h>
 
 #include <string>
-#include <vector>
 
 #include "../../include/pct.h"
 #include "pct_ctx.h"
@@ -491,22 +490,16 @@ pct_status pct_hull_ranges(pct_ctx* c, int64_t first, int64_t count, int32_t* ou
   if (!c->hull_mask) return fail(PCT_ERR_STATE, "no hull set");
   if (first < 0 || count < 0 || first + count > c->n) return fail(PCT_ERR_INVALID_ARG, "range outside [0, n)");
   PCT_CK(cudaSetDevice(c->device));
-  std::vector<int32_t> stored;
-  std::vector<int64_t> where;
-  stored.resize((size_t)c->n);
-  PCT_CK(cudaMemcpyAsync(stored.data(), c->hull_range, (size_t)c->n * sizeof(int32_t), cudaMemcpyDeviceToHost,
-                         c->stream));
-  if (c->where) {
-    where.resize((size_t)c->n);
-    PCT_CK(cudaMemcpyAsync(where.data(), c->where, (size_t)c->n * sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
-  }
-  pct_status st = sync_and_check(c);
-  if (st != PCT_OK) return st;
-  for (int64_t p = 0; p < count; ++p) {
-    const int32_t v = stored[(size_t)(c->where ? where[(size_t)(first + p)] : first + p)];
-    out[2 * p] = v & 0xffff;
-    out[2 * p + 1] = v >> 16;
-  }
+  if (count == 0) return PCT_OK;
+  int32_t* d = nullptr;
+  PCT_ALLOC(d, (size_t)count * 2 * sizeof(int32_t));
+  cudaError_t e = pct::launch_gather_ranges(c->hull_range, c->where, first, count, d, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(out, d, (size_t)count * 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  cudaFree(d);
+  c->launches += 1;
+  if (e != cudaSuccess) return fail(PCT_ERR_CUDA, "hull ranges: %s", cudaGetErrorString(e));
   return PCT_OK;
 }
 

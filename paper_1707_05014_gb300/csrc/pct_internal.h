@@ -68,6 +68,10 @@ cudaError_t launch_mlp_family(double R, double du, int K, float4* fam, int n64, 
 // range[i] for stored histories [0, n) against the hull mask (M bytes).
 cudaError_t launch_hull_ranges(const Geo& g, const Rec& r, int64_t n, const uint8_t* mask, int32_t* range,
                                cudaStream_t s);
+// out[2p], out[2p+1] = (iin, iout) of load-order history first + p (stored
+// position where[first + p], or first + p without a map).
+cudaError_t launch_gather_ranges(const int32_t* range, const int64_t* where, int64_t first, int64_t count,
+                                 int32_t* out, cudaStream_t s);
 // Space carving: out[j] = 0 for every voxel on the (hull-free) row of a stored
 // history with wepl <= wepl_max, else 1; then `dilate` 6-neighbour growth
 // steps (tmp: M bytes of scratch).
