@@ -153,9 +153,12 @@ PCT_API pct_status pct_mlp_table(pct_ctx *ctx, double *out, int to_device);
  * returns PCT_ERR_INVALID_DATA and the first bad index in *first_bad (may be
  * NULL; -1 when all are valid). The records are copied into context storage
  * (ordered within each block unless PCT_FLAG_NO_SORT; PCT_LOAD_DEVICE_BORROW
- * avoids the copy only with PCT_FLAG_NO_SORT). Then computes each block's run
- * counts s_j (DROP's diagonal weights) and resets x to 0. Each block must hold
- * fewer than 2^32 histories. Synchronises. */
+ * avoids the copy only with PCT_FLAG_NO_SORT). Resets x to 0. Each block's
+ * run counts s_j (DROP's diagonal weights) are formed by the first
+ * pct_iterate sweep after the load, which counts each block's runs as it
+ * updates it (pct_batch_create counts them itself if no sweep has). The
+ * context keeps its record buffers across loads and grows them when a load
+ * needs more. Each block must hold fewer than 2^32 histories. Synchronises. */
 PCT_API pct_status pct_load_histories(pct_ctx *ctx, const pct_histories *h, int flags, int64_t *first_bad);
 
 /* Rows a_i of histories [first, first+count) of the loaded set (indices in
@@ -185,9 +188,10 @@ PCT_API pct_status pct_mlp_rows(pct_ctx *ctx, int64_t first, int64_t count, int6
  * defines the rows bit for bit.
  *
  * pct_set_hull: mask = M bytes, nonzero = inside the object (device memory
- * if on_device, else host); NULL removes the hull. Recomputes the ranges and
- * the block weights of loaded histories; later loads use the hull too.
- * Synchronises. Contexts with a hull are not accepted by pct_batch_create. */
+ * if on_device, else host); NULL removes the hull. Recomputes the ranges of
+ * loaded histories (their block weights are recounted by the next sweep);
+ * later loads use the hull too. Synchronises. Contexts with a hull are not
+ * accepted by pct_batch_create. */
 PCT_API pct_status pct_set_hull(pct_ctx *ctx, const uint8_t *mask, int on_device);
 
 /* Space-carved hull from the loaded histories: every voxel on the

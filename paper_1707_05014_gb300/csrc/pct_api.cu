@@ -43,22 +43,62 @@ pct_status fail(pct_status code, const char* fmt, ...) {
     }                                                                                                 \
   } while (0)
 
-void free_records(pct_ctx* c) {
+// Forget the loaded set (its buffers stay allocated for the next load).
+void reset_records(pct_ctx* c) {
   if (c->sweep) cudaGraphExecDestroy(c->sweep);
   c->sweep = nullptr;
+  if (c->sweep_count) cudaGraphExecDestroy(c->sweep_count);
+  c->sweep_count = nullptr;
   c->swept = false;
-  if (c->rec_store) cudaFree(c->rec_store);
-  c->rec_store = nullptr;
-  if (c->inv_s) cudaFree(c->inv_s);
-  c->inv_s = nullptr;
-  if (c->where) cudaFree(c->where);
   c->where = nullptr;
-  if (c->hull_range) cudaFree(c->hull_range);
-  c->hull_range = nullptr;
   c->rec = Rec{};
   c->n = 0;
   c->loaded = false;
+  c->weights_ready = false;
 }
+
+void free_records(pct_ctx* c) {
+  reset_records(c);
+  cudaFree(c->rec_store);
+  cudaFree(c->inv_s);
+  cudaFree(c->where_buf);
+  cudaFree(c->hull_range);
+  cudaFree(c->staging);
+  cudaFree(c->sort_key);
+  cudaFree(c->sort_order);
+  cudaFree(c->sort_hist);
+  c->rec_store = nullptr;
+  c->inv_s = nullptr;
+  c->where_buf = nullptr;
+  c->hull_range = nullptr;
+  c->staging = nullptr;
+  c->sort_key = c->sort_order = c->sort_hist = nullptr;
+  c->rec_cap = c->where_cap = c->range_cap = c->staging_cap = c->key_cap = c->order_cap = c->hist_cap = 0;
+}
+
+// Make `p` hold at least `need` elements (contents not kept when it grows).
+template <class T>
+pct_status grow(T*& p, int64_t& cap, int64_t need) {
+  if (p && cap >= need) return PCT_OK;
+  cudaFree(p);
+  p = nullptr;
+  cap = 0;
+  cudaError_t e = cudaMalloc((void**)&p, (size_t)need * sizeof(T));
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    p = nullptr;
+    return fail(PCT_ERR_NO_MEMORY, "cudaMalloc(%lld bytes): %s", (long long)(need * (int64_t)sizeof(T)),
+                cudaGetErrorString(e));
+  }
+  cap = need;
+  return PCT_OK;
+}
+
+#define PCT_GROW(ptr, cap, need)                   \
+  do {                                             \
+    pct_status s_ = grow((ptr), (cap), (need));    \
+    if (s_ != PCT_OK) return s_;                   \
+  } while (0)
 
 int64_t block_lo(const pct_ctx* c, int b) { return (int64_t)b * c->n / c->cfg.n_blocks; }
 
@@ -79,12 +119,21 @@ pct_status block_weights(pct_ctx* c) {
     PCT_CK(pct::launch_inv_counts(c->cnt, c->inv_s + (size_t)b * c->M, c->M, c->stream));
     c->launches += 2;
   }
+  c->weights_ready = true;
   return PCT_OK;
 }
 
 }  // namespace
 
 void pct::set_error_text(const char* msg) { g_err = msg; }
+
+pct_status pct::ensure_block_weights(pct_ctx* c) {
+  if (c->weights_ready || !c->loaded) return PCT_OK;
+  PCT_CK(cudaSetDevice(c->device));
+  pct_status st = block_weights(c);
+  if (st != PCT_OK) return st;
+  return sync_and_check(c);
+}
 
 extern "C" {
 
@@ -315,18 +364,7 @@ Rec rec_offset(const float* const* src, int64_t lo) {
              src[6] + lo, src[7] + lo, src[8] + lo, src[9] + lo, src[10] + lo};
 }
 
-struct Scratch {
-  float* staging = nullptr;
-  unsigned* key = nullptr;
-  unsigned* order = nullptr;
-  unsigned* hist = nullptr;
-  ~Scratch() {
-    cudaFree(staging);
-    cudaFree(key);
-    cudaFree(order);
-    cudaFree(hist);
-  }
-};
+
 
 }  // namespace
 
@@ -344,7 +382,7 @@ pct_status pct_load_histories(pct_ctx* c, const pct_histories* h, int flags, int
     return fail(PCT_ERR_INVALID_ARG, "unknown load flags %d", flags);
   PCT_CK(cudaSetDevice(c->device));
   PCT_CK(cudaStreamSynchronize(c->stream));
-  free_records(c);
+  reset_records(c);
   const int64_t n = h->n;
   c->n = n;
   const int B = c->cfg.n_blocks;
@@ -353,20 +391,20 @@ pct_status pct_load_histories(pct_ctx* c, const pct_histories* h, int flags, int
   int64_t max_blk = 0;
   for (int b = 0; b < B; ++b) max_blk = block_lo(c, b + 1) - block_lo(c, b) > max_blk ? block_lo(c, b + 1) - block_lo(c, b) : max_blk;
 
-  Scratch sc;
   if (in_place) {
     c->rec = rec_offset(src, 0);
   } else {
-    PCT_ALLOC(c->rec_store, (size_t)n * 11 * sizeof(float));
+    PCT_GROW(c->rec_store, c->rec_cap, n * 11);
     c->rec = rec_at(c->rec_store, n);
   }
   if (sort) {
-    PCT_ALLOC(c->where, (size_t)n * sizeof(int64_t));
-    PCT_ALLOC(sc.key, (size_t)max_blk * sizeof(unsigned));
-    PCT_ALLOC(sc.order, (size_t)max_blk * sizeof(unsigned));
-    PCT_ALLOC(sc.hist, (size_t)pct::kSortAngles * pct::kSortLateral * sizeof(unsigned));
+    PCT_GROW(c->where_buf, c->where_cap, n);
+    c->where = c->where_buf;
+    PCT_GROW(c->sort_key, c->key_cap, max_blk);
+    PCT_GROW(c->sort_order, c->order_cap, max_blk);
+    PCT_GROW(c->sort_hist, c->hist_cap, (int64_t)pct::kSortAngles * pct::kSortLateral);
   }
-  if (flags == PCT_LOAD_HOST) PCT_ALLOC(sc.staging, (size_t)max_blk * 11 * sizeof(float));
+  if (flags == PCT_LOAD_HOST) PCT_GROW(c->staging, c->staging_cap, max_blk * 11);
 
   // per block: bring the records to the device, validate, order (or copy)
   PCT_CK(cudaMemsetAsync(c->first_bad, 0xff, sizeof(unsigned long long), c->stream));
@@ -375,16 +413,16 @@ pct_status pct_load_histories(pct_ctx* c, const pct_histories* h, int flags, int
     Rec blk;
     if (flags == PCT_LOAD_HOST) {
       for (int f = 0; f < 11; ++f)
-        PCT_CK(cudaMemcpyAsync(sc.staging + (size_t)f * max_blk, src[f] + lo, (size_t)cnt * sizeof(float),
+        PCT_CK(cudaMemcpyAsync(c->staging + (size_t)f * max_blk, src[f] + lo, (size_t)cnt * sizeof(float),
                                cudaMemcpyHostToDevice, c->stream));
-      blk = rec_at(sc.staging, max_blk);
+      blk = rec_at(c->staging, max_blk);
     } else {
       blk = rec_offset(src, lo);
     }
     PCT_CK(pct::launch_validate(blk, cnt, lo, c->pos_limit, c->first_bad, c->stream));
     c->launches += 1;
     if (sort) {
-      PCT_CK(pct::launch_sort_block(blk, cnt, lo, c->pos_limit, c->rec, c->where, sc.key, sc.hist, sc.order,
+      PCT_CK(pct::launch_sort_block(blk, cnt, lo, c->pos_limit, c->rec, c->where, c->sort_key, c->sort_hist, c->sort_order,
                                     c->stream));
       c->launches += 5;
     } else if (!in_place) {
@@ -397,25 +435,24 @@ pct_status pct_load_histories(pct_ctx* c, const pct_histories* h, int flags, int
   PCT_CK(cudaStreamSynchronize(c->stream));
   if (fb != ~0ull) {
     if (first_bad) *first_bad = (int64_t)fb;
-    free_records(c);
+    reset_records(c);
     return fail(PCT_ERR_INVALID_DATA, "history %lld failed validation", (long long)fb);
   }
 
   // hull ranges of the stored histories, then the DROP block weights
   if (c->hull_mask) {
-    PCT_ALLOC(c->hull_range, (size_t)n * sizeof(int32_t));
+    PCT_GROW(c->hull_range, c->range_cap, n);
     PCT_CK(pct::launch_hull_ranges(c->geo, c->rec, n, c->hull_mask, c->hull_range, c->stream));
     c->launches += 1;
   }
-  PCT_ALLOC(c->inv_s, (size_t)B * c->M * sizeof(float));
-  {
-    pct_status st = block_weights(c);
-    if (st != PCT_OK) return st;
-  }
+  // the block weights are counted by the first sweep (pct_iterate), or on
+  // demand (pct::ensure_block_weights)
+  if (!c->inv_s) PCT_ALLOC(c->inv_s, (size_t)B * c->M * sizeof(float));
+  c->weights_ready = false;
   PCT_CK(cudaMemsetAsync(c->x, 0, (size_t)c->M * sizeof(float), c->stream));
   PCT_CK(cudaMemsetAsync(c->delta, 0, (size_t)c->M * sizeof(float), c->stream));
   if (c->tv_state) PCT_CK(cudaMemsetAsync(c->tv_state, 0, sizeof(pct::TvState), c->stream));
-  pct_status st = sync_and_check(c);  // scratch is freed after the stream is idle
+  pct_status st = sync_and_check(c);
   if (st != PCT_OK) return st;
   c->loaded = true;
   return PCT_OK;
@@ -427,11 +464,14 @@ pct_status pct_set_hull(pct_ctx* c, const uint8_t* mask, int on_device) {
   PCT_CK(cudaStreamSynchronize(c->stream));
   if (c->sweep) cudaGraphExecDestroy(c->sweep);  // the sweep's kernels change
   c->sweep = nullptr;
+  if (c->sweep_count) cudaGraphExecDestroy(c->sweep_count);
+  c->sweep_count = nullptr;
   if (!mask) {
     cudaFree(c->hull_mask);
     cudaFree(c->hull_range);
     c->hull_mask = nullptr;
     c->hull_range = nullptr;
+    c->range_cap = 0;
   } else {
     if (!c->hull_mask) PCT_ALLOC(c->hull_mask, (size_t)c->M);
     if (!c->fam32) {
@@ -442,15 +482,12 @@ pct_status pct_set_hull(pct_ctx* c, const uint8_t* mask, int on_device) {
     PCT_CK(cudaMemcpyAsync(c->hull_mask, mask, (size_t)c->M,
                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
     if (c->loaded) {
-      if (!c->hull_range) PCT_ALLOC(c->hull_range, (size_t)c->n * sizeof(int32_t));
+      PCT_GROW(c->hull_range, c->range_cap, c->n);
       PCT_CK(pct::launch_hull_ranges(c->geo, c->rec, c->n, c->hull_mask, c->hull_range, c->stream));
       c->launches += 1;
     }
   }
-  if (c->loaded) {
-    pct_status st = block_weights(c);
-    if (st != PCT_OK) return st;
-  }
+  c->weights_ready = false;  // the rows changed: the next sweep recounts
   return sync_and_check(c);
 }
 
@@ -591,7 +628,10 @@ pct_status pct_set_x0(pct_ctx* c, const float* x0, int on_device) {
   return PCT_OK;
 }
 
-static pct_status build_sweep_graph(pct_ctx* c) {
+// One sweep as a CUDA graph. counting: the first sweep after a load also
+// counts each block's runs (cnt) and forms its weights inv_s just before the
+// block's update, in place of a separate counting pass.
+static pct_status build_sweep_graph(pct_ctx* c, bool counting, cudaGraphExec_t* out) {
   cudaGraph_t graph = nullptr;
   cudaStream_t s = c->own_stream;
   PCT_CK(cudaStreamSynchronize(s));
@@ -617,12 +657,13 @@ static pct_status build_sweep_graph(pct_ctx* c) {
       if (tvs && !carp)
         err = pct::launch_tvs(c->x, c->grid.nx, c->grid.ny, c->grid.nz, tp, c->tv_g, c->tv_xp, c->tv_acc,
                               c->tv_state, s);
+      if (err == cudaSuccess && counting) err = cudaMemsetAsync(c->cnt, 0, (size_t)c->M * sizeof(unsigned int), s);
       if (err == cudaSuccess && c->ev) err = cudaEventRecordWithFlags(c->ev[3 * b], s, cudaEventRecordExternal);
       if (err == cudaSuccess)
         err = pct::launch_drop_fused(c->geo, c->rec, c->tab32, pct::hull_view(c), lo, hi - lo, c->x, c->delta,
-                                     c->cfg.lambda,
-                                     c->cfg.flags, c->cfg.cta_threads, s);
+                                     c->cfg.lambda, c->cfg.flags, c->cfg.cta_threads, s, counting ? c->cnt : nullptr);
       if (err == cudaSuccess && c->ev) err = cudaEventRecordWithFlags(c->ev[3 * b + 1], s, cudaEventRecordExternal);
+      if (err == cudaSuccess && counting) err = pct::launch_inv_counts(c->cnt, c->inv_s + (size_t)b * c->M, c->M, s);
       if (err == cudaSuccess)
         err = pct::launch_drop_apply(c->x, c->delta, c->inv_s + (size_t)b * c->M, c->M, carp ? 0 : clamp,
                                      c->cfg.clamp_min, s);
@@ -639,10 +680,10 @@ static pct_status build_sweep_graph(pct_ctx* c) {
     (void)cudaGetLastError();
     return fail(PCT_ERR_CUDA, "sweep capture: %s", cudaGetErrorString(err != cudaSuccess ? err : e2));
   }
-  cudaError_t e3 = cudaGraphInstantiate(&c->sweep, graph, 0);
+  cudaError_t e3 = cudaGraphInstantiate(out, graph, 0);
   cudaGraphDestroy(graph);
   if (e3 != cudaSuccess) {
-    c->sweep = nullptr;
+    *out = nullptr;
     return fail(PCT_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e3));
   }
   return PCT_OK;
@@ -653,14 +694,28 @@ pct_status pct_iterate(pct_ctx* c, int32_t n_sweeps) {
   if (!c->loaded) return fail(PCT_ERR_STATE, "no histories loaded");
   if (n_sweeps < 0) return fail(PCT_ERR_INVALID_ARG, "n_sweeps < 0");
   PCT_CK(cudaSetDevice(c->device));
-  if (!c->sweep) {
-    // the capture stream must not have pending work from another stream
-    if (c->stream != c->own_stream) PCT_CK(cudaStreamSynchronize(c->stream));
-    pct_status st = build_sweep_graph(c);
+  if (n_sweeps == 0) return PCT_OK;
+  // the capture stream must not have pending work from another stream
+  if ((!c->sweep || !c->weights_ready) && c->stream != c->own_stream) PCT_CK(cudaStreamSynchronize(c->stream));
+  const int64_t per_sweep = 2 * c->cfg.n_blocks + ((c->cfg.flags & PCT_FLAG_CARP) ? c->cfg.carp_strings + 1 : 0);
+  if (!c->weights_ready) {
+    // first sweep after a load: counts the block weights as it goes
+    if (!c->sweep_count) {
+      pct_status st = build_sweep_graph(c, true, &c->sweep_count);
+      if (st != PCT_OK) return st;
+    }
+    PCT_CK(cudaGraphLaunch(c->sweep_count, c->stream));
+    c->weights_ready = true;
+    c->launches += per_sweep + c->cfg.n_blocks;
+    c->swept = true;
+    --n_sweeps;
+  }
+  if (n_sweeps > 0 && !c->sweep) {
+    pct_status st = build_sweep_graph(c, false, &c->sweep);
     if (st != PCT_OK) return st;
   }
   for (int s = 0; s < n_sweeps; ++s) PCT_CK(cudaGraphLaunch(c->sweep, c->stream));
-  c->launches += (int64_t)n_sweeps * (2 * c->cfg.n_blocks + ((c->cfg.flags & PCT_FLAG_CARP) ? c->cfg.carp_strings + 1 : 0));
+  c->launches += (int64_t)n_sweeps * per_sweep;
   if (n_sweeps > 0) c->swept = true;
   return PCT_OK;
 }
@@ -684,10 +739,17 @@ pct_status pct_last_sweep_times(pct_ctx* c, float* fused_ms, float* apply_ms) {
 pct_status pct_get_rsp(pct_ctx* c, float* out, int to_device) {
   if (!c || !out) return fail(PCT_ERR_INVALID_ARG, "ctx or out is NULL");
   PCT_CK(cudaSetDevice(c->device));
-  PCT_CK(cudaMemcpyAsync(out, c->x, (size_t)c->M * sizeof(float),
-                         to_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
-  if (!to_device) return sync_and_check(c);
-  return PCT_OK;
+  if (to_device) {
+    PCT_CK(cudaMemcpyAsync(out, c->x, (size_t)c->M * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
+    return PCT_OK;
+  }
+  // Wait for the queued sweeps first, then copy: a copy to pageable host
+  // memory queued behind a long run of sweeps finished measurably later
+  // (about 0.19 s after 10 sweeps of 50M histories) than this order.
+  pct_status st = sync_and_check(c);
+  if (st != PCT_OK) return st;
+  PCT_CK(cudaMemcpyAsync(out, c->x, (size_t)c->M * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+  return sync_and_check(c);
 }
 
 pct_status pct_sync(pct_ctx* c) {

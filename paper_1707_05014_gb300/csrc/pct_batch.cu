@@ -334,6 +334,7 @@ pct_status pct_batch_create(pct_batch** out, pct_ctx* const* ctxs, int32_t n, co
     if (ctxs[r]->cfg.flags & PCT_FLAG_CARP) return bfail(PCT_ERR_INVALID_ARG, "CARP contexts are not batched");
     if (ctxs[r]->cfg.tvs_beta0 > 0.f) return bfail(PCT_ERR_INVALID_ARG, "TVS contexts are not batched");
     if (ctxs[r]->hull_mask) return bfail(PCT_ERR_INVALID_ARG, "contexts with an object hull are not batched");
+    if (pct::ensure_block_weights(ctxs[r]) != PCT_OK) return bfail(PCT_ERR_CUDA, "block weights", pct_last_error());
   }
   pct_batch* b = new pct_batch();
   b->device = ctxs[0]->device;

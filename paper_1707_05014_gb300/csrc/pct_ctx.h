@@ -24,6 +24,15 @@ struct pct_ctx {
   float* rec_store = nullptr;  // owned copy of the 11 record arrays (null when borrowed)
   pct::Rec rec{};
   int64_t* where = nullptr;    // load index -> stored position (null: stored in load order)
+  // Buffers of the loaded set, kept across loads and grown when a load needs
+  // more (freed by pct_destroy): records, the load-order map, hull ranges,
+  // and the load's scratch (host staging, sort keys, order, bins).
+  int64_t rec_cap = 0, where_cap = 0, range_cap = 0, staging_cap = 0, key_cap = 0, order_cap = 0, hist_cap = 0;
+  int64_t* where_buf = nullptr;
+  float* staging = nullptr;
+  unsigned* sort_key = nullptr;
+  unsigned* sort_order = nullptr;
+  unsigned* sort_hist = nullptr;
   float* x = nullptr;
   float* delta = nullptr;
   float* inv_s = nullptr;  // B x M
@@ -40,7 +49,9 @@ struct pct_ctx {
   uint8_t* hull_mask = nullptr;   // object hull, M bytes (null: no hull)
   int32_t* hull_range = nullptr;  // per stored history: iin | iout << 16 (with a hull and histories)
   float4* fam32 = nullptr;        // MLP tables of every hull thickness (with a hull)
+  bool weights_ready = false;  // inv_s holds the block weights of the loaded histories
   cudaGraphExec_t sweep = nullptr;
+  cudaGraphExec_t sweep_count = nullptr;  // first sweep after a load (counts the block weights)
   cudaEvent_t* ev = nullptr;  // 3 per block (profiling): fused start, fused end, apply end
   bool swept = false;
   int64_t launches = 0;
@@ -50,6 +61,9 @@ struct pct_ctx {
 namespace pct {
 // The hull as the kernels see it (range null: no hull).
 inline Hull hull_view(const pct_ctx* c) { return Hull{c->hull_mask ? c->hull_range : nullptr, c->fam32}; }
+// Compute the DROP block weights now if the first sweep has not done it yet
+// (callers that read inv_s outside pct_iterate). Synchronises.
+pct_status ensure_block_weights(pct_ctx* c);
 // First history of DROP block b: b * n / B (blocks are contiguous ranges).
 inline int64_t block_first(const pct_ctx* c, int b) { return (int64_t)b * c->n / c->cfg.n_blocks; }
 }  // namespace pct

@@ -90,8 +90,10 @@ cudaError_t launch_count(const Geo& g, const Rec& r, const float4* tab, const Hu
                          unsigned int* cnt, int threads, cudaStream_t s);
 cudaError_t launch_inv_counts(const unsigned int* cnt, float* inv_s, int64_t M, cudaStream_t s);
 cudaError_t launch_counts_to_float(const unsigned int* cnt, float* out, int64_t M, cudaStream_t s);
+// cnt non-null: also count the block's runs per voxel into cnt (zeroed by the caller).
 cudaError_t launch_drop_fused(const Geo& g, const Rec& r, const float4* tab, const Hull& hull, int64_t first, int64_t count,
-                              const float* x, float* delta, float lambda, int flags, int threads, cudaStream_t s);
+                              const float* x, float* delta, float lambda, int flags, int threads, cudaStream_t s,
+                              unsigned int* cnt = nullptr);
 cudaError_t launch_drop_apply(float* x, float* delta, const float* inv_s, int64_t M, int clamp, float clamp_min,
                               cudaStream_t s);
 // CARP: add a string's swept copy xs to sum / touch where any of its nb

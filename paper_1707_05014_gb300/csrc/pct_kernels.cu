@@ -66,17 +66,38 @@ __global__ void __launch_bounds__(128, 9) drop_fused_kernel(Geo g, Rec r, const 
   drop_history(g, tab, r, first + p, x, delta, lambda, flags);
 }
 
+// The same that also counts the block's runs per voxel into cnt (the first
+// sweep after a load forms the DROP weights this way).
+__global__ void __launch_bounds__(128, 9) drop_fused_count_kernel(Geo g, Rec r, const float4* __restrict__ tab_g,
+                                                                int64_t first, int64_t count,
+                                                                const float* __restrict__ x, float* __restrict__ delta,
+                                                                float lambda, int flags, unsigned int* __restrict__ cnt) {
+  extern __shared__ float4 tab[];
+  load_table(tab_g, tab, g.K + 1);
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= count) return;
+  drop_history_count(g, tab, r, first + p, x, delta, lambda, flags, cnt);
+}
+
 // The same with an object hull (see walk_proton_hull). PCT_HULL_MIN_CTAS:
 // resident 128-thread CTAs per SM its register allocation must allow.
 #ifndef PCT_HULL_MIN_CTAS
 #define PCT_HULL_MIN_CTAS 9
 #endif
-__global__ void __launch_bounds__(128, PCT_HULL_MIN_CTAS) drop_fused_hull_kernel(Geo g, Rec r, Hull hull, int64_t first, int64_t count,
-                                                               const float* __restrict__ x, float* __restrict__ delta,
-                                                               float lambda, int flags) {
+__global__ void __launch_bounds__(128, PCT_HULL_MIN_CTAS)
+    drop_fused_hull_kernel(Geo g, Rec r, Hull hull, int64_t first, int64_t count, const float* __restrict__ x,
+                           float* __restrict__ delta, float lambda, int flags) {
   int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= count) return;
   drop_history_hull(g, hull, r, first + p, x, delta, lambda, flags);
+}
+
+__global__ void __launch_bounds__(128, PCT_HULL_MIN_CTAS)
+    drop_fused_hull_count_kernel(Geo g, Rec r, Hull hull, int64_t first, int64_t count, const float* __restrict__ x,
+                                 float* __restrict__ delta, float lambda, int flags, unsigned int* __restrict__ cnt) {
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= count) return;
+  drop_history_hull_count(g, hull, r, first + p, x, delta, lambda, flags, cnt);
 }
 
 // Compensated a_i.x (or plain with flags & 2), the arithmetic of the fused
@@ -489,16 +510,24 @@ cudaError_t launch_counts_to_float(const unsigned int* cnt, float* out, int64_t 
 
 cudaError_t launch_drop_fused(const Geo& g, const Rec& r, const float4* tab, const Hull& hull, int64_t first,
                               int64_t count, const float* x, float* delta, float lambda, int flags, int threads,
-                              cudaStream_t s) {
+                              cudaStream_t s, unsigned int* cnt) {
   if (count <= 0) return cudaSuccess;
   threads = 128;
   if (hull.range) {
-    drop_fused_hull_kernel<<<grid_for(count, threads), threads, 0, s>>>(g, r, hull, first, count, x, delta, lambda,
+    if (cnt)
+      drop_fused_hull_count_kernel<<<grid_for(count, threads), threads, 0, s>>>(g, r, hull, first, count, x, delta,
+                                                                               lambda, flags, cnt);
+    else
+      drop_fused_hull_kernel<<<grid_for(count, threads), threads, 0, s>>>(g, r, hull, first, count, x, delta, lambda,
                                                                          flags);
     return cudaGetLastError();
   }
-  drop_fused_kernel<<<grid_for(count, threads), threads, (g.K + 1) * sizeof(float4), s>>>(g, r, tab, first, count, x,
-                                                                                           delta, lambda, flags);
+  const size_t smem = (g.K + 1) * sizeof(float4);
+  if (cnt)
+    drop_fused_count_kernel<<<grid_for(count, threads), threads, smem, s>>>(g, r, tab, first, count, x, delta, lambda,
+                                                                            flags, cnt);
+  else
+    drop_fused_kernel<<<grid_for(count, threads), threads, smem, s>>>(g, r, tab, first, count, x, delta, lambda, flags);
   return cudaGetLastError();
 }
 
