@@ -148,3 +148,21 @@ def test_hull_contexts_are_not_batched(pct):
         a.set_hull(_mask(wl))
         with pytest.raises(pct.PctError):
             pct.Batch([a])
+
+
+def test_hull_set_after_sweeps_is_recounted_by_the_next_sweep(pct, oracle):
+    # sweeps without a hull, then a hull: the next sweep recounts the block
+    # weights for the hull rows and the image follows the oracle's hull DROP
+    wl = S.tiny_workload(20_000, seed=49)
+    rec = S.make_histories(wl)
+    g = wl.grid
+    hull = _mask(wl)
+    with pct.Context(g, n_blocks=5) as ctx:
+        ctx.load(rec)
+        ctx.iterate(2)
+        ctx.set_hull(hull)
+        ctx.set_x0(np.zeros(g.m, np.float32))
+        ctx.iterate(2)
+        x = ctx.get_rsp().astype(np.float64)
+    xo = oracle.drop(g, rec, 5, 2, mode=oracle.MODE_FP32, hull=hull)
+    assert np.max(np.abs(x - xo) / np.maximum(np.abs(xo), 1.0)) <= 1e-3

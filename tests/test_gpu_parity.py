@@ -236,3 +236,35 @@ def test_tvs_parity(pct, oracle, carp):
     assert err.max() <= 1e-3, err.max()
     plain = oracle.carp(wl.grid, rec, 2, 3, n_blocks=4) if carp else oracle.drop(wl.grid, rec, 4, 3)
     assert oracle.tv_value(wl.grid, x) < oracle.tv_value(wl.grid, plain)
+
+
+def test_empty_load_is_rejected(pct):
+    wl = S.tiny_workload(10, seed=12)
+    rec = {k: v[:0] for k, v in S.make_histories(wl).items()}
+    with pct.Context(wl.grid, n_blocks=1) as ctx:
+        with pytest.raises(pct.PctError) as ei:
+            ctx.load(rec)
+        assert ei.value.code == -1
+
+
+def test_reloads_of_other_sizes_match_fresh_contexts(pct, oracle):
+    # One context reloaded with growing and shrinking sets (its buffers are
+    # kept and grown across loads; the first sweep after each load counts the
+    # block weights) gives the result of a fresh context each time.
+    wl = S.tiny_workload(20_000, seed=13)
+    g = wl.grid
+    full = S.make_histories(wl)
+    with pct.Context(g, n_blocks=4) as reused:
+        for n in (5000, 20_000, 3001, 12_000):
+            rec = S.subset(full, slice(0, n))
+            reused.load(rec)
+            reused.iterate(2)
+            a = reused.get_rsp()
+            with pct.Context(g, n_blocks=4) as fresh:
+                fresh.load(rec)
+                fresh.iterate(2)
+                b = fresh.get_rsp()
+            assert np.abs(a - b).max() <= 1e-4 * max(1.0, np.abs(b).max()), n
+            # and both follow the oracle
+            xo = oracle.drop(g, rec, 4, 2, mode=oracle.MODE_FP32)
+            assert np.max(np.abs(a - xo) / np.maximum(np.abs(xo), 1.0)) <= 1e-3, n
