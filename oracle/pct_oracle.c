@@ -19,7 +19,7 @@
  * with y = (lateral position, slope), S1/S2 the scattering matrices before and
  * after the node, integrated here by 64-point Gauss-Legendre quadrature.
  *
- * Readings where the paper is silent (each listed in the design notes):
+ * Readings where the paper is silent:
  *   - 1/(beta^2 p^2)(w) is Schulte's 5th-order water polynomial for 200 MeV,
  *     w = depth from the entry plane in cm; Highland factor
  *     E0^2 (1 + 0.038 ln(L/X0))^2 / X0 with L the sub-path length.

@@ -6,7 +6,7 @@ the calls):
   2. the network gives x0' = x1 + f(x1);
   3. fallback: if the data residual |b - A x0'|^2 (on a 1/64 sample of the
      histories) is larger than that of x1, keep x1 (the plain solver's data
-     fit is the judge);
+     fit decides);
   4. further DROP sweeps from the chosen image.
 
 Training pairs are (x1, x_S): the first sweep and the plain solver's result

@@ -1,6 +1,6 @@
 """GPU parity: the CUDA path through the C ABI against the FP64 oracle.
 
-Bars (stated in the design notes):
+Bars:
 * MLP table: FP64 on both sides, |diff| <= 1e-12 (c2, c4 scaled by 2R).
 * Interior MLP nodes (Q20) and voxel index lists: bit-exact against the
   oracle's FP32-order node mode; run counts s_j bit-exact.
