@@ -139,7 +139,7 @@ def _cpu_threads():
         return os.cpu_count() or 1
 
 
-def oracle_rate(wl, n_sample: int, sweeps: int = 1):
+def oracle_rate(wl, n_sample: int, sweeps: int = 1, node_step: float = 0.0):
     """Time the FP64 CPU oracle (single thread) on the first n_sample histories
     of the workload (generated on the host with the same recipe)."""
     import oracle as O
@@ -148,7 +148,7 @@ def oracle_rate(wl, n_sample: int, sweeps: int = 1):
     rec = S.make_histories(wl, n=n_sample, seed_offset=777)
     O.build()
     t = time.perf_counter()
-    O.drop(wl.grid, rec, wl.n_blocks, sweeps, mode=O.MODE_FP32)
+    O.drop(wl.grid, rec, wl.n_blocks, sweeps, mode=O.MODE_FP32, node_step=node_step)
     dt = time.perf_counter() - t
     return n_sample * sweeps / dt, dt
 
@@ -524,7 +524,7 @@ def run_ours(args):
     torch.cuda.synchronize()
 
     flags = P.FLAG_PROFILE | (P.FLAG_NO_SORT if args.no_sort else 0)
-    ctx = P.Context(g, n_blocks=wl.n_blocks, flags=flags, device=local)
+    ctx = P.Context(g, n_blocks=wl.n_blocks, flags=flags, node_step=args.node_step, device=local)
     ctx.load(rec, borrow=True)
     hull = None
     if args.hull:  # object hull carved from the data (untimed set-up, like the load)
@@ -567,7 +567,7 @@ def run_ours(args):
     peaks, src = _peaks()
     per_block = wl.n / wl.n_blocks
     avg_fused_s = statistics.mean(fused_ms) / 1e3
-    ctx_rows = P.Context(g, n_blocks=1, device=local)  # runs per history on a sample (unit count)
+    ctx_rows = P.Context(g, n_blocks=1, node_step=args.node_step, device=local)  # runs per history (unit count)
     sample = {k: v[: min(wl.n, 200_000)] for k, v in rec.items()}
     ctx_rows.load(sample, borrow=True)
     if hull is not None:
@@ -613,7 +613,7 @@ def run_ours(args):
         del rec
         torch.cuda.empty_cache()
         ctx.close()
-        ctx2 = P.Context(g, n_blocks=wl.n_blocks, device=local)
+        ctx2 = P.Context(g, n_blocks=wl.n_blocks, node_step=args.node_step, device=local)
         xs = []
         times = []
         for i in range(1 + args.e2e_steps):
@@ -638,7 +638,7 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and args.cpu_sample > 0:
-        r, dt = oracle_rate(wl, args.cpu_sample)
+        r, dt = oracle_rate(wl, args.cpu_sample, node_step=args.node_step)
         cpu = {"value": r, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"{args.cpu_sample} histories of the same workload, 1 sweep, {wl.n_blocks} blocks "
                          f"(FP64 oracle, single thread, {dt:.1f} s)"}
@@ -648,7 +648,9 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": wl.name + ("_hull" if args.hull else ""), "grid": "160x160x64 @ 1.25 mm (1.64M voxels)",
+            "config": {"workload": wl.name + ("_hull" if args.hull else "") + (f"_step{args.node_step:g}mm" if args.node_step > 0 else ""),
+                       "grid": "160x160x64 @ 1.25 mm (1.64M voxels)",
+                       "mlp_node_step_mm": args.node_step if args.node_step > 0 else min(g.hx, g.hy, g.hz) / 2,
                        "histories_per_gpu": wl.n, "angles": 90, "n_blocks": wl.n_blocks,
                        "step": "one DROP sweep over all histories", "parallelism": f"replicas{world}",
                        "l2": "records 2.2 GB per sweep > 129 MB L2 (no flush needed); x and delta L2-resident",
@@ -676,6 +678,7 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=200_000)
     ap.add_argument("--no-sort", action="store_true", help="keep each block in load order (A/B of the ordering)")
     ap.add_argument("--hull", action="store_true", help="head / table2: MLP inside a hull carved from the data")
+    ap.add_argument("--node-step", type=float, default=0.0, help="head: MLP node spacing in mm (default min(h)/2)")
     ap.add_argument("--hull-wepl", type=float, default=1.0, help="carving: histories with WEPL <= this (mm) are air")
     ap.add_argument("--hull-dilate", type=int, default=1, help="carving: 6-neighbour growth steps of the hull")
     ap.add_argument("--workload", default="head", choices=["head", "batched", "precision", "warmstart", "table2"])
