@@ -139,18 +139,29 @@ def _cpu_threads():
         return os.cpu_count() or 1
 
 
-def oracle_rate(wl, n_sample: int, sweeps: int = 1, node_step: float = 0.0):
-    """Time the FP64 CPU oracle (single thread) on the first n_sample histories
-    of the workload (generated on the host with the same recipe)."""
-    import oracle as O
+def oracle_sample(wl, n_sample: int):
+    """n_sample histories of the workload, generated on the host with the same
+    recipe (a different seed stream from the GPU set)."""
     from paper_1707_05014_gb300 import synthetic as S
 
-    rec = S.make_histories(wl, n=n_sample, seed_offset=777)
+    return S.make_histories(wl, n=n_sample, seed_offset=777)
+
+
+def oracle_rate(wl, rec, sweeps: int = 1, node_step: float = 0.0, threads: int = 1):
+    """Time the FP64 CPU oracle's DROP on the host histories `rec`: single
+    thread (threads = 1) or each block's histories split over `threads`
+    OpenMP threads (0: all host cores). Returns (rate, seconds, threads)."""
+    import oracle as O
+
     O.build()
+    n = len(rec["t0"])
     t = time.perf_counter()
-    O.drop(wl.grid, rec, wl.n_blocks, sweeps, mode=O.MODE_FP32, node_step=node_step)
+    if threads == 1:
+        O.drop(wl.grid, rec, wl.n_blocks, sweeps, mode=O.MODE_FP32, node_step=node_step)
+    else:
+        O.drop_threads(wl.grid, rec, wl.n_blocks, sweeps, threads=threads, mode=O.MODE_FP32, node_step=node_step)
     dt = time.perf_counter() - t
-    return n_sample * sweeps / dt, dt
+    return n * sweeps / dt, dt, (1 if threads == 1 else (threads or O.max_threads()))
 
 
 def run_reference(args):
@@ -163,22 +174,25 @@ def run_reference(args):
     from paper_1707_05014_gb300 import synthetic as S
 
     wl = S.head_workload(args.n)
+    rec = oracle_sample(wl, args.ref_sample)
     rates = []
+    cores = 1
     for i in range(args.warmup + args.steps):
-        r, dt = oracle_rate(wl, args.ref_sample)
+        r, dt, cores = oracle_rate(wl, rec, threads=0)
         if i >= args.warmup:
             rates.append((r, dt))
     total_units = args.ref_sample * len(rates)
     total_t = sum(dt for _, dt in rates)
     value = total_units / total_t
-    sample = f"{args.ref_sample} histories of the {wl.name} workload, 1 sweep, {wl.n_blocks} blocks, per step"
+    sample = (f"{args.ref_sample} histories of the {wl.name} workload, 1 sweep, {wl.n_blocks} blocks, per step; "
+              f"FP64 oracle, each block's histories split over {cores} OpenMP threads")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_t / len(rates),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": wl.name, "grid": "160x160x64x1.25mm", "histories": wl.n, "n_blocks": wl.n_blocks,
                    "sample_histories": args.ref_sample},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -638,10 +652,14 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and args.cpu_sample > 0:
-        r, dt = oracle_rate(wl, args.cpu_sample, node_step=args.node_step)
-        cpu = {"value": r, "unit": UNIT, "cores": 1, "kind": "oracle",
+        crec = oracle_sample(wl, args.cpu_sample)
+        r1, dt1, _ = oracle_rate(wl, crec, node_step=args.node_step, threads=1)
+        r, dt, cores = oracle_rate(wl, crec, node_step=args.node_step, threads=0)
+        cpu = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{args.cpu_sample} histories of the same workload, 1 sweep, {wl.n_blocks} blocks "
-                         f"(FP64 oracle, single thread, {dt:.1f} s)"}
+                         f"(FP64 oracle, each block's histories split over {cores} OpenMP threads, {dt:.1f} s; "
+                         f"single thread {dt1:.1f} s)",
+               "single_thread_value": r1}
 
     if rank == 0:
         line = {
@@ -675,7 +693,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--e2e-sweeps", type=int, default=10)
     ap.add_argument("--cpu-sample", type=int, default=1_000_000)
-    ap.add_argument("--ref-sample", type=int, default=200_000)
+    ap.add_argument("--ref-sample", type=int, default=1_000_000)
     ap.add_argument("--no-sort", action="store_true", help="keep each block in load order (A/B of the ordering)")
     ap.add_argument("--hull", action="store_true", help="head / table2: MLP inside a hull carved from the data")
     ap.add_argument("--node-step", type=float, default=0.0, help="head: MLP node spacing in mm (default min(h)/2)")

@@ -48,8 +48,8 @@ def build(force: bool = False) -> str:
     os.makedirs(os.path.dirname(LIB), exist_ok=True)
     if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
         tmp = LIB + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-                               SRC, "-o", tmp, "-lm"])
+        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC",
+                               "-shared", SRC, "-o", tmp, "-lm"])
         os.replace(tmp, LIB)
     return LIB
 
@@ -105,6 +105,10 @@ def lib():
                               ctypes.c_int, dp, dp]
         L.or_drop.argtypes = [gp, dp, rp, ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                               ctypes.c_int, ctypes.c_double, dp, dp]
+        L.or_drop_threads.argtypes = [gp, dp, rp, ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                      ctypes.c_int, ctypes.c_int, dp, dp]
+        L.or_max_threads.argtypes = []
+        L.or_max_threads.restype = ctypes.c_int
     return _lib
 
 
@@ -295,6 +299,28 @@ def drop(g, rec, n_blocks: int, n_sweeps: int, lam: float = 1.0, x0: Optional[np
     if rc != 0:
         raise MemoryError("oracle drop: allocation failed")
     return (x, resid[:n_sweeps]) if return_resid else x
+
+
+def drop_threads(g, rec, n_blocks: int, n_sweeps: int, threads: int = 0, lam: float = 1.0,
+                 x0: Optional[np.ndarray] = None, mode: int = MODE_FP32, node_step: float = 0.0, hull=None):
+    """DROP as ``drop`` with each block's histories split over ``threads``
+    OpenMP threads (0: all); only the order of the sums differs."""
+    h = _RecHolder(rec)
+    tab = _tab(g, None, 0, node_step)
+    gg = _grid(g, node_step, hull)
+    M = g.nx * g.ny * g.nz
+    x = np.zeros(M) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+    resid = np.zeros(max(n_sweeps, 1))
+    rc = lib().or_drop_threads(ctypes.byref(gg), _ptr(tab, ctypes.c_double), ctypes.byref(h.s), h.n, n_blocks,
+                               float(lam), n_sweeps, mode, int(threads), _ptr(x, ctypes.c_double),
+                               _ptr(resid, ctypes.c_double))
+    if rc != 0:
+        raise MemoryError("oracle drop_threads: allocation failed")
+    return x
+
+
+def max_threads() -> int:
+    return int(lib().or_max_threads())
 
 
 def carp(g, rec, n_strings: int, n_sweeps: int, lam: float = 1.0, x0: Optional[np.ndarray] = None,

@@ -41,6 +41,9 @@
  * solver always run in double.
  */
 #include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -250,7 +253,18 @@ static double **or_fam = NULL;
 static int or_fam_K = -1;
 static double or_fam_du = 0.0, or_fam_R = 0.0;
 
+static const double *or_family_locked(const or_geom *o, int n);
+
 static const double *or_family(const or_geom *o, int n) {
+  const double *t;
+#ifdef _OPENMP
+#pragma omp critical(or_family_cache)
+#endif
+  t = or_family_locked(o, n);
+  return t;
+}
+
+static const double *or_family_locked(const or_geom *o, int n) {
   if (or_fam_K != o->K || or_fam_du != o->du || or_fam_R != o->R) {
     if (or_fam) {
       for (int i = 0; i <= or_fam_K; ++i) free(or_fam[i]);
@@ -739,6 +753,89 @@ int or_drop(const or_grid *g, const double *tab, const or_rec *r, int64_t n, int
   free(row.j);
   free(row.l);
   return 0;
+}
+
+/*
+ * The same DROP sweeps with the histories of each block split over `threads`
+ * OpenMP threads (0: all available). Each thread accumulates its own update
+ * and run counts; they are summed in thread order before the block update,
+ * so the result differs from or_drop only in the order of the sums. Used to
+ * time the oracle on all host cores.
+ */
+int or_drop_threads(const or_grid *g, const double *tab, const or_rec *r, int64_t n, int n_blocks, double lambda,
+                    int n_sweeps, int mode, int threads, double *x, double *resid) {
+#ifndef _OPENMP
+  (void)threads;
+  return or_drop(g, tab, r, n, n_blocks, lambda, n_sweeps, mode, 0, 0.0, x, resid);
+#else
+  or_geom o;
+  or_geometry(g, &o);
+  const int T = threads > 0 ? threads : omp_get_max_threads();
+  const int64_t M = (int64_t)g->nx * g->ny * g->nz;
+  double *delta = (double *)calloc((size_t)T * M, sizeof(double));
+  int32_t *cnt = (int32_t *)calloc((size_t)T * M, sizeof(int32_t));
+  if (!delta || !cnt) {
+    free(delta);
+    free(cnt);
+    return -1;
+  }
+  for (int sw = 0; sw < n_sweeps; ++sw) {
+    double rr = 0.0;
+    for (int b = 0; b < n_blocks; ++b) {
+      const int64_t lo = (int64_t)b * n / n_blocks, hi = (int64_t)(b + 1) * n / n_blocks;
+#pragma omp parallel num_threads(T) reduction(+ : rr)
+      {
+        const int t = omp_get_thread_num();
+        double *dt = delta + (size_t)t * M;
+        int32_t *ct = cnt + (size_t)t * M;
+        memset(dt, 0, M * sizeof(double));
+        memset(ct, 0, M * sizeof(int32_t));
+        or_row row = {0};
+#pragma omp for schedule(static)
+        for (int64_t i = lo; i < hi; ++i) {
+          or_walk_row(g, &o, tab, r, i, mode, &row);
+          double ax = 0.0, nn = 0.0;
+          for (int64_t q = 0; q < row.n; ++q) {
+            ax += row.l[q] * x[row.j[q]];
+            nn += row.l[q] * row.l[q];
+          }
+          if (nn <= 0.0) continue;
+          const double res = (double)r->wepl[i] - ax;
+          rr += res * res;
+          const double ri = lambda * res / nn;
+          for (int64_t q = 0; q < row.n; ++q) {
+            dt[row.j[q]] += row.l[q] * ri;
+            ct[row.j[q]] += 1;
+          }
+        }
+        free(row.j);
+        free(row.l);
+      }
+#pragma omp parallel for num_threads(T) schedule(static)
+      for (int64_t j = 0; j < M; ++j) {
+        double d = 0.0;
+        int64_t c = 0;
+        for (int t = 0; t < T; ++t) {
+          d += delta[(size_t)t * M + j];
+          c += cnt[(size_t)t * M + j];
+        }
+        if (c > 0) x[j] += d / (double)c;
+      }
+    }
+    if (resid) resid[sw] = rr;
+  }
+  free(delta);
+  free(cnt);
+  return 0;
+#endif
+}
+
+int or_max_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
 }
 
 /* ------------------------------------------------------------------ */

@@ -138,3 +138,17 @@ def test_carp_consistent_data_residual_decreases(oracle):
     x, res = oracle.carp(g, rec, 5, 30, lam=1.0, return_resid=True)
     assert np.all(np.diff(res[1:]) < 0)
     assert res[-1] < 2e-2 * res[0]
+
+
+def test_threaded_drop_equals_single_thread(oracle):
+    # The all-core oracle (histories of a block split over threads, per-thread
+    # updates summed in thread order) is the same DROP: only the order of the
+    # sums differs. With and without an object hull.
+    wl = S.tiny_workload(6000, seed=21)
+    g = wl.grid
+    rec = S.make_histories(wl)
+    hull = (S.voxelize(wl.phantom(), g, ss=1) > 0.5).astype(np.uint8)
+    for h in (None, hull):
+        a = oracle.drop(g, rec, 4, 2, hull=h)
+        b = oracle.drop_threads(g, rec, 4, 2, threads=3, hull=h)
+        assert np.abs(a - b).max() <= 1e-12 * max(1.0, np.abs(a).max())
