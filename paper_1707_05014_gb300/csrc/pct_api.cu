@@ -43,12 +43,18 @@ pct_status fail(pct_status code, const char* fmt, ...) {
     }                                                                                                 \
   } while (0)
 
-// Forget the loaded set (its buffers stay allocated for the next load).
-void reset_records(pct_ctx* c) {
+void drop_graphs(pct_ctx* c) {
   if (c->sweep) cudaGraphExecDestroy(c->sweep);
   c->sweep = nullptr;
   if (c->sweep_count) cudaGraphExecDestroy(c->sweep_count);
   c->sweep_count = nullptr;
+  c->graph_n = -1;
+}
+
+// Forget the loaded set (its buffers, and the sweep graphs, stay for the
+// next load; pct_load_histories drops the graphs if what they captured
+// changes).
+void reset_records(pct_ctx* c) {
   c->swept = false;
   c->where = nullptr;
   c->rec = Rec{};
@@ -58,6 +64,7 @@ void reset_records(pct_ctx* c) {
 }
 
 void free_records(pct_ctx* c) {
+  drop_graphs(c);
   reset_records(c);
   cudaFree(c->rec_store);
   cudaFree(c->inv_s);
@@ -445,6 +452,9 @@ pct_status pct_load_histories(pct_ctx* c, const pct_histories* h, int flags, int
     PCT_CK(pct::launch_hull_ranges(c->geo, c->rec, n, c->hull_mask, c->hull_range, c->stream));
     c->launches += 1;
   }
+  // the sweep graphs captured the record pointers, the block ranges (from n)
+  // and the hull ranges: keep them only if none of these changed
+  if (c->graph_n != n || c->graph_rec != c->rec.t0 || c->graph_range != pct::hull_view(c).range) drop_graphs(c);
   // the block weights are counted by the first sweep (pct_iterate), or on
   // demand (pct::ensure_block_weights)
   if (!c->inv_s) PCT_ALLOC(c->inv_s, (size_t)B * c->M * sizeof(float));
@@ -462,10 +472,7 @@ pct_status pct_set_hull(pct_ctx* c, const uint8_t* mask, int on_device) {
   if (!c) return fail(PCT_ERR_INVALID_ARG, "ctx is NULL");
   PCT_CK(cudaSetDevice(c->device));
   PCT_CK(cudaStreamSynchronize(c->stream));
-  if (c->sweep) cudaGraphExecDestroy(c->sweep);  // the sweep's kernels change
-  c->sweep = nullptr;
-  if (c->sweep_count) cudaGraphExecDestroy(c->sweep_count);
-  c->sweep_count = nullptr;
+  drop_graphs(c);  // the sweep's kernels change
   if (!mask) {
     cudaFree(c->hull_mask);
     cudaFree(c->hull_range);
@@ -686,6 +693,9 @@ static pct_status build_sweep_graph(pct_ctx* c, bool counting, cudaGraphExec_t* 
     *out = nullptr;
     return fail(PCT_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e3));
   }
+  c->graph_n = c->n;
+  c->graph_rec = c->rec.t0;
+  c->graph_range = pct::hull_view(c).range;
   return PCT_OK;
 }
 

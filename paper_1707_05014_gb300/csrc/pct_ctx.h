@@ -52,6 +52,11 @@ struct pct_ctx {
   bool weights_ready = false;  // inv_s holds the block weights of the loaded histories
   cudaGraphExec_t sweep = nullptr;
   cudaGraphExec_t sweep_count = nullptr;  // first sweep after a load (counts the block weights)
+  // What the two sweep graphs captured: a reload with the same history count,
+  // record storage and hull keeps them (no destroy and rebuild per load).
+  int64_t graph_n = -1;
+  const float* graph_rec = nullptr;
+  const int32_t* graph_range = nullptr;
   cudaEvent_t* ev = nullptr;  // 3 per block (profiling): fused start, fused end, apply end
   bool swept = false;
   int64_t launches = 0;
