@@ -52,3 +52,50 @@ def test_last_error_is_reported_without_gpu():
     c = pct._Config(1, 2.5, 0.0, 0, 0.0, 1, 128)
     assert L.pct_create(ctypes.byref(h), ctypes.byref(g), ctypes.byref(c), 0) == -1
     assert b"lambda" in L.pct_last_error()
+
+
+def _lib_and_types():
+    from paper_1707_05014_gb300 import build, pct
+
+    lib = pct.load_library(build.build())
+    return lib, pct
+
+
+def _cfg(pct, **kw):
+    c = dict(n_blocks=10, lam=1.0, node_step_mm=0.0, flags=0, clamp_min=0.0, threads_per_proton=1, cta_threads=128,
+             tvs_beta0=0.0, tvs_alpha=0.99, tvs_eps=1e-4, tvs_tries=4, carp_strings=0)
+    c.update(kw)
+    return pct._Config(*c.values())
+
+
+@pytest.mark.parametrize("grid,cfg,msg", [
+    ((0, 32, 32, 2.0, 2.0, 2.0), {}, "grid dims"),
+    ((600, 32, 32, 2.0, 2.0, 2.0), {}, "grid dims"),
+    ((32, 32, 32, 0.0, 2.0, 2.0), {}, "voxel sizes"),
+    ((32, 32, 32, 2.0, float("nan"), 2.0), {}, "voxel sizes"),
+    ((32, 32, 32, 2.0, 2.0, 2.0), {"n_blocks": 0}, "n_blocks"),
+    ((32, 32, 32, 2.0, 2.0, 2.0), {"lam": 2.0}, "lambda"),
+    ((32, 32, 32, 2.0, 2.0, 2.0), {"threads_per_proton": 4}, "threads_per_proton"),
+    ((32, 32, 32, 2.0, 2.0, 2.0), {"node_step_mm": 1e-3}, "node count"),
+    ((512, 512, 512, 1.0, 1.0, 1.0), {"node_step_mm": 100.0}, "fixed-point node range"),
+])
+def test_create_rejects_bad_arguments_before_touching_the_gpu(grid, cfg, msg):
+    # Argument checks run on the host before any CUDA call, so they answer the
+    # same with or without a GPU: PCT_ERR_INVALID_ARG, a message, no context.
+    lib, pct = _lib_and_types()
+    out = ctypes.c_void_p(123)
+    rc = lib.pct_create(ctypes.byref(out), ctypes.byref(pct._Grid(*grid)), ctypes.byref(_cfg(pct, **cfg)), 0)
+    assert rc == -1
+    assert msg in lib.pct_last_error().decode()
+    assert not out.value
+
+
+def test_null_pointers_are_rejected():
+    lib, pct = _lib_and_types()
+    assert lib.pct_create(None, None, None, 0) == -1
+    out = ctypes.c_void_p()
+    assert lib.pct_create(ctypes.byref(out), None, None, 0) == -1
+    assert lib.pct_measure_roofs(0, 0, None) == -1
+    assert lib.pct_destroy(None) == 0  # NULL is a no-op
+    lib.pct_drop_block_noalloc.argtypes = [ctypes.c_void_p] * 5
+    assert lib.pct_drop_block_noalloc(None, None, None, None, None) == -1
