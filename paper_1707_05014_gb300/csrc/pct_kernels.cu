@@ -1,11 +1,14 @@
 // Hot-path kernels: record validation, per-block run counts, the fused
-// MLP + DROP projection kernel, the block apply, and the CSR row export.
+// MLP + DROP projection kernel (and its first-sweep variant that also counts
+// the block weights), the block apply, CARP, TVS, projection and residual,
+// the CSR row export and the load-time ordering.
 //
 // DROP (arXiv 1707.05014 Sec. 2.1, Fig. 1), block b:
 //   for i in b:  r_i = lambda (b_i - a_i.x) / |a_i|^2,  delta += r_i a_i
 //   x_j += delta_j / s_j     (s_j = number of runs of block b in voxel j)
-// The fused kernel computes a_i twice from the MLP (once for a_i.x and
-// |a_i|^2, once for the scatter) instead of storing it.
+// The fused kernel walks each row a_i from the MLP once per sweep, keeps it
+// in thread-local memory for the gather of a_i.x and the scatter, and never
+// stores it across sweeps.
 #include "pct_drop.cuh"
 
 namespace pct {
