@@ -144,9 +144,9 @@ def head_phantom(seed: int = 0, jitter: float = 0.0) -> Phantom:
     return Phantom(RSP_AIR, tuple(parts))
 
 
-# cylinder) is a chosen one: the paper shows the phantom (Fig. 3) only as an image.
+# Inserts with the "true" RSPs of Table 2 (Sec. 4.2); the layout (a ring of
 # 12 mm cylinders at 50 mm from the axis of a 150 mm water-equivalent
-# cylinder) is this build's own, the paper's Fig. 3 being an image only.
+# cylinder) is a chosen one: the paper shows the phantom (Fig. 3) only as an image.
 CATPHAN_INSERTS = (("Teflon", 1.790), ("PMP", 0.883), ("LDPE", 0.979), ("Polystyrene", 1.024),
                    ("Delrin", 1.359), ("Air 1", 0.00113), ("Air 2", 0.00113))
 CATPHAN_BODY = 1.0
