@@ -134,7 +134,8 @@ PCT_API pct_status pct_destroy(pct_ctx *ctx);
 
 /* Use `stream` (a cudaStream_t, or the special handles cudaStreamLegacy /
  * cudaStreamPerThread; NULL = the context's own non-blocking stream) for all
- * later device work of ctx. The caller keeps the stream alive. */
+ * later device work of ctx. The caller keeps the stream alive. Switching to a
+ * different stream first waits for the work queued on the current one. */
 PCT_API pct_status pct_set_stream(pct_ctx *ctx, void *stream);
 
 /* Derived geometry: plane half-distance R (mm), node spacing du (mm),

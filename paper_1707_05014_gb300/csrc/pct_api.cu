@@ -334,7 +334,13 @@ pct_status pct_destroy(pct_ctx* c) {
 
 pct_status pct_set_stream(pct_ctx* c, void* stream) {
   if (!c) return fail(PCT_ERR_INVALID_ARG, "ctx is NULL");
-  c->stream = stream ? (cudaStream_t)stream : c->own_stream;
+  cudaStream_t next = stream ? (cudaStream_t)stream : c->own_stream;
+  if (next != c->stream) {
+    // work queued on the old stream finishes before any on the new one starts
+    PCT_CK(cudaSetDevice(c->device));
+    PCT_CK(cudaStreamSynchronize(c->stream));
+  }
+  c->stream = next;
   return PCT_OK;
 }
 
@@ -454,7 +460,9 @@ pct_status pct_load_histories(pct_ctx* c, const pct_histories* h, int flags, int
   }
   // the sweep graphs captured the record pointers, the block ranges (from n)
   // and the hull ranges: keep them only if none of these changed
-  if (c->graph_n != n || c->graph_rec != c->rec.t0 || c->graph_range != pct::hull_view(c).range) drop_graphs(c);
+  if (c->graph_n != n || memcmp(&c->graph_rec, &c->rec, sizeof(Rec)) != 0 ||
+      c->graph_range != pct::hull_view(c).range)
+    drop_graphs(c);
   // the block weights are counted by the first sweep (pct_iterate), or on
   // demand (pct::ensure_block_weights)
   if (!c->inv_s) PCT_ALLOC(c->inv_s, (size_t)B * c->M * sizeof(float));
@@ -694,7 +702,7 @@ static pct_status build_sweep_graph(pct_ctx* c, bool counting, cudaGraphExec_t* 
     return fail(PCT_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e3));
   }
   c->graph_n = c->n;
-  c->graph_rec = c->rec.t0;
+  c->graph_rec = c->rec;
   c->graph_range = pct::hull_view(c).range;
   return PCT_OK;
 }

@@ -55,7 +55,7 @@ struct pct_ctx {
   // What the two sweep graphs captured: a reload with the same history count,
   // record storage and hull keeps them (no destroy and rebuild per load).
   int64_t graph_n = -1;
-  const float* graph_rec = nullptr;
+  pct::Rec graph_rec{};  // all eleven record pointers (a borrowed load may move any of them)
   const int32_t* graph_range = nullptr;
   cudaEvent_t* ev = nullptr;  // 3 per block (profiling): fused start, fused end, apply end
   bool swept = false;

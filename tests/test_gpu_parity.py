@@ -268,3 +268,27 @@ def test_reloads_of_other_sizes_match_fresh_contexts(pct, oracle):
             # and both follow the oracle
             xo = oracle.drop(g, rec, 4, 2, mode=oracle.MODE_FP32)
             assert np.max(np.abs(a - xo) / np.maximum(np.abs(xo), 1.0)) <= 1e-3, n
+
+
+def test_borrowed_reload_with_moved_arrays_matches_fresh_context(pct):
+    # A borrowed, unsorted reload of the same size that keeps the t0 array but
+    # moves the ten others: the sweep graphs captured every record pointer, so
+    # the reused context must rebuild them and match a fresh context. The
+    # first set stays alive throughout.
+    import torch
+
+    wl = S.tiny_workload(6000, seed=14)
+    a = {k: torch.from_numpy(v).cuda() for k, v in S.make_histories(wl).items()}
+    other = S.make_histories(S.tiny_workload(6000, seed=15))
+    b = {k: (a[k] if k == "t0" else torch.from_numpy(v).cuda()) for k, v in other.items()}
+    with pct.Context(wl.grid, n_blocks=3, flags=pct.FLAG_NO_SORT) as reused:
+        reused.load(a, borrow=True)
+        reused.iterate(2)
+        reused.load(b, borrow=True)
+        reused.iterate(2)
+        x = reused.get_rsp()
+    with pct.Context(wl.grid, n_blocks=3, flags=pct.FLAG_NO_SORT) as fresh:
+        fresh.load(b, borrow=True)
+        fresh.iterate(2)
+        y = fresh.get_rsp()
+    assert np.abs(x - y).max() <= 1e-4 * max(1.0, np.abs(y).max())
