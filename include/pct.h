@@ -298,7 +298,8 @@ typedef struct pct_batch_config {
 
 /* Group n loaded contexts (same device) for batched sweeps. cfg may be NULL
  * (defaults). The contexts must outlive the batch and must not be reloaded
- * while it exists. DROP contexts without TVS only. */
+ * or given a hull while it exists (pct_batch_iterate and pct_batch_autotune
+ * then return PCT_ERR_STATE). DROP contexts without TVS only. */
 PCT_API pct_status pct_batch_create(pct_batch **out, pct_ctx *const *ctxs, int32_t n, const pct_batch_config *cfg);
 PCT_API pct_status pct_batch_destroy(pct_batch *batch);
 

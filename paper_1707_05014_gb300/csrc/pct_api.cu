@@ -396,6 +396,7 @@ pct_status pct_load_histories(pct_ctx* c, const pct_histories* h, int flags, int
   PCT_CK(cudaSetDevice(c->device));
   PCT_CK(cudaStreamSynchronize(c->stream));
   reset_records(c);
+  ++c->generation;
   const int64_t n = h->n;
   c->n = n;
   const int B = c->cfg.n_blocks;
@@ -481,6 +482,7 @@ pct_status pct_set_hull(pct_ctx* c, const uint8_t* mask, int on_device) {
   PCT_CK(cudaSetDevice(c->device));
   PCT_CK(cudaStreamSynchronize(c->stream));
   drop_graphs(c);  // the sweep's kernels change
+  ++c->generation;
   if (!mask) {
     cudaFree(c->hull_mask);
     cudaFree(c->hull_range);

@@ -151,6 +151,7 @@ __global__ void __launch_bounds__(kThreads, 6) batch_kernel(const ReconDesc* __r
 struct pct_batch {
   int device = 0;
   std::vector<pct_ctx*> ctx;
+  std::vector<uint64_t> gen;  // each context's generation when the batch was made
   pct_batch_config cfg{};
   int n_sms = 0;
   int max_ctas_per_sm = 0;
@@ -289,6 +290,17 @@ pct_status enqueue_branches(pct_batch* b, int n_sweeps, cudaStream_t s) {
 
 pct_status enqueue_any(pct_batch* b, int n_sweeps, cudaStream_t s, long long spin_limit);
 
+// The descriptors and the plan hold each context's record pointers, block
+// ranges and weights as they were at pct_batch_create: refuse to run on a
+// context reloaded or given a hull since.
+pct_status check_contexts(const pct_batch* b) {
+  for (size_t r = 0; r < b->ctx.size(); ++r)
+    if (!b->ctx[r]->loaded || b->ctx[r]->generation != b->gen[r])
+      return bfail(PCT_ERR_STATE, "a context was reloaded or given a hull after pct_batch_create",
+                   "create the batch again");
+  return PCT_OK;
+}
+
 long long spin_limit_of(const pct_batch* b) {
   const double lim = b->cfg.wait_limit_s > 0 ? b->cfg.wait_limit_s : 2.0;
   return (long long)(lim / 300e-9) + 1;  // ~300 ns per polling round (256 ns sleep + read)
@@ -339,6 +351,7 @@ pct_status pct_batch_create(pct_batch** out, pct_ctx* const* ctxs, int32_t n, co
   pct_batch* b = new pct_batch();
   b->device = ctxs[0]->device;
   b->ctx.assign(ctxs, ctxs + n);
+  for (int r = 0; r < n; ++r) b->gen.push_back(ctxs[r]->generation);
   if (cfg) b->cfg = *cfg;
   pct_status st = PCT_OK;
   do {
@@ -419,6 +432,8 @@ pct_status pct_batch_destroy(pct_batch* b) {
 pct_status pct_batch_iterate(pct_batch* b, int32_t n_sweeps, void* stream) {
   if (!b) return bfail(PCT_ERR_INVALID_ARG, "batch is NULL");
   if (n_sweeps < 0) return bfail(PCT_ERR_INVALID_ARG, "n_sweeps < 0");
+  pct_status cs = check_contexts(b);
+  if (cs != PCT_OK) return cs;
   if (n_sweeps == 0) return PCT_OK;
   PCT_BCK(cudaSetDevice(b->device));
   cudaStream_t s = stream ? (cudaStream_t)stream : b->own_stream;
@@ -463,6 +478,8 @@ pct_status pct_batch_sync(pct_batch* b, void* stream) {
 
 pct_status pct_batch_autotune(pct_batch* b, pct_batch_config* chosen, float* best_ms) {
   if (!b) return bfail(PCT_ERR_INVALID_ARG, "batch is NULL");
+  pct_status cs = check_contexts(b);
+  if (cs != PCT_OK) return cs;
   PCT_BCK(cudaSetDevice(b->device));
   cudaStream_t s = b->own_stream;
   // save every x: the trial sweeps change them

@@ -61,6 +61,7 @@ struct pct_ctx {
   bool swept = false;
   int64_t launches = 0;
   bool loaded = false;
+  uint64_t generation = 0;  // bumped by every load and hull change (a batch checks it)
 };
 
 namespace pct {

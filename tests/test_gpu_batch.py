@@ -98,3 +98,24 @@ def test_bounded_wait_reports_timeout_and_gpu_stays_usable(P):
     c.iterate(1)
     assert np.isfinite(c.get_rsp()).all()
     c.close()
+
+
+def test_batch_refuses_a_reloaded_context(P):
+    # the batch holds each context's records and block ranges as they were at
+    # creation: after a reload (or a hull) it reports a state error, and a new
+    # batch over the reloaded context runs
+    w = S.tiny_workload(8000, seed=55)
+    rec = S.make_histories(w)
+    with P.Context(w.grid, n_blocks=2) as c:
+        c.load(rec)
+        with P.Batch([c]) as b:
+            b.iterate(1)
+            b.sync()
+            c.load(S.subset(rec, slice(0, 5000)))
+            with pytest.raises(P.PctError) as ei:
+                b.iterate(1)
+            assert ei.value.code == -7  # PCT_ERR_STATE
+        with P.Batch([c]) as b:
+            b.iterate(1)
+            b.sync()
+        assert np.isfinite(c.get_rsp()).all()
