@@ -151,6 +151,17 @@ def _torch():
     return torch
 
 
+def _check_vector(a, n: int, what: str, device: Optional[int] = None) -> None:
+    """Raise ValueError unless `a` is a 1-D array or tensor of n values (and,
+    for a CUDA tensor, on `device`): the library reads exactly n values from
+    the pointer it is given."""
+    shape = tuple(a.shape) if hasattr(a, "shape") else (len(a),)
+    if len(shape) != 1 or shape[0] != n:
+        raise ValueError(f"{what}: expected {n} values, got shape {shape}")
+    if device is not None and _is_tensor(a) and a.is_cuda and a.device.index != device:
+        raise ValueError(f"{what}: tensor on cuda:{a.device.index}, context on cuda:{device}")
+
+
 def _is_tensor(a) -> bool:
     try:
         import torch
@@ -233,11 +244,14 @@ class Context:
         or used in place with ``borrow=True``; the caller keeps them alive)."""
         arrs = [rec[f] for f in FIELDS]
         n = len(arrs[0])
-        if _is_tensor(arrs[0]) and arrs[0].is_cuda:
+        on_gpu = [_is_tensor(a) and a.is_cuda for a in arrs]
+        for f, a in zip(FIELDS, arrs):
+            _check_vector(a, n, f"history array {f!r}", self.device)
+        if any(on_gpu) and not all(on_gpu):
+            raise ValueError("history arrays must be all CUDA tensors or all host arrays")
+        if on_gpu[0]:
             torch = _torch()
             arrs = [a.to(torch.float32).contiguous() for a in arrs]
-            if not all(a.is_cuda for a in arrs):
-                raise ValueError("tensors must all be on the same device")
             ptrs = [a.data_ptr() for a in arrs]
             flags = LOAD_DEVICE_BORROW if borrow else LOAD_DEVICE_COPY
         elif _is_tensor(arrs[0]):  # host tensors (e.g. pinned): copied by the library
@@ -286,6 +300,10 @@ class Context:
     def set_hull(self, mask) -> None:
         """Object hull (M values, nonzero = inside; numpy or CUDA tensor), or
         None to remove it."""
+        if mask is not None:
+            if not _is_tensor(mask):
+                mask = np.asarray(mask)
+            _check_vector(mask.reshape(-1), self.M, "hull mask", self.device)
         self._bind_stream()
         if mask is None:
             _check(self._L.pct_set_hull(self._h, None, 0))
@@ -294,8 +312,6 @@ class Context:
             _check(self._L.pct_set_hull(self._h, ctypes.c_void_p(m.data_ptr()), 1))
         else:
             m = np.ascontiguousarray(np.asarray(mask).reshape(-1) != 0, dtype=np.uint8)
-            if m.size != self.M:
-                raise ValueError("hull mask must hold one value per voxel")
             _check(self._L.pct_set_hull(self._h, m.ctypes.data_as(ctypes.c_void_p), 0))
 
     def carve_hull(self, wepl_max: float, dilate: int = 1) -> None:
@@ -348,13 +364,16 @@ class Context:
         return out
 
     def set_x0(self, x0) -> None:
+        _check_vector(x0.reshape(-1) if hasattr(x0, "reshape") else x0, self.M, "x0", self.device)
+        if _is_tensor(x0) and not x0.is_cuda:
+            x0 = x0.numpy()
         self._bind_stream()
         if _is_tensor(x0):
             x0 = x0.to(_torch().float32).contiguous()
             _check(self._L.pct_set_x0(self._h, ctypes.c_void_p(x0.data_ptr()), 1))
             self._x0_keep = x0
         else:
-            a = np.ascontiguousarray(x0, dtype=np.float32)
+            a = np.ascontiguousarray(np.asarray(x0).reshape(-1), dtype=np.float32)
             _check(self._L.pct_set_x0(self._h, a.ctypes.data_as(ctypes.c_void_p), 0))
 
     def iterate(self, n_sweeps: int) -> None:
@@ -486,6 +505,15 @@ class Net:
     def __exit__(self, *a):
         self.close()
 
+    def _volume(self, t, what: str):
+        """t as a contiguous float32 CUDA tensor of nz*ny*nx values on the
+        network's device (the library reads exactly that many)."""
+        m = self.shape[0] * self.shape[1] * self.shape[2]
+        if not (_is_tensor(t) and t.is_cuda):
+            raise ValueError(f"{what}: expected a CUDA tensor")
+        _check_vector(t.reshape(-1), m, what, self.device)
+        return t.to(_torch().float32).contiguous()
+
     def _x0(self):
         torch = _torch()
         if self._scratch is None:
@@ -500,12 +528,12 @@ class Net:
 
     def set_params(self, p: np.ndarray) -> None:
         a = np.ascontiguousarray(p, dtype=np.float32)
-        assert a.size == self.n_params
+        _check_vector(a.reshape(-1), self.n_params, "network parameters")
         _check(self._L.pct_net_set_params(self._h, a.ctypes.data_as(ctypes.c_void_p)))
 
     def forward(self, x1):
         torch = _torch()
-        x1 = x1.to(torch.float32).contiguous()
+        x1 = self._volume(x1, "x1")
         x0 = torch.empty_like(x1)
         _check(self._L.pct_net_forward(self._h, ctypes.c_void_p(x1.data_ptr()), ctypes.c_void_p(x0.data_ptr()),
                                        _stream_ptr()))
@@ -513,8 +541,8 @@ class Net:
 
     def gradients(self, x1, target):
         torch = _torch()
-        x1 = x1.to(torch.float32).contiguous()
-        target = target.to(torch.float32).contiguous()
+        x1 = self._volume(x1, "x1")
+        target = self._volume(target, "target")
         torch.cuda.synchronize()
         g = np.empty(self.n_params, dtype=np.float32)
         loss = ctypes.c_double(0.0)
@@ -524,6 +552,8 @@ class Net:
         return loss.value, g
 
     def train_step(self, x1, target, lr: float = 1e-3, want_loss: bool = True):
+        x1 = self._volume(x1, "x1")
+        target = self._volume(target, "target")
         loss = ctypes.c_double(0.0)
         _check(self._L.pct_net_train_step(self._h, ctypes.c_void_p(x1.data_ptr()), ctypes.c_void_p(target.data_ptr()),
                                           ctypes.c_void_p(self._x0().data_ptr()), float(lr),
