@@ -292,3 +292,23 @@ def test_borrowed_reload_with_moved_arrays_matches_fresh_context(pct):
         fresh.iterate(2)
         y = fresh.get_rsp()
     assert np.abs(x - y).max() <= 1e-4 * max(1.0, np.abs(y).max())
+
+
+def test_sweeps_on_a_side_stream_are_ordered_before_later_calls(pct):
+    # sweeps queued on another torch stream, then the image read on the default
+    # stream: switching streams waits for the old one, so the read sees all sweeps
+    import torch
+
+    wl = S.tiny_workload(20_000, seed=16)
+    rec = S.make_histories(wl)
+    with pct.Context(wl.grid, n_blocks=4) as ref:
+        ref.load(rec)
+        ref.iterate(3)
+        a = ref.get_rsp()
+    side = torch.cuda.Stream()
+    with pct.Context(wl.grid, n_blocks=4) as ctx:
+        ctx.load(rec)
+        with torch.cuda.stream(side):
+            ctx.iterate(3)
+        b = ctx.get_rsp()
+    assert np.abs(a - b).max() <= 1e-4 * max(1.0, np.abs(a).max())
