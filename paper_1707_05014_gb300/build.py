@@ -2,7 +2,10 @@
 
 Each .cu file compiles to an object in parallel; nvcc links them into one
 shared library with the CUDA runtime linked statically. The output lands in
-``paper_1707_05014_gb300/_build/`` (git-ignored).
+``paper_1707_05014_gb300/_build/`` (git-ignored). Objects and the library are
+written under per-process names and the library is renamed into place, so
+builds started by several processes at once do not overwrite each other's
+files.
 """
 from __future__ import annotations
 
@@ -55,9 +58,9 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     objs = []
     cmds = []
     for src in sources():
-        obj = os.path.join(OUT_DIR, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(OUT_DIR, f"{os.path.basename(src)[:-3]}.{os.getpid()}.o")
         objs.append(obj)
-        cmds.append([nv, *ARCH, *NVFLAGS, *extra, "-dc" if False else "-c", src, "-o", obj])
+        cmds.append([nv, *ARCH, *NVFLAGS, *extra, "-c", src, "-o", obj])
 
     def run(cmd):
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -72,6 +75,8 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     tmp = LIB + f".{os.getpid()}.tmp"
     link = [nv, *ARCH, "-shared", "-cudart", "static", *objs, "-o", tmp]
     r = subprocess.run(link, capture_output=True, text=True)
+    for obj in objs:
+        os.remove(obj)
     if r.returncode != 0:
         sys.stderr.write(r.stdout + r.stderr)
         raise RuntimeError("link failed")
