@@ -2,25 +2,35 @@
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline
 and reference legs may import this package. It wraps ``pct_oracle.c`` (plain C,
-FP64, single thread) through ctypes; it shares no code with the CUDA library.
+FP64, single-threaded except ``drop_threads``) through ctypes; it shares no
+code with the CUDA library.
 
 Functions (all follow arXiv 1707.05014 Sec. 2 / 2.1 and the MLP form of
 Schulte et al. 2008 that Sec. 2 cites):
 
 * ``mlp_table``   -- per-node coefficients (c1, c2, c3, c4), Sec. 2 (MLP).
+* ``mlp_table_n`` -- the same for a water layer of n node intervals (object hull).
 * ``nodes``       -- quantised interior MLP nodes (FP64 or FP32-mirror order).
 * ``rows``        -- CSR rows of A: voxel indices and chord lengths, Sec. 2.
 * ``project``     -- a_i . x for a range of protons.
 * ``block_counts``-- s_j of one DROP block.
 * ``drop``        -- DROP sweeps, Sec. 2.1 / Fig. 1.
+* ``drop_threads``-- the same sweeps with each block split over OpenMP threads
+  (sums in another order; used to time the oracle on all host cores).
 * ``carp``        -- CARP sweeps, Sec. 2.2 / Fig. 2 (strings + component averaging).
 * ``solve_tvs``   -- DROP / CARP with total-variation superiorization, Sec. 4.2.
+* ``hull_ranges``, ``carve_hull`` -- MLP inside an object hull: per-history
+  hull entry/exit nodes, and the hull carved from low-WEPL histories.
 
-Pins (tests/test_oracle_*.py): table identities (translation / straight-line
-invariance, depth reversal), the constant-scattering special case against the
-cubic Hermite interpolant, quadrature against closed-form polynomial integrals,
-straight-line walks, brute-force supersampled chords, total chord = clipped
-polyline length, and DROP against a dense weighted least-squares solve.
+Pins (tests/test_oracle_*.py): the energy polynomial against the relativistic
+entry value and a Bethe-stopping integration in water, table identities
+(translation / straight-line invariance, depth reversal), the
+constant-scattering special case against the cubic Hermite interpolant, the
+table against the Gaussian-conditioning form, quadrature against closed-form
+polynomial integrals, straight-line and tie-rule walks, brute-force
+supersampled chords, total chord = clipped polyline length, DROP against a
+dense weighted least-squares solve and the one-row ART projection, hull layer
+tables, ranges and carving against independent re-derivations.
 """
 from __future__ import annotations
 
