@@ -12,6 +12,8 @@ Schulte et al. 2008 that Sec. 2 cites):
 * ``mlp_table_n`` -- the same for a water layer of n node intervals (object hull).
 * ``nodes``       -- quantised interior MLP nodes (FP64 or FP32-mirror order).
 * ``rows``        -- CSR rows of A: voxel indices and chord lengths, Sec. 2.
+* ``reentries``   -- how often a row re-enters a voxel (where run counts and the
+  textbook one-entry-per-voxel row differ).
 * ``project``     -- a_i . x for a range of protons.
 * ``block_counts``-- s_j of one DROP block.
 * ``drop``        -- DROP sweeps, Sec. 2.1 / Fig. 1.
@@ -267,6 +269,26 @@ def rows(g, rec, first: int = 0, count: Optional[int] = None, mode: int = MODE_F
         if need <= cap:
             return rp, vox[:need].copy(), ln[:need].copy()
         cap = int(need)
+
+
+def reentries(g, rec, first: int = 0, count: Optional[int] = None, mode: int = MODE_FP32, node_step: float = 0.0,
+              hull=None) -> Dict[str, int]:
+    """How often a row returns to a voxel it has already left (Sec. 2 rows).
+
+    Runs are maximal stretches in one voxel, and the convention here counts
+    runs: s_j = runs in voxel j over a block, |a_i|^2 = sum of squared run
+    lengths. Both equal the textbook row (one entry per voxel) exactly when no
+    row re-enters a voxel; this reports how often one does. Returns the number
+    of rows, of rows with a re-entered voxel, of runs, and of runs beyond the
+    first in their voxel."""
+    rp, vox, _ = rows(g, rec, first, count, mode=mode, node_step=node_step, hull=hull)
+    n = len(rp) - 1
+    M = int(g.nx) * int(g.ny) * int(g.nz)
+    row = np.repeat(np.arange(n, dtype=np.int64), np.diff(rp))
+    keys = np.unique(row * M + vox.astype(np.int64))
+    distinct = np.bincount(keys // M, minlength=n)
+    return {"rows": n, "rows_with_reentry": int(np.count_nonzero(distinct < np.diff(rp))),
+            "runs": int(len(vox)), "repeated_runs": int(len(vox) - len(keys))}
 
 
 def project(g, rec, x: np.ndarray, first: int = 0, count: Optional[int] = None, mode: int = MODE_FP32, table=None,

@@ -192,3 +192,33 @@ def test_fp64_and_fp32_rows_agree_except_near_ties(oracle):
     assert np.median(d) < 1e-5
     assert np.percentile(d, 99) < 1e-4
     assert d.max() < 1e-2
+
+
+def test_reentry_count_on_a_path_that_bulges_over_a_face(oracle):
+    # One voxel column along the beam (nx = 1, hx = 64 mm) and a path that
+    # starts and ends 0.05 mm below the face y = 0 with slopes +-0.01: the MLP
+    # bulges about 0.16 mm over the face and comes back, so the row is
+    # (iy 15, iy 16, iy 15) and voxel iy 15 is re-entered once.
+    g = S.Grid(1, 32, 4, 64.0, 2.0, 2.0)
+    r = S.straight_records(g, [-0.05], [0.3], [0.01], [0.0], [0.0])
+    r["t2"][:] = np.float32(-0.05)
+    r["st2"][:] = np.float32(-0.01)
+    rp, vox, ln = oracle.rows(g, r)
+    ix, iy, iz = _split(g, vox)
+    assert list(iy) == [15, 16, 15] and np.all(ix == 0) and np.all(iz == 2)
+    assert oracle.reentries(g, r) == {"rows": 1, "rows_with_reentry": 1, "runs": 3, "repeated_runs": 1}
+    # the straight path through the same points never re-enters
+    s = S.straight_records(g, [-0.05], [0.3], [0.0], [0.0], [0.0])
+    assert oracle.reentries(g, s) == {"rows": 1, "rows_with_reentry": 0, "runs": 1, "repeated_runs": 0}
+
+
+@pytest.mark.parametrize("wl", [S.tiny_workload(20_000, seed=3), S.head_workload(20_000, seed=4)],
+                         ids=["water", "head"])
+def test_reentry_is_rare_on_the_workloads(oracle, wl):
+    # run counts and squared-run norms equal the textbook row definitions
+    # except on rows that re-enter a voxel; on the workloads that is a few in
+    # 1e5 rows (the oracle's count on 2e5 rows: water 4, head 1)
+    r = oracle.reentries(wl.grid, S.make_histories(wl))
+    print(wl.name, r)
+    assert r["rows_with_reentry"] <= 1e-3 * r["rows"]
+    assert r["repeated_runs"] <= 1e-4 * r["runs"]
