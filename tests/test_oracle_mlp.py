@@ -201,3 +201,47 @@ def test_straight_measurement_gives_straight_nodes(oracle):
         v = float(rec["v0"][i]) + float(rec["sv0"][i]) * (u + R)
         ref = np.stack([(u * c - t * s) / g.hx + g.nx / 2, (u * s + t * c) / g.hy + g.ny / 2, v / g.hz + g.nz / 2], 1)
         assert np.abs(q[i] - ref).max() < 5e-6
+
+
+@pytest.mark.slow
+def test_table_is_the_conditional_mean_of_a_simulated_scattering_walk(oracle):
+    # Independent of the estimator's formula: simulate lateral multiple
+    # scattering as a random walk whose slope variance grows at a rate
+    # proportional to 1/(beta^2 p^2)(depth) (the same energy polynomial, pinned
+    # above), draw 200k walks across the 200 mm slab of the head grid, and
+    # regress the position at interior nodes on (t0, s0, t2, s2). For this
+    # Gaussian process the conditional mean is linear in the four measurements
+    # and the regression recovers it, so the coefficients must match the
+    # oracle's table without the Highland log term (the log term depends on
+    # the whole sub-path length and is not a property of such a walk) within a
+    # few standard errors; the table with scattering held at its entry value
+    # must not (it is off by about a hundred standard errors).
+    g = S.Grid(160, 160, 8, 1.25, 1.25, 1.25)
+    R, du, K, _ = oracle.geom_info(g)
+    tab = oracle.mlp_table(g, flags=oracle.F_NO_LOG)
+    flat = oracle.mlp_table(g, flags=oracle.F_NO_LOG | oracle.F_CONST_SCATTER)
+    rng = np.random.Generator(np.random.Philox(7))
+    n = 200_000
+    t0, s0 = rng.normal(0.0, 1.0, n), rng.normal(0.0, 0.01, n)
+    t, s = t0.copy(), s0.copy()
+    q0, f0 = 1e-4 / (2 * R), oracle.inv_beta2p2(0.0)
+    probe = (K // 4, K // 2, 3 * K // 4)
+    at = {}
+    for k in range(K):
+        # one exact step of ds = sqrt(q) dW, dt = s du over du, with q taken at
+        # the step's mid-depth (it changes by < 1 % over a step)
+        q = q0 * oracle.inv_beta2p2((k + 0.5) * du / 10.0) / f0
+        z1, z2 = rng.standard_normal(n), rng.standard_normal(n)
+        t += s * du + math.sqrt(q * du**3) * (0.5 * z1 + z2 / math.sqrt(12.0))
+        s += math.sqrt(q * du) * z1
+        if k + 1 in probe:
+            at[k + 1] = t.copy()
+    X = np.stack([t0, s0, t, s], axis=1)
+    worst_flat = 0.0
+    for k in probe:
+        c = np.linalg.lstsq(X, at[k], rcond=None)[0]
+        resid = at[k] - X @ c
+        se = np.sqrt(np.diag(np.linalg.inv(X.T @ X)) * resid.var())
+        assert np.all(np.abs(c - tab[k]) <= 5.0 * se), (k, c, tab[k], se)
+        worst_flat = max(worst_flat, float(np.max(np.abs(c - flat[k]) / se)))
+    assert worst_flat > 30.0
