@@ -103,9 +103,10 @@ typedef struct pct_config {
                                up to floating-point summation order)          */
 
 /* One history per index: entry state at u = -R, exit state at u = +R, the
- * WEPL b_i (mm) and the gantry angle as cos/sin (Sec. 2: "entry position and
- * direction", "exit position and direction", WEPL). Eleven float arrays of n
- * elements each (structure of arrays). */
+ * WEPL b_i (mm) and the gantry angle as cos/sin (Sec. 2: each proton is
+ * measured by its position and direction before and after the object, and
+ * by its WEPL). Eleven float arrays of n elements each (structure of
+ * arrays). */
 typedef struct pct_histories {
   int64_t n;
   const float *t0, *v0, *st0, *sv0; /* lateral / vertical position and slope at u = -R */

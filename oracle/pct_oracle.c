@@ -1018,7 +1018,7 @@ int or_tvs_apply(const or_grid *g, or_tvs *p, double *x) {
 
 /*
  * DROP (or_drop) with a TVS perturbation of the image entering every block
- * (Sec. 4.2: "applied to the initial solution that enters each block"), or
+ * (Sec. 4.2 applies TVS to the image each DROP block starts from), or
  * CARP with `carp` strings (carp > 0) with one perturbation at the start of
  * every iteration.
  */
