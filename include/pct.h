@@ -49,8 +49,8 @@ typedef int pct_status;
 #define PCT_ERR_TIMEOUT (-6)      /* a bounded device-side wait ran out          */
 #define PCT_ERR_STATE (-7)        /* call out of order (e.g. iterate before load) */
 
-/* Voxel grid: nx*ny*nz voxels of hx*hy*hz mm (Sec. 2: "a discrete rectangular
- * grid of M voxels"). Each of nx, ny, nz must lie in [1, 512]. */
+/* Voxel grid: nx*ny*nz voxels of hx*hy*hz mm (Sec. 2: the RSP is sought on a
+ * box of M voxels). Each of nx, ny, nz must lie in [1, 512]. */
 typedef struct pct_grid {
   int32_t nx, ny, nz;
   double hx, hy, hz;
