@@ -91,6 +91,9 @@ static void or_geometry(const or_grid *g, or_geom *o) {
   o->E = (int)ceil((0.5 * sqrt(X * X + Y * Y) - o->R) / o->du) + 2;
 }
 
+/* Planes at u = -R and +R, node spacing du, K node intervals between the
+ * planes and E extension nodes on each side (Sec. 2 fixes none of these; the
+ * readings are listed in the header comment). */
 int or_geom_info(const or_grid *g, double *R, double *du, int *K, int *E) {
   or_geom o;
   or_geometry(g, &o);
@@ -109,7 +112,8 @@ static const double OR_A[6] = {7.457e-6, 4.548e-7, -5.777e-8, 1.301e-8, -9.228e-
 static const double OR_E0 = 13.6;  /* MeV  */
 static const double OR_X0 = 36.08; /* cm, radiation length of water */
 
-/* 1/(beta^2 p^2) at water depth w (cm), MeV^-2 */
+/* 1/(beta^2 p^2) at water depth w (cm), MeV^-2: the 200 MeV water polynomial
+ * of the MLP formalism that Sec. 2 cites */
 double or_inv_beta2p2(double w, int flags) {
   if (flags & OR_F_CONST_SCATTER) return OR_A[0];
   double s = 0.0, wp = 1.0;
@@ -155,7 +159,8 @@ void or_gauss_legendre(int n, double *x, double *w) {
 static double or_glx[OR_NGL], or_glw[OR_NGL];
 static int or_gl_ready = 0;
 
-/* integral over w in [a, b] of (c - w)^m / (beta^2 p^2)(w) dw */
+/* integral over w in [a, b] of (c - w)^m / (beta^2 p^2)(w) dw: the moments
+ * that make up the MLP's scattering matrices (Sec. 2, cited formalism) */
 double or_moment(double a, double b, double c, int m, int flags) {
   if (!or_gl_ready) {
     or_gauss_legendre(OR_NGL, or_glx, or_glw);
@@ -228,8 +233,8 @@ static void or_table_fill(double W, double du, int n, int flags, double *out) {
   }
 }
 
-/* MLP table between the measurement planes (the whole slab, W = 2R): nodes
- * k = 0..K at depth u_k. out: (K+1)*4. */
+/* MLP table between the measurement planes (Sec. 2; the whole slab, W = 2R):
+ * nodes k = 0..K at depth u_k. out: (K+1)*4. */
 int or_mlp_table(const or_grid *g, int flags, double *out) {
   or_geom o;
   or_geometry(g, &o);
@@ -237,7 +242,8 @@ int or_mlp_table(const or_grid *g, int flags, double *out) {
   return o.K;
 }
 
-/* Table of a hull of n node intervals (thickness n du; n = K is the slab). */
+/* Table of a hull of n node intervals (thickness n du; n = K is the slab):
+ * the cited MLP estimator run inside the object only (Sec. 2). */
 static double or_layer_cm(const or_geom *o, int n) { return n == o->K ? 2.0 * o->R / 10.0 : n * o->du / 10.0; }
 
 int or_mlp_table_n(const or_grid *g, int flags, int n, double *out) {
@@ -431,7 +437,8 @@ static void or_node(const or_grid *g, const or_geom *o, const or_path *p, const 
   }
 }
 
-/* Hull entry/exit nodes of protons [first, first+count): out (count, 2). */
+/* Hull entry/exit nodes of protons [first, first+count): out (count, 2)
+ * (where the MLP of Sec. 2 starts and ends with an object hull). */
 int or_hull_ranges(const or_grid *g, const double *tab, const or_rec *r, int64_t first, int64_t count, int mode,
                    int32_t *out) {
   or_geom o;
@@ -445,7 +452,8 @@ int or_hull_ranges(const or_grid *g, const double *tab, const or_rec *r, int64_t
   return 0;
 }
 
-/* Interior nodes k = 0..K of protons [first, first+count): out (count, K+1, 3) */
+/* MLP nodes k = 0..K of protons [first, first+count) (Sec. 2), quantised:
+ * out (count, K+1, 3) */
 int or_nodes(const or_grid *g, const double *tab, const or_rec *r, int64_t first, int64_t count, int mode,
              int32_t *out) {
   or_geom o;
@@ -458,7 +466,8 @@ int or_nodes(const or_grid *g, const double *tab, const or_rec *r, int64_t first
   return 0;
 }
 
-/* All polyline nodes k = -E..K+E of proton i: out (K + 2E + 1, 3) */
+/* All polyline nodes k = -E..K+E of proton i (the MLP of Sec. 2 with its
+ * straight extensions): out (K + 2E + 1, 3) */
 int or_polyline(const or_grid *g, const double *tab, const or_rec *r, int64_t i, int mode, int32_t *out) {
   or_geom o;
   or_geometry(g, &o);
@@ -597,7 +606,8 @@ static void or_walk_row(const or_grid *g, const or_geom *o, const double *tab, c
 }
 
 /*
- * Rows of protons [first, first+count) in CSR form. row_ptr has count+1
+ * Rows of A (Sec. 2: the path length of each proton in every voxel it
+ * touches) for protons [first, first+count) in CSR form. row_ptr has count+1
  * entries. Writes at most cap runs; returns the number needed (>= 0).
  */
 int64_t or_rows(const or_grid *g, const double *tab, const or_rec *r, int64_t first, int64_t count, int mode,
@@ -621,7 +631,6 @@ int64_t or_rows(const or_grid *g, const double *tab, const or_rec *r, int64_t fi
   return tot;
 }
 
-/* y_i = a_i . x for protons [first, first+count) (forward projection). */
 /*
  * Space-carved object hull: every voxel on the row of a proton whose WEPL is
  * at most wepl_max (it crossed air only) is outside the object; the hull is
@@ -662,6 +671,8 @@ int or_carve_hull(const or_grid *g, const double *tab, const or_rec *r, int64_t 
   return 0;
 }
 
+/* y_i = a_i . x for protons [first, first+count): the WEPL the image x
+ * predicts for each proton (Sec. 2, A x = b). */
 int or_project(const or_grid *g, const double *tab, const or_rec *r, int64_t first, int64_t count, int mode,
                const double *x, double *y) {
   or_geom o;
@@ -678,7 +689,8 @@ int or_project(const or_grid *g, const double *tab, const or_rec *r, int64_t fir
   return 0;
 }
 
-/* Run counts s_j of block b (rows of protons [b N/B, (b+1) N/B)). out: M */
+/* Run counts s_j of block b (rows of protons [b N/B, (b+1) N/B)): the
+ * diagonal weights of the DROP block update (Sec. 2.1). out: M */
 int or_block_counts(const or_grid *g, const double *tab, const or_rec *r, int64_t n, int n_blocks, int b, int mode,
                     double *out) {
   or_geom o;
