@@ -1,7 +1,9 @@
 // Object-hull set-up kernels (pct_set_hull, pct_carve_hull, pct_hull_ranges):
 // each history's hull entry/exit nodes, space carving of the hull from
 // low-WEPL histories with 6-neighbour growth, and the gather of ranges in
-// load order. The hull path itself is walk_proton_hull (pct_walk.cuh).
+// load order. The hull path itself is walk_proton_hull (pct_walk.cuh). The
+// MLP formalism that Sec. 2 cites estimates the path inside the object and
+// takes it straight outside; the hull says where the object is.
 #include "pct_walk.cuh"
 
 namespace pct {

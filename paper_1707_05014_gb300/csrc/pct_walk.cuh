@@ -128,18 +128,7 @@ __device__ __forceinline__ void node_range(const Geo& g, const RecV& r, int& klo
   if (isfinite(ux)) khi = min(khi, max(g.K, g.K + (int)ceilf((ux + g.u0) / g.du) + 2));
 }
 
-// Walk one proton's polyline, calling visit(j, len) for every run in path
-// order (j = voxel index, len = chord in mm).
-//
-// Per segment P -> Q the voxel index along an axis changes exactly when a face
-// is crossed (floor(Q/2^20) != floor(P/2^20), with the half-open convention:
-// a face reached exactly counts when moving up, not when moving down). When
-// every axis moves less than one voxel -- always the case for valid records,
-// whose segments span at most ~0.6 voxel -- each axis crosses at most one
-// face, and the (at most three) crossings are ordered in one event loop by
-// exact 32x32->64-bit cross-multiplication; tied crossings form one event.
-// Longer segments take the general loop that re-arms an axis after each face.
-// Segment state carried along the polyline.
+// Segment state carried along the polyline (see walk_proton for the rules).
 struct WalkState {
   int3 P;        // current node, Q20
   float3 qP;     // current node, float grid coordinates
