@@ -204,7 +204,8 @@ def test_straight_measurement_gives_straight_nodes(oracle):
 
 
 @pytest.mark.slow
-def test_table_is_the_conditional_mean_of_a_simulated_scattering_walk(oracle):
+@pytest.mark.parametrize("layer", ["slab", "hull_layer"])
+def test_table_is_the_conditional_mean_of_a_simulated_scattering_walk(oracle, layer):
     # Independent of the estimator's formula: simulate lateral multiple
     # scattering as a random walk whose slope variance grows at a rate
     # proportional to 1/(beta^2 p^2)(depth) (the same energy polynomial, pinned
@@ -216,10 +217,18 @@ def test_table_is_the_conditional_mean_of_a_simulated_scattering_walk(oracle):
     # the whole sub-path length and is not a property of such a walk) within a
     # few standard errors; the table with scattering held at its entry value
     # must not (it is off by about a hundred standard errors).
+    # The hull layer case: a water layer of 150 node intervals (93.75 mm) that
+    # the proton enters at its first node, with depth counted from there.
     g = S.Grid(160, 160, 8, 1.25, 1.25, 1.25)
     R, du, K, _ = oracle.geom_info(g)
-    tab = oracle.mlp_table(g, flags=oracle.F_NO_LOG)
-    flat = oracle.mlp_table(g, flags=oracle.F_NO_LOG | oracle.F_CONST_SCATTER)
+    if layer == "slab":
+        tab = oracle.mlp_table(g, flags=oracle.F_NO_LOG)
+        flat = oracle.mlp_table(g, flags=oracle.F_NO_LOG | oracle.F_CONST_SCATTER)
+    else:
+        K = 150
+        R = K * du / 2
+        tab = oracle.mlp_table_n(g, K, flags=oracle.F_NO_LOG)
+        flat = oracle.mlp_table_n(g, K, flags=oracle.F_NO_LOG | oracle.F_CONST_SCATTER)
     rng = np.random.Generator(np.random.Philox(7))
     n = 200_000
     t0, s0 = rng.normal(0.0, 1.0, n), rng.normal(0.0, 0.01, n)
