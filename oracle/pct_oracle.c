@@ -13,6 +13,14 @@
  *   Sec. 2.1 : DROP -- block-sequential diagonally relaxed orthogonal
  *              projections over a user-chosen number of blocks, a fixed
  *              number of iterations (Fig. 1).
+ *   Sec. 2.2 : CARP -- strings swept from a common image, then component
+ *              averaging (Fig. 2).
+ *   Sec. 4.2 : total-variation superiorization inside DROP and CARP.
+ *   Object hull: the cited MLP estimator runs inside the object and takes
+ *              the path straight outside it; hull entry/exit nodes and a
+ *              hull carved from the data.
+ * Every function is pinned by tests against what the paper and the
+ * mathematics fix (closed forms, limits, brute force, independent physics).
  * The paper cites the MLP formalism (Schulte et al. 2008) without printing it;
  * this file follows that published form directly:
  *     y1 = (S1^-1 + R1^T S2^-1 R1)^-1 (S1^-1 R0 y0 + R1^T S2^-1 y2),
