@@ -11,9 +11,9 @@ copy of x back to the host).
 
   python bench.py [--steps K] [--warmup W] [--gpus N] [--impl ours|reference]
 
-``--impl reference`` times the FP64 CPU oracle (the reference arm of this
-build: there is no reference code, only the paper) on a bounded sample of the
-same workload on the host cores.
+``--impl reference`` times the FP64 CPU oracle (the reference arm: there is
+no reference code to run, only the paper) on a bounded sample of the same
+workload on the host cores.
 """
 from __future__ import annotations
 
