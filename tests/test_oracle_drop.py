@@ -62,6 +62,20 @@ def test_one_proton_block_is_an_exact_projection(oracle):
     assert abs((float(r["wepl"][0]) - y[0]) - 0.75 * float(r["wepl"][0])) < 1e-12
 
 
+def test_repeated_proton_block_divides_by_the_run_counts(oracle):
+    # A block of m copies of one proton: every voxel of its row has s_j = m,
+    # and the m equal contributions a_ij r divided by s_j make one exact
+    # projection, so the residual is exactly zero after the block. Without the
+    # division the step would be m times too long (residual -(m-1) r).
+    g, rec = _tiny()
+    for m in (2, 3):
+        r = S.subset(rec, np.zeros(m, dtype=np.int64))
+        assert np.all(oracle.block_counts(g, r, 1, 0)[oracle.rows(g, r)[1]] == m)
+        x = oracle.drop(g, r, n_blocks=1, n_sweeps=1, lam=1.0)
+        y = oracle.project(g, r, x)
+        assert np.all(np.abs(y - float(r["wepl"][0])) < 1e-12 * max(1.0, float(r["wepl"][0])))
+
+
 def test_block_counts_are_run_counts(oracle):
     g, rec = _tiny()
     rp, vox, _ = oracle.rows(g, rec)
