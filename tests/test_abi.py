@@ -99,3 +99,23 @@ def test_null_pointers_are_rejected():
     assert lib.pct_destroy(None) == 0  # NULL is a no-op
     lib.pct_drop_block_noalloc.argtypes = [ctypes.c_void_p] * 5
     assert lib.pct_drop_block_noalloc(None, None, None, None, None) == -1
+
+
+@pytest.mark.parametrize("grid,n,lam,code,msg", [
+    ((256, 256, 64, 1.0, 1.0, 1.0), 10, 1.0, -5, "fixed scratch"),  # 4.2M voxels > the 2,097,152 of the scratch
+    ((128, 128, 128, 1.0, 1.0, 1.0), 10, 2.5, -1, "lambda"),  # exactly 2,097,152 voxels fit; lambda stops it next
+    ((64, 64, 64, 1.0, 1.0, 1.0), 0, 1.0, -1, "n must be"),
+    ((600, 64, 64, 1.0, 1.0, 1.0), 10, 1.0, -1, "grid dims"),
+])
+def test_no_alloc_update_checks_sizes_before_touching_the_gpu(grid, n, lam, code, msg):
+    # The no-allocation block update validates the grid against its fixed
+    # scratch and the history count on the host, before any CUDA call.
+    lib, pct = _lib_and_types()
+    lib.pct_drop_block_noalloc.argtypes = [ctypes.c_void_p] * 5
+    g = pct._Grid(*grid)
+    c = _cfg(pct, lam=lam)
+    buf = (ctypes.c_float * 1)()
+    h = pct._Hist(n, *([ctypes.addressof(buf)] * 11))
+    rc = lib.pct_drop_block_noalloc(ctypes.byref(g), ctypes.byref(c), ctypes.byref(h), ctypes.addressof(buf), None)
+    assert rc == code
+    assert msg in lib.pct_last_error().decode()
