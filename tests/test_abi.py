@@ -119,3 +119,14 @@ def test_no_alloc_update_checks_sizes_before_touching_the_gpu(grid, n, lam, code
     rc = lib.pct_drop_block_noalloc(ctypes.byref(g), ctypes.byref(c), ctypes.byref(h), ctypes.addressof(buf), None)
     assert rc == code
     assert msg in lib.pct_last_error().decode()
+
+
+def test_batch_and_network_arguments_are_checked_before_the_gpu():
+    lib, pct = _lib_and_types()
+    out = ctypes.c_void_p(7)
+    assert lib.pct_batch_create(ctypes.byref(out), None, 0, None) == -1
+    assert "at least one context" in lib.pct_last_error().decode() and not out.value
+    for dims in ((8, 8, 12), (4, 8, 8), (0, 16, 16)):
+        out = ctypes.c_void_p(7)
+        assert lib.pct_net_create(ctypes.byref(out), *dims, 0, 0) == -1
+        assert "multiples of 8" in lib.pct_last_error().decode() and not out.value
