@@ -427,6 +427,14 @@ def run_warmstart(args):
     B.build()
     g = W.training_grid()
     log = lambda m: print(m, file=sys.stderr, flush=True)  # noqa: E731
+    tuning = None
+    if args.ws_tune_blocks:  # blocks-per-update picked on a training head (seed 999), then used throughout
+        t0 = time.time()
+        args.ws_blocks, trials = W.tune_blocks(g, args.ws_test_n, 999, args.ws_target, args.ws_max_sweeps,
+                                               device=local)
+        tuning = {"chosen": args.ws_blocks, "ms_to_target": {str(b): ms for b, ms in trials.items()},
+                  "tuning_s": time.time() - t0}
+        log(f"blocks per update: {tuning}")
     t0 = time.time()
     pairs = W.make_training_pairs(g, args.ws_pairs, args.ws_train_n, args.ws_train_sweeps, device=local, log=log,
                                   blocks=args.ws_blocks)
@@ -467,6 +475,7 @@ def run_warmstart(args):
         "plain_seconds": statistics.mean(plain_ms) / 1e3 if plain_ms else None,
         "speedup": (statistics.mean(plain_ms) / statistics.mean(warm_ms)) if plain_ms and warm_ms else None,
         "tests": results, "train_loss": hist, "training_data_s": t_data, "training_s": t_train,
+        "blocks_tuning": tuning,
     }
     print(json.dumps(line), flush=True)
     net.close()
@@ -709,6 +718,8 @@ def main():
     ap.add_argument("--ws-train-n", type=int, default=50_000_000)
     ap.add_argument("--ws-train-sweeps", type=int, default=3)
     ap.add_argument("--ws-blocks", type=int, default=50)
+    ap.add_argument("--ws-tune-blocks", action="store_true",
+                    help="warmstart: pick the block count by time to the target on a training head")
     ap.add_argument("--ws-epochs", type=int, default=10)
     ap.add_argument("--ws-tests", type=int, default=2)
     ap.add_argument("--ws-test-n", type=int, default=1_000_000_000)

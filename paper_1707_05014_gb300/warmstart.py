@@ -130,3 +130,51 @@ def solve_to_target(ctx: P.Context, x_true: np.ndarray, grid: S.Grid, target: fl
         sweeps += 1
         errs.append(err())
     return {"reached": errs[-1] <= target, "sweeps": sweeps, "ms": t_ms, "errors": errs, "net_used": used_net}
+
+
+def pick_blocks(trial: Callable[[int, Optional[float]], Optional[float]], candidates: Sequence[int]) -> Tuple[int, Dict]:
+    """Blocks-per-update autotuner: the DROP block count B (Sec. 2.1 leaves it
+    to the user) with the shortest time to the target.
+
+    trial(B, limit_ms) returns the time (ms) one reconstruction with B blocks
+    takes to reach the target, or None if it does not reach it; limit_ms is
+    the best time so far (None at first), which a trial may use to give up
+    early. Candidates are tried in the given order. Returns the chosen B and
+    every candidate's result; raises ValueError if none reaches the target.
+    B changes the iteration itself, so it is tuned for time to a result,
+    never for throughput."""
+    if not candidates:
+        raise ValueError("no block counts to try")
+    results: Dict[int, Optional[float]] = {}
+    best_b, best_ms = None, None
+    for b in candidates:
+        if b < 1:
+            raise ValueError(f"block count {b} < 1")
+        ms = trial(b, best_ms)
+        results[b] = ms
+        if ms is not None and (best_ms is None or ms < best_ms):
+            best_b, best_ms = b, ms
+    if best_b is None:
+        raise ValueError("no block count reached the target")
+    return best_b, results
+
+
+def tune_blocks(grid: S.Grid, n: int, seed: int, target: float, max_sweeps: int,
+                candidates: Sequence[int] = (10, 20, 50, 100), device: int = 0) -> Tuple[int, Dict]:
+    """pick_blocks on one seeded training head: for each B, a plain
+    reconstruction from x = 0 timed to the target mean RSP error (the known
+    phantom of a training case decides; held-out cases are never used)."""
+    import torch
+
+    def trial(b: int, limit_ms: Optional[float]) -> Optional[float]:
+        wl = head_workload(grid, n, seed, n_blocks=b)
+        x_true = S.voxelize(wl.phantom(), grid, ss=2)
+        rec = S.make_histories_device(wl, device=f"cuda:{device}")
+        with P.Context(grid, n_blocks=b, device=device) as ctx:
+            ctx.load(rec)
+            del rec
+            torch.cuda.empty_cache()
+            r = solve_to_target(ctx, x_true, grid, target, max_sweeps)
+        return r["ms"] if r["reached"] else None
+
+    return pick_blocks(trial, candidates)
