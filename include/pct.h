@@ -306,7 +306,8 @@ PCT_API pct_status pct_batch_destroy(pct_batch *batch);
 
 /* n_sweeps DROP sweeps of every reconstruction in one persistent launch
  * (captured once per n_sweeps as a CUDA graph), queued on `stream` (a
- * cudaStream_t; NULL = the batch's own stream). Asynchronous. */
+ * cudaStream_t; NULL = the batch's own stream). Asynchronous; first waits
+ * on the host for the work of any context whose stream is not `stream`. */
 PCT_API pct_status pct_batch_iterate(pct_batch *batch, int32_t n_sweeps, void *stream);
 
 /* Wait for the batch's work on `stream` (NULL = own stream); returns

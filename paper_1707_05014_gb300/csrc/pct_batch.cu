@@ -437,6 +437,10 @@ pct_status pct_batch_iterate(pct_batch* b, int32_t n_sweeps, void* stream) {
   if (n_sweeps == 0) return PCT_OK;
   PCT_BCK(cudaSetDevice(b->device));
   cudaStream_t s = stream ? (cudaStream_t)stream : b->own_stream;
+  // work a context queued on its own stream (a load's counting sweep, its own
+  // sweeps) finishes before the batch reads and writes its image
+  for (auto* c : b->ctx)
+    if (c->stream != s) PCT_BCK(cudaStreamSynchronize(c->stream));
   if (b->cfg.debug_unreachable_wait) return enqueue(b, n_sweeps, s, spin_limit_of(b));  // persistent only
   if (!b->graph || b->graph_sweeps != n_sweeps) {
     if (b->graph) cudaGraphExecDestroy(b->graph);
@@ -482,6 +486,7 @@ pct_status pct_batch_autotune(pct_batch* b, pct_batch_config* chosen, float* bes
   if (cs != PCT_OK) return cs;
   PCT_BCK(cudaSetDevice(b->device));
   cudaStream_t s = b->own_stream;
+  for (auto* c : b->ctx) PCT_BCK(cudaStreamSynchronize(c->stream));  // the contexts' queued work first
   // save every x: the trial sweeps change them
   int64_t off = 0;
   for (auto* c : b->ctx) {
