@@ -248,3 +248,60 @@ def test_fp32_fp64_index_list_mismatches_are_slivers(oracle):
         for k in set(da) | set(db):
             assert abs(da.get(k, 0.0) - db.get(k, 0.0)) <= 1e-3 * g.hx
     assert 0 < mismatched <= 0.01 * 20_000
+
+
+def test_extension_nodes_follow_the_measured_rays(oracle):
+    # Outside the planes the path is the straight ray along the measured slope:
+    # t = t0 + st0 (u - u0) before u0 and t = t2 + st2 (u - u2) after u2 (and
+    # the same for v), for bent records too. Checked node by node against that
+    # closed form in FP64 mode (Q20 rounding: 1e-6 voxel).
+    wl = S.tiny_workload(40, seed=31)
+    g = wl.grid
+    rec = S.make_histories(wl)
+    R, du, K, E = oracle.geom_info(g)
+    for i in range(40):
+        Q = oracle.polyline(g, rec, i, mode=oracle.MODE_FP64).astype(np.float64) / 2.0**20
+        c, s = float(rec["cphi"][i]), float(rec["sphi"][i])
+        for k in list(range(-E, 0)) + list(range(K + 1, K + E + 1)):
+            u = -R + k * du
+            if k < 0:
+                t = float(rec["t0"][i]) + float(rec["st0"][i]) * (u + R)
+                v = float(rec["v0"][i]) + float(rec["sv0"][i]) * (u + R)
+            else:
+                t = float(rec["t2"][i]) + float(rec["st2"][i]) * (u - R)
+                v = float(rec["v2"][i]) + float(rec["sv2"][i]) * (u - R)
+            ref = np.array([(u * c - t * s) / g.hx + g.nx / 2, (u * s + t * c) / g.hy + g.ny / 2, v / g.hz + g.nz / 2])
+            q = Q[k + E]
+            if np.all(np.abs(ref) < 999):  # inside the clamped range
+                assert np.abs(q - ref).max() < 2e-6, (i, k)
+
+
+def test_straight_row_length_is_the_line_inside_the_box(oracle):
+    # For a consistent straight record the row's total chord is the length of
+    # the straight line inside the grid box, computed here from the line itself
+    # (not from the oracle's polyline), for oblique angles and slopes.
+    g = G32
+    hi = np.array([g.nx * g.hx, g.ny * g.hy, g.nz * g.hz]) / 2
+    rng = np.random.Generator(np.random.Philox(32))
+    n = 30
+    t, v = rng.uniform(-20, 20, n), rng.uniform(-20, 20, n)
+    st, sv = rng.normal(0, 0.2, n), rng.normal(0, 0.2, n)
+    rec = S.straight_records(g, t, v, st, sv, np.zeros(n))
+    phi = rng.uniform(0, 2 * np.pi, n)
+    rec["cphi"][:] = np.cos(phi).astype(np.float32)
+    rec["sphi"][:] = np.sin(phi).astype(np.float32)
+    rp, vox, ln = oracle.rows(g, rec, mode=oracle.MODE_FP64)
+    R = oracle.geom_info(g)[0]
+    for i in range(n):
+        c, s = float(rec["cphi"][i]), float(rec["sphi"][i])
+        t0, v0 = float(rec["t0"][i]), float(rec["v0"][i])
+        a, b = float(rec["st0"][i]), float(rec["sv0"][i])
+
+        def p(u):  # the straight line through the entry state (u0 = -R)
+            tt, vv = t0 + a * (u + R), v0 + b * (u + R)
+            return np.array([u * c - tt * s, u * s + tt * c, vv])
+
+        p0, p1 = p(-1000.0), p(1000.0)
+        ref = _clip_len(p0, p1, -hi, hi)
+        got = ln[rp[i]:rp[i + 1]].sum()
+        assert abs(got - ref) <= 1e-6 * max(ref, 1.0), (i, got, ref)
