@@ -187,3 +187,24 @@ def test_threaded_drop_equals_single_thread(oracle):
         a = oracle.drop(g, rec, 4, 2, hull=h)
         b = oracle.drop_threads(g, rec, 4, 2, threads=3, hull=h)
         assert np.abs(a - b).max() <= 1e-12 * max(1.0, np.abs(a).max())
+
+
+@pytest.mark.parametrize("n,B", [(200, 3), (157, 7)])
+def test_blocks_are_consecutive_ranges_applied_in_sequence(oracle, n, B):
+    # Sec. 2.1 / Fig. 1: the image each block produces seeds the next block,
+    # and a sweep visits the blocks in order; block b holds histories
+    # [b n / B, (b + 1) n / B). One B-block sweep must equal B one-block sweeps
+    # over those ranges chained through x0, and two sweeps must chain the same
+    # way (a ragged n checks the rounding of the block boundaries).
+    g, rec = _tiny()
+    rec = S.subset(rec, slice(0, n))
+    x = np.zeros(g.m)
+    for _ in range(2):
+        for b in range(B):
+            lo, hi = b * n // B, (b + 1) * n // B
+            x = oracle.drop(g, S.subset(rec, slice(lo, hi)), 1, 1, lam=0.8, x0=x)
+    ref = oracle.drop(g, rec, B, 2, lam=0.8)
+    assert np.abs(ref - x).max() <= 1e-12 * max(1.0, np.abs(x).max())
+    # a different split of the same histories gives a different image
+    other = oracle.drop(g, rec, B + 1, 2, lam=0.8)
+    assert np.abs(other - ref).max() > 1e-6
