@@ -130,3 +130,31 @@ def test_batch_and_network_arguments_are_checked_before_the_gpu():
         out = ctypes.c_void_p(7)
         assert lib.pct_net_create(ctypes.byref(out), *dims, 0, 0) == -1
         assert "multiples of 8" in lib.pct_last_error().decode() and not out.value
+
+
+def test_header_is_plain_c_and_links_against_the_library(tmp_path):
+    # A C (not C++) caller: include/pct.h compiles as C99 with warnings as
+    # errors, and a program that takes the address of every declared entry
+    # point links against libpct.so (names and C linkage agree).
+    import shutil
+    import subprocess
+
+    from paper_1707_05014_gb300 import build
+
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    lib = build.build()
+    names = _declared("pct.h")
+    src = tmp_path / "use_pct.c"
+    src.write_text("#include \"pct.h\"\n#include <stdio.h>\nint main(void) {\n  void *p[] = {\n" +
+                   ",\n".join(f"    (void *)&{n}" for n in names) +
+                   "\n  };\n  printf(\"%d\\n\", (int)(sizeof p / sizeof p[0]));\n  return 0;\n}\n")
+    exe = tmp_path / "use_pct"
+    r = subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-Werror",
+                        "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe),
+                        "-L", os.path.dirname(lib), "-lpct", f"-Wl,-rpath,{os.path.dirname(lib)}"],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert out.returncode == 0 and int(out.stdout) == len(names)
