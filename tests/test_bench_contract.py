@@ -32,3 +32,33 @@ def test_reference_arm_prints_one_contract_line():
 
 def test_reference_arm_other_ranks_exit_without_work():
     assert _run({"RANK": "1"}) == []
+
+
+def test_clock_record_parses_nvidia_smi_samples():
+    # The clocks object of the bench line: median SM clock under load, the
+    # maximum, and every throttle reason seen Active (a run with hw_slowdown or
+    # a thermal slowdown is rejected by the rules; sw_power_cap is kept).
+    sys.path.insert(0, ROOT)
+    import bench
+
+    class Done:
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+
+    cs = bench.ClockSampler(0)
+    cs._p = Done()
+    cs.rows = [r.split(", ") for r in (
+        "0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "0, 1980, 2070, 1400.0, 0x4, Not Active, Not Active, Not Active, Active",
+        "0, 2070, 2070, 1200.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "0, [N/A], 2070, 0, 0x0, Not Active, Not Active, Not Active, Not Active",
+    )]
+    out = cs.stop()
+    assert out["sm_mhz"] == 2070.0 and out["sm_max_mhz"] == 2070.0 and out["samples"] == 3
+    assert out["reasons"] == ["sw_power_cap"]
+    cs.rows.append("0, 1500, 2070, 1000, 0x8, Active, Not Active, Active, Not Active".split(", "))
+    assert cs.stop()["reasons"] == ["hw_slowdown", "sw_power_cap", "sw_thermal_slowdown"]
+    assert bench.ClockSampler(0).stop()["reasons"] == ["nvidia-smi unavailable"]
