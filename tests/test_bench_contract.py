@@ -62,3 +62,18 @@ def test_clock_record_parses_nvidia_smi_samples():
     cs.rows.append("0, 1500, 2070, 1000, 0x8, Active, Not Active, Active, Not Active".split(", "))
     assert cs.stop()["reasons"] == ["hw_slowdown", "sw_power_cap", "sw_thermal_slowdown"]
     assert bench.ClockSampler(0).stop()["reasons"] == ["nvidia-smi unavailable"]
+
+
+def test_traffic_counters_are_used_only_for_the_sources_they_were_taken_on(monkeypatch):
+    # roofline.traffic comes from the committed ncu summary only while the
+    # fused kernel's sources hash to the value recorded with it; otherwise null.
+    sys.path.insert(0, ROOT)
+    import bench
+
+    with open(os.path.join(ROOT, "profiles", "drop_fused_head_counters.json")) as f:
+        rec = json.load(f)
+    assert rec["sources"] == list(bench.FUSED_SOURCES) and rec["dram_bytes_per_history"] > 44
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: rec["source_hash"])
+    assert bench.ncu_counters()["dram_bytes_per_history"] == rec["dram_bytes_per_history"]
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: "0" * 16)
+    assert bench.ncu_counters() is None
