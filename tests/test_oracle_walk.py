@@ -276,10 +276,12 @@ def test_extension_nodes_follow_the_measured_rays(oracle):
                 assert np.abs(q - ref).max() < 2e-6, (i, k)
 
 
-def test_straight_row_length_is_the_line_inside_the_box(oracle):
+@pytest.mark.parametrize("node_step", [0.0, 64.0 / 2047.0], ids=["default_step", "max_nodes"])
+def test_straight_row_length_is_the_line_inside_the_box(oracle, node_step):
     # For a consistent straight record the row's total chord is the length of
     # the straight line inside the grid box, computed here from the line itself
-    # (not from the oracle's polyline), for oblique angles and slopes.
+    # (not from the oracle's polyline), for oblique angles and slopes; also at
+    # the largest node count the library accepts (K + 1 = 2048).
     g = G32
     hi = np.array([g.nx * g.hx, g.ny * g.hy, g.nz * g.hz]) / 2
     rng = np.random.Generator(np.random.Philox(32))
@@ -290,8 +292,9 @@ def test_straight_row_length_is_the_line_inside_the_box(oracle):
     phi = rng.uniform(0, 2 * np.pi, n)
     rec["cphi"][:] = np.cos(phi).astype(np.float32)
     rec["sphi"][:] = np.sin(phi).astype(np.float32)
-    rp, vox, ln = oracle.rows(g, rec, mode=oracle.MODE_FP64)
-    R = oracle.geom_info(g)[0]
+    rp, vox, ln = oracle.rows(g, rec, mode=oracle.MODE_FP64, node_step=node_step)
+    R, _, K, _ = oracle.geom_info(g, node_step)
+    assert K == (64 if node_step == 0.0 else 2047)
     for i in range(n):
         c, s = float(rec["cphi"][i]), float(rec["sphi"][i])
         t0, v0 = float(rec["t0"][i]), float(rec["v0"][i])
