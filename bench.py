@@ -298,14 +298,12 @@ def run_batched(args):
 
 def run_precision(args):
     """Precision variant: 250M histories on the head grid, 40 blocks, 8 sweeps
-    (FP32 fused MLP + projection with Kahan a_i.x, FP64 MLP tables), timed;
-    then the error of every stage against the FP64 oracle on a 1M-history
-    subset: nodes, index lists and chords, a_i.x with and without Kahan, and
-    the image after the 8 sweeps."""
-    import numpy as np
+    (FP32 fused MLP + projection with Kahan a_i.x, FP64 MLP tables), timed.
+    The error of every stage against the FP64 oracle on a 1M-history subset
+    (nodes, index lists and chords, a_i.x with and without Kahan, the image
+    after the 8 sweeps) is test infrastructure: tests/precision_report.py."""
     import torch
 
-    import oracle as O
     from paper_1707_05014_gb300 import build as B
     from paper_1707_05014_gb300 import pct as P
     from paper_1707_05014_gb300 import synthetic as S
@@ -313,7 +311,6 @@ def run_precision(args):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     B.build()
-    O.build()
     n_full = args.n if args.n != 50_000_000 else 250_000_000
     base = S.head_workload(n_full, seed=3)
     wl = S.Workload(f"head160_precision_{n_full}", base.grid, n_full, 3, 90, base.t_range, base.v_range, 40, 8,
@@ -343,66 +340,13 @@ def run_precision(args):
     ctx.close()
     value = wl.n * args.steps / (ms / 1e3)
 
-    # error budget against the FP64 oracle on a 1M-history subset (host copy)
-    ns = args.precision_subset
-    sub = S.make_histories(wl, n=ns, seed_offset=11)
-    x_true = S.voxelize(wl.phantom(), g, ss=2)
-    prec = {"subset_histories": ns}
-    with P.Context(g, n_blocks=40, device=local) as c:
-        c.load(sub)
-        k = min(ns, 20_000)
-        rp, vox, ln, nodes = (t.cpu().numpy() for t in c.rows(0, k, with_nodes=True))
-        n64 = O.nodes(g, sub, 0, k, mode=O.MODE_FP64).astype(np.int64)
-        dq = np.abs(nodes.astype(np.int64) - n64) / 2.0**20
-        prec["node_error_voxels"] = {"max": float(dq.max()), "rms": float(np.sqrt((dq**2).mean()))}
-        orp, ovox, oln = O.rows(g, sub, 0, k, mode=O.MODE_FP64)
-        same, d = 0, []
-        for i in range(k):
-            a, b = vox[rp[i]:rp[i + 1]], ovox[orp[i]:orp[i + 1]]
-            if len(a) == len(b) and np.array_equal(a, b):
-                same += 1
-                d.append(np.abs(ln[rp[i]:rp[i + 1]] - oln[orp[i]:orp[i + 1]]) / np.maximum(oln[orp[i]:orp[i + 1]], g.hx))
-        d = np.concatenate(d)
-        prec["index_lists_identical_to_fp64_nodes"] = same / k
-        prec["chord_error_rel"] = {"median": float(np.median(d)), "p99": float(np.percentile(d, 99)),
-                                   "max": float(d.max())}
-        c.set_x0(x_true.astype(np.float32))
-        yk = c.project(0, k).cpu().numpy().astype(np.float64)
-    with P.Context(g, n_blocks=40, flags=P.FLAG_NO_KAHAN, device=local) as c:
-        c.load(S.subset(sub, slice(0, k)))
-        c.set_x0(x_true.astype(np.float32))
-        yp = c.project(0, k).cpu().numpy().astype(np.float64)
-    y32 = O.project(g, S.subset(sub, slice(0, k)), x_true, mode=O.MODE_FP32)
-    y64 = O.project(g, S.subset(sub, slice(0, k)), x_true, mode=O.MODE_FP64)
-    m = y32 > 1.0
-    prec["ax_rel_error_vs_fp64_sum_same_rows"] = {
-        "kahan": {"max": float(np.max(np.abs(yk - y32)[m] / y32[m])), "mean": float(np.mean(np.abs(yk - y32)[m] / y32[m]))},
-        "plain": {"max": float(np.max(np.abs(yp - y32)[m] / y32[m])), "mean": float(np.mean(np.abs(yp - y32)[m] / y32[m]))}}
-    prec["ax_rel_error_vs_fp64_oracle"] = {"max": float(np.max(np.abs(yk - y64)[m] / y64[m])),
-                                           "mean": float(np.mean(np.abs(yk - y64)[m] / y64[m]))}
-    with P.Context(g, n_blocks=40, device=local) as c:
-        c.load(sub)
-        c.iterate(wl.n_sweeps)
-        xg = c.get_rsp().astype(np.float64)
-    t0 = time.perf_counter()
-    xo = O.drop(g, sub, 40, wl.n_sweeps, mode=O.MODE_FP64)
-    t_or = time.perf_counter() - t0
-    rel = np.abs(xg - xo) / np.maximum(np.abs(xo), 1.0)
-    roi = S.interior_mask(x_true, g)
-    prec["rsp_error_vs_fp64_oracle"] = {"max": float(rel.max()), "mean": float(rel.mean()),
-                                        "p999": float(np.percentile(rel, 99.9)), "bar": 1e-3,
-                                        "roi_max": float(rel[roi].max()), "roi_mean": float(rel[roi].mean()),
-                                        "note": "all voxels include sparsely sampled ones where a single index-list "
-                                                "difference between FP32 and FP64 nodes decides the update"}
-    prec["mean_rsp_error_vs_truth"] = {"gpu": S.mean_rsp_error(xg, x_true, g), "oracle": S.mean_rsp_error(xo, x_true, g)}
-    prec["oracle_seconds"] = t_or
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": 1,
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": wl.name, "grid": "160x160x64 @ 1.25 mm", "histories": wl.n, "n_blocks": 40,
                    "step": "one DROP sweep", "kahan": True, "mlp_table": "fp64 on GPU"},
-        "precision": prec, "clocks": clk,
+        "precision": "error budget against the FP64 oracle: python tests/precision_report.py", "clocks": clk,
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -725,7 +669,6 @@ def main():
     ap.add_argument("--ws-test-n", type=int, default=1_000_000_000)
     ap.add_argument("--ws-target", type=float, default=0.01)
     ap.add_argument("--ws-max-sweeps", type=int, default=10)
-    ap.add_argument("--precision-subset", type=int, default=1_000_000, help="oracle subset of the precision run")
     ap.add_argument("--n-recon", type=int, default=32, help="reconstructions of the batched workload")
     args = ap.parse_args()
     if args.impl == "reference":
