@@ -77,3 +77,28 @@ def test_traffic_counters_are_used_only_for_the_sources_they_were_taken_on(monke
     assert bench.ncu_counters()["dram_bytes_per_history"] == rec["dram_bytes_per_history"]
     monkeypatch.setattr(bench, "kernel_source_hash", lambda: "0" * 16)
     assert bench.ncu_counters() is None
+
+
+def test_oracle_is_loaded_only_by_tests_smoke_and_the_cpu_legs():
+    # The oracle is test infrastructure: the package never imports it, and
+    # bench.py loads it in one function only, the timing of the CPU baseline and
+    # of the reference arm (oracle_rate).
+    import ast
+
+    pkg = os.path.join(ROOT, "paper_1707_05014_gb300")
+    for name in os.listdir(pkg):
+        if name.endswith(".py"):
+            assert "oracle" not in {a.name.split(".")[0] for n in ast.walk(ast.parse(open(os.path.join(pkg, name)).read()))
+                                    if isinstance(n, ast.Import) for a in n.names}, name
+            assert not any(isinstance(n, ast.ImportFrom) and (n.module or "").startswith("oracle")
+                           for n in ast.walk(ast.parse(open(os.path.join(pkg, name)).read()))), name
+    tree = ast.parse(open(os.path.join(ROOT, "bench.py")).read())
+    users = set()
+    for f in [n for n in ast.walk(tree) if isinstance(n, ast.FunctionDef)]:
+        for n in ast.walk(f):
+            if isinstance(n, ast.Import) and any(a.name.split(".")[0] == "oracle" for a in n.names):
+                users.add(f.name)
+            if isinstance(n, ast.ImportFrom) and (n.module or "").startswith("oracle"):
+                users.add(f.name)
+    assert users == {"oracle_rate"}
+    assert not any(isinstance(n, (ast.Import, ast.ImportFrom)) and "oracle" in ast.dump(n) for n in tree.body)
