@@ -246,6 +246,36 @@ PCT_API pct_status pct_set_x0(pct_ctx *ctx, const float *x0, int on_device);
  * per sweep. */
 PCT_API pct_status pct_iterate(pct_ctx *ctx, int32_t n_sweeps);
 
+/* ---- A DROP block shared by several processes (Sec. 1 and Sec. 3.1: the
+ * histories are distributed over processors, each of which works on its own
+ * part). Each rank's context holds its share of the histories, B blocks over
+ * them, so that global block b is the union of the ranks' blocks b. One block
+ * update is then
+ *   pct_block_partial on every rank -> all-reduce(sum) of delta and counts
+ *   -> pct_block_apply with the sums on every rank,
+ * which gives every rank the x of one DROP block over the union (Sec. 2.1),
+ * up to floating-point summation order. The run counts of a block do not
+ * change between sweeps, so their sum can be reduced once and kept. ---- */
+
+/* This rank's part of block `block` with the context's current x:
+ * delta_out[j] = lambda sum_i a_ij (b_i - a_i.x) / |a_i|^2 over the block's
+ * histories in this context (DEVICE, M floats, overwritten), and, if
+ * counts_out is not NULL, the block's run counts s_j as float (DEVICE, M
+ * floats, overwritten). x is not changed. Asynchronous. */
+PCT_API pct_status pct_block_partial(pct_ctx *ctx, int32_t block, float *delta_out, float *counts_out);
+
+/* x_j += delta_j / counts_j where counts_j > 0 (voxels no rank's histories
+ * touch are unchanged), then the PCT_FLAG_CLAMP clamp if set: the DROP block
+ * update from the sums of every rank's pct_block_partial output (DEVICE
+ * arrays of M floats, read only). Asynchronous. */
+PCT_API pct_status pct_block_apply(pct_ctx *ctx, const float *delta, const float *counts);
+
+/* Testing hook (process-wide): with k >= 1, the k-th device allocation that a
+ * context makes from now on fails as if the device had no memory left (the
+ * call reports PCT_ERR_NO_MEMORY); later allocations succeed again. k <= 0
+ * disarms it. */
+PCT_API void pct_debug_fail_alloc(int64_t k);
+
 /* With PCT_FLAG_PROFILE: wait for the queued work, then write the device
  * time (ms) of each block's fused MLP + projection kernel and of each block's
  * apply kernel in the most recent sweep to fused_ms[b] and apply_ms[b]
@@ -379,10 +409,11 @@ PCT_API pct_status pct_net_train_step(pct_net *net, const float *x1, const float
  * Scratch: a fixed 16.1 MiB device array inside the library (its update
  * accumulator, run counts and MLP table) that every GPU loading the library
  * holds until exit. Grids above 2,097,152 voxels return PCT_ERR_CAPACITY.
- * The first call on a device looks up that array's device address with the
- * device current; make the first call before any stream capture. Every call
- * uses the same array and clears what must start at zero, so calls that
- * overlap on the GPU (different streams or threads, same device) race.
+ * Every call looks up that array's device address in the context current on
+ * the calling thread (the current device's), so the call follows a reset or
+ * a change of context. Every call on a device uses the same array and clears
+ * what must start at zero, so calls that overlap on the GPU (different
+ * streams or threads, same device) race.
  * Validates the records (as pct_load_histories does) and synchronises the
  * stream once to report PCT_ERR_INVALID_DATA; the update itself is queued
  * asynchronously. No cudaMalloc, cudaFree or other allocating call is made. */

@@ -134,8 +134,22 @@ def forward(p: np.ndarray, x1: np.ndarray, bf16: bool = False):
     raise AssertionError("unreachable")
 
 
-def loss_and_grads(p: np.ndarray, x1: np.ndarray, target: np.ndarray, bf16: bool = False):
-    """L1 loss mean|x0 - target| and its gradient w.r.t. p (flat, like p)."""
+def forward_scale(p: np.ndarray, x1: np.ndarray, bf16: bool = False) -> np.ndarray:
+    """Per voxel, |b| + sum over taps and channels of |W| |h| of the last layer
+    (h its input): the sum of the magnitudes of the terms that make up f. A
+    change of every stored input activation by at most a relative e changes f
+    by at most e times this scale."""
+    _, c = forward(p, x1, bf16)
+    W, b = c["layers"][-1]
+    h = c["acts"][-1]
+    return conv(np.abs(h), np.abs(W), np.abs(b), 1)[..., 0]
+
+
+def loss_and_grads(p: np.ndarray, x1: np.ndarray, target: np.ndarray, bf16: bool = False, scales: bool = False):
+    """L1 loss mean|x0 - target| and its gradient w.r.t. p (flat, like p).
+    With scales=True also returns, per parameter, the sum of the magnitudes
+    of the terms of its gradient (sum |h| |g| for a weight, sum |g| for a
+    bias), the scale of an element-wise bound on the gradient."""
     q = (lambda a: to_bf16(a)) if bf16 else (lambda a: a)
     x0, c = forward(p, x1, bf16)
     n = x0.size
@@ -147,6 +161,7 @@ def loss_and_grads(p: np.ndarray, x1: np.ndarray, target: np.ndarray, bf16: bool
     df[..., 0] = np.sign(x0 - target) / n
     gpre[nl - 1] = q(df)
     grads = []
+    sgrads = []
     for li in range(nl - 1, -1, -1):
         ci, co, kind, _ = SPEC[li]
         W, _ = layers[li]
@@ -158,6 +173,15 @@ def loss_and_grads(p: np.ndarray, x1: np.ndarray, target: np.ndarray, bf16: bool
             dW = conv_wgrad(h, g, 2)
         else:
             dW = conv_wgrad(up2(h), g, 1)
+        if scales:
+            ah, ag = np.abs(h), np.abs(g)
+            if kind == "s1":
+                sW = conv_wgrad(ah, ag, 1)
+            elif kind == "s2":
+                sW = conv_wgrad(ah, ag, 2)
+            else:
+                sW = conv_wgrad(up2(ah), ag, 1)
+            sgrads.append((li, sW, ag.reshape(-1, co).sum(axis=0)))
         grads.append((li, dW, g.reshape(-1, co).sum(axis=0)))
         if li == 0:
             break
@@ -171,17 +195,23 @@ def loss_and_grads(p: np.ndarray, x1: np.ndarray, target: np.ndarray, bf16: bool
             if skip == li - 1:
                 dh = dh + gpre[u]
         gpre[li - 1] = q(dh * (acts[li - 1] > 0))
-    flat = np.zeros(param_count())
     off = []
     o = 0
     for ci, co, _, _ in SPEC:
         off.append(o)
         o += 27 * ci * co + co
-    for li, dW, db in grads:
-        ci, co, _, _ = SPEC[li]
-        flat[off[li]:off[li] + 27 * ci * co] = dW.ravel()
-        flat[off[li] + 27 * ci * co:off[li] + 27 * ci * co + co] = db
-    return loss, flat
+
+    def pack(items):
+        flat = np.zeros(param_count())
+        for li, dW, db in items:
+            ci, co, _, _ = SPEC[li]
+            flat[off[li]:off[li] + 27 * ci * co] = dW.ravel()
+            flat[off[li] + 27 * ci * co:off[li] + 27 * ci * co + co] = db
+        return flat
+
+    if scales:
+        return loss, pack(grads), pack(sgrads)
+    return loss, pack(grads)
 
 
 def init_params(seed: int = 0) -> np.ndarray:

@@ -5,6 +5,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
 #include <string>
 
 #include "../../include/pct.h"
@@ -34,9 +35,25 @@ pct_status fail(pct_status code, const char* fmt, ...) {
     if (e_ != cudaSuccess) return fail(PCT_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
   } while (0)
 
+// Failure injection for tests (pct_debug_fail_alloc): when armed with k, the
+// k-th device allocation made through dev_alloc from then on fails as if the
+// device had no memory left; each later allocation succeeds again.
+std::atomic<int64_t> g_fail_alloc_countdown{0};
+
+cudaError_t dev_alloc(void** p, size_t bytes) {
+  int64_t k = g_fail_alloc_countdown.load();
+  while (k > 0 && !g_fail_alloc_countdown.compare_exchange_weak(k, k - 1)) {
+  }
+  if (k == 1) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(p, bytes);
+}
+
 #define PCT_ALLOC(ptr, bytes)                                                                         \
   do {                                                                                                \
-    cudaError_t e_ = cudaMalloc((void**)&(ptr), (bytes));                                             \
+    cudaError_t e_ = dev_alloc((void**)&(ptr), (bytes));                                              \
     if (e_ != cudaSuccess) {                                                                          \
       (void)cudaGetLastError();                                                                       \
       return fail(PCT_ERR_NO_MEMORY, "cudaMalloc(%lld bytes): %s", (long long)(bytes), cudaGetErrorString(e_)); \
@@ -90,7 +107,7 @@ pct_status grow(T*& p, int64_t& cap, int64_t need) {
   cudaFree(p);
   p = nullptr;
   cap = 0;
-  cudaError_t e = cudaMalloc((void**)&p, (size_t)need * sizeof(T));
+  cudaError_t e = dev_alloc((void**)&p, (size_t)need * sizeof(T));
   if (e != cudaSuccess) {
     (void)cudaGetLastError();
     p = nullptr;
@@ -136,6 +153,7 @@ void pct::set_error_text(const char* msg) { g_err = msg; }
 
 pct_status pct::ensure_block_weights(pct_ctx* c) {
   if (c->weights_ready || !c->loaded) return PCT_OK;
+  pct::DeviceGuard device_guard_;
   PCT_CK(cudaSetDevice(c->device));
   pct_status st = block_weights(c);
   if (st != PCT_OK) return st;
@@ -145,6 +163,8 @@ pct_status pct::ensure_block_weights(pct_ctx* c) {
 extern "C" {
 
 const char* pct_last_error(void) { return g_err.c_str(); }
+
+void pct_debug_fail_alloc(int64_t k) { g_fail_alloc_countdown.store(k > 0 ? k : 0); }
 
 pct_status pct_create(pct_ctx** out, const pct_grid* grid, const pct_config* cfg, int device) {
   if (!out) return fail(PCT_ERR_INVALID_ARG, "out is NULL");
@@ -220,6 +240,7 @@ pct_status pct_create(pct_ctx** out, const pct_grid* grid, const pct_config* cfg
   G.bx = (float)(0.5 * X);
   G.by = (float)(0.5 * Y);
 
+  pct::DeviceGuard device_guard_;
   pct_status st = PCT_OK;
   do {
     cudaError_t e = cudaSetDevice(device);
@@ -234,13 +255,13 @@ pct_status pct_create(pct_ctx** out, const pct_grid* grid, const pct_config* cfg
     }
     c->stream = c->own_stream;
     size_t M = (size_t)c->M;
-    if (cudaMalloc((void**)&c->tab64, (c->K + 1) * 4 * sizeof(double)) != cudaSuccess ||
-        cudaMalloc((void**)&c->tab32, (c->K + 1) * sizeof(float4)) != cudaSuccess ||
-        cudaMalloc((void**)&c->x, M * sizeof(float)) != cudaSuccess ||
-        cudaMalloc((void**)&c->delta, M * sizeof(float)) != cudaSuccess ||
-        cudaMalloc((void**)&c->cnt, M * sizeof(unsigned int)) != cudaSuccess ||
-        cudaMalloc((void**)&c->first_bad, sizeof(unsigned long long)) != cudaSuccess ||
-        cudaMalloc((void**)&c->acc, sizeof(double)) != cudaSuccess) {
+    if (dev_alloc((void**)&c->tab64, (c->K + 1) * 4 * sizeof(double)) != cudaSuccess ||
+        dev_alloc((void**)&c->tab32, (c->K + 1) * sizeof(float4)) != cudaSuccess ||
+        dev_alloc((void**)&c->x, M * sizeof(float)) != cudaSuccess ||
+        dev_alloc((void**)&c->delta, M * sizeof(float)) != cudaSuccess ||
+        dev_alloc((void**)&c->cnt, M * sizeof(unsigned int)) != cudaSuccess ||
+        dev_alloc((void**)&c->first_bad, sizeof(unsigned long long)) != cudaSuccess ||
+        dev_alloc((void**)&c->acc, sizeof(double)) != cudaSuccess) {
       (void)cudaGetLastError();
       st = fail(PCT_ERR_NO_MEMORY, "device allocation failed for a %lld-voxel grid", (long long)c->M);
       break;
@@ -254,9 +275,9 @@ pct_status pct_create(pct_ctx** out, const pct_grid* grid, const pct_config* cfg
     }
     c->launches += 1;
     if (c->cfg.flags & PCT_FLAG_CARP) {
-      if (cudaMalloc((void**)&c->carp_sum, M * sizeof(float)) != cudaSuccess ||
-          cudaMalloc((void**)&c->carp_touch, M * sizeof(float)) != cudaSuccess ||
-          cudaMalloc((void**)&c->carp_x0, M * sizeof(float)) != cudaSuccess) {
+      if (dev_alloc((void**)&c->carp_sum, M * sizeof(float)) != cudaSuccess ||
+          dev_alloc((void**)&c->carp_touch, M * sizeof(float)) != cudaSuccess ||
+          dev_alloc((void**)&c->carp_x0, M * sizeof(float)) != cudaSuccess) {
         (void)cudaGetLastError();
         st = fail(PCT_ERR_NO_MEMORY, "CARP buffers");
         break;
@@ -269,10 +290,10 @@ pct_status pct_create(pct_ctx** out, const pct_grid* grid, const pct_config* cfg
       }
     }
     if (c->cfg.tvs_beta0 > 0.f) {
-      if (cudaMalloc((void**)&c->tv_g, M * sizeof(float)) != cudaSuccess ||
-          cudaMalloc((void**)&c->tv_xp, M * sizeof(float)) != cudaSuccess ||
-          cudaMalloc((void**)&c->tv_acc, 3 * sizeof(double)) != cudaSuccess ||
-          cudaMalloc((void**)&c->tv_state, sizeof(pct::TvState)) != cudaSuccess) {
+      if (dev_alloc((void**)&c->tv_g, M * sizeof(float)) != cudaSuccess ||
+          dev_alloc((void**)&c->tv_xp, M * sizeof(float)) != cudaSuccess ||
+          dev_alloc((void**)&c->tv_acc, 3 * sizeof(double)) != cudaSuccess ||
+          dev_alloc((void**)&c->tv_state, sizeof(pct::TvState)) != cudaSuccess) {
         (void)cudaGetLastError();
         st = fail(PCT_ERR_NO_MEMORY, "TVS buffers");
         break;
@@ -303,6 +324,7 @@ pct_status pct_create(pct_ctx** out, const pct_grid* grid, const pct_config* cfg
 
 pct_status pct_destroy(pct_ctx* c) {
   if (!c) return PCT_OK;
+  pct::DeviceGuard device_guard_;
   cudaSetDevice(c->device);
   if (c->own_stream) cudaStreamSynchronize(c->own_stream);
   if (c->stream && c->stream != c->own_stream) cudaStreamSynchronize(c->stream);
@@ -335,6 +357,7 @@ pct_status pct_destroy(pct_ctx* c) {
 pct_status pct_set_stream(pct_ctx* c, void* stream) {
   if (!c) return fail(PCT_ERR_INVALID_ARG, "ctx is NULL");
   cudaStream_t next = stream ? (cudaStream_t)stream : c->own_stream;
+  pct::DeviceGuard device_guard_;
   if (next != c->stream) {
     // work queued on the old stream finishes before any on the new one starts
     PCT_CK(cudaSetDevice(c->device));
@@ -356,6 +379,7 @@ pct_status pct_geometry(const pct_ctx* c, double* R, double* du, int32_t* K, int
 
 pct_status pct_mlp_table(pct_ctx* c, double* out, int to_device) {
   if (!c || !out) return fail(PCT_ERR_INVALID_ARG, "ctx or out is NULL");
+  pct::DeviceGuard device_guard_;
   PCT_CK(cudaSetDevice(c->device));
   size_t bytes = (size_t)(c->K + 1) * 4 * sizeof(double);
   PCT_CK(cudaMemcpyAsync(out, c->tab64, bytes, to_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
@@ -393,6 +417,7 @@ pct_status pct_load_histories(pct_ctx* c, const pct_histories* h, int flags, int
     if (!src[f]) return fail(PCT_ERR_INVALID_ARG, "history array %d is NULL", f);
   if (flags != PCT_LOAD_HOST && flags != PCT_LOAD_DEVICE_COPY && flags != PCT_LOAD_DEVICE_BORROW)
     return fail(PCT_ERR_INVALID_ARG, "unknown load flags %d", flags);
+  pct::DeviceGuard device_guard_;
   PCT_CK(cudaSetDevice(c->device));
   PCT_CK(cudaStreamSynchronize(c->stream));
   reset_records(c);
@@ -479,6 +504,7 @@ pct_status pct_load_histories(pct_ctx* c, const pct_histories* h, int flags, int
 
 pct_status pct_set_hull(pct_ctx* c, const uint8_t* mask, int on_device) {
   if (!c) return fail(PCT_ERR_INVALID_ARG, "ctx is NULL");
+  pct::DeviceGuard device_guard_;
   PCT_CK(cudaSetDevice(c->device));
   PCT_CK(cudaStreamSynchronize(c->stream));
   drop_graphs(c);  // the sweep's kernels change
@@ -512,10 +538,11 @@ pct_status pct_carve_hull(pct_ctx* c, float wepl_max, int32_t dilate) {
   if (!c) return fail(PCT_ERR_INVALID_ARG, "ctx is NULL");
   if (!c->loaded) return fail(PCT_ERR_STATE, "no histories loaded");
   if (dilate < 0) return fail(PCT_ERR_INVALID_ARG, "dilate must be >= 0");
+  pct::DeviceGuard device_guard_;
   PCT_CK(cudaSetDevice(c->device));
   uint8_t *out = nullptr, *tmp = nullptr;
-  cudaError_t e = cudaMalloc((void**)&out, (size_t)c->M);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&tmp, (size_t)c->M);
+  cudaError_t e = dev_alloc((void**)&out, (size_t)c->M);
+  if (e == cudaSuccess) e = dev_alloc((void**)&tmp, (size_t)c->M);
   if (e != cudaSuccess) {
     (void)cudaGetLastError();
     cudaFree(out);
@@ -533,6 +560,7 @@ pct_status pct_carve_hull(pct_ctx* c, float wepl_max, int32_t dilate) {
 pct_status pct_get_hull(pct_ctx* c, uint8_t* out) {
   if (!c || !out) return fail(PCT_ERR_INVALID_ARG, "ctx or out is NULL");
   if (!c->hull_mask) return fail(PCT_ERR_STATE, "no hull set");
+  pct::DeviceGuard device_guard_;
   PCT_CK(cudaSetDevice(c->device));
   PCT_CK(cudaMemcpyAsync(out, c->hull_mask, (size_t)c->M, cudaMemcpyDeviceToHost, c->stream));
   return sync_and_check(c);
@@ -543,6 +571,7 @@ pct_status pct_hull_ranges(pct_ctx* c, int64_t first, int64_t count, int32_t* ou
   if (!c->loaded) return fail(PCT_ERR_STATE, "no histories loaded");
   if (!c->hull_mask) return fail(PCT_ERR_STATE, "no hull set");
   if (first < 0 || count < 0 || first + count > c->n) return fail(PCT_ERR_INVALID_ARG, "range outside [0, n)");
+  pct::DeviceGuard device_guard_;
   PCT_CK(cudaSetDevice(c->device));
   if (count == 0) return PCT_OK;
   int32_t* d = nullptr;
@@ -560,6 +589,7 @@ pct_status pct_hull_ranges(pct_ctx* c, int64_t first, int64_t count, int32_t* ou
 pct_status pct_mlp_table_n(pct_ctx* c, int32_t n, double* out) {
   if (!c || !out) return fail(PCT_ERR_INVALID_ARG, "ctx or out is NULL");
   if (n < 1 || n > c->K) return fail(PCT_ERR_INVALID_ARG, "n must be in [1, K]");
+  pct::DeviceGuard device_guard_;
   PCT_CK(cudaSetDevice(c->device));
   double* d = nullptr;
   PCT_ALLOC(d, (size_t)(n + 1) * 4 * sizeof(double));
@@ -580,6 +610,7 @@ pct_status pct_mlp_rows(pct_ctx* c, int64_t first, int64_t count, int64_t* row_p
   if (!c->loaded) return fail(PCT_ERR_STATE, "no histories loaded");
   if (first < 0 || count < 0 || first + count > c->n) return fail(PCT_ERR_INVALID_ARG, "range outside [0, n)");
   if (cap < 0 || (cap > 0 && (!vox || !len))) return fail(PCT_ERR_INVALID_ARG, "bad row buffers");
+  pct::DeviceGuard device_guard_;
   PCT_CK(cudaSetDevice(c->device));
   PCT_CK(pct::launch_row_counts(c->geo, c->rec, c->tab32, pct::hull_view(c), first, count, c->where, row_ptr,
                                 c->stream));
@@ -602,6 +633,7 @@ pct_status pct_project(pct_ctx* c, int64_t first, int64_t count, float* y) {
   if (!c || (count > 0 && !y)) return fail(PCT_ERR_INVALID_ARG, "ctx or y is NULL");
   if (!c->loaded) return fail(PCT_ERR_STATE, "no histories loaded");
   if (first < 0 || count < 0 || first + count > c->n) return fail(PCT_ERR_INVALID_ARG, "range outside [0, n)");
+  pct::DeviceGuard device_guard_;
   PCT_CK(cudaSetDevice(c->device));
   PCT_CK(pct::launch_project(c->geo, c->rec, c->tab32, pct::hull_view(c), first, count, c->where, c->x, c->cfg.flags,
                              y, c->stream));
@@ -613,6 +645,7 @@ pct_status pct_residual(pct_ctx* c, int64_t stride, double* sum_sq) {
   if (!c || !sum_sq) return fail(PCT_ERR_INVALID_ARG, "ctx or sum_sq is NULL");
   if (stride < 1) return fail(PCT_ERR_INVALID_ARG, "stride must be >= 1");
   if (!c->loaded) return fail(PCT_ERR_STATE, "no histories loaded");
+  pct::DeviceGuard device_guard_;
   PCT_CK(cudaSetDevice(c->device));
   PCT_CK(cudaMemsetAsync(c->acc, 0, sizeof(double), c->stream));
   PCT_CK(pct::launch_residual(c->geo, c->rec, c->tab32, pct::hull_view(c), c->n, stride, c->x, c->cfg.flags, c->acc,
@@ -626,6 +659,7 @@ pct_status pct_block_counts(pct_ctx* c, int32_t block, float* out) {
   if (!c || !out) return fail(PCT_ERR_INVALID_ARG, "ctx or out is NULL");
   if (!c->loaded) return fail(PCT_ERR_STATE, "no histories loaded");
   if (block < 0 || block >= c->cfg.n_blocks) return fail(PCT_ERR_INVALID_ARG, "block out of range");
+  pct::DeviceGuard device_guard_;
   PCT_CK(cudaSetDevice(c->device));
   const int64_t lo = block_lo(c, block), hi = block_lo(c, block + 1);
   PCT_CK(cudaMemsetAsync(c->cnt, 0, (size_t)c->M * sizeof(unsigned int), c->stream));
@@ -638,6 +672,7 @@ pct_status pct_block_counts(pct_ctx* c, int32_t block, float* out) {
 
 pct_status pct_set_x0(pct_ctx* c, const float* x0, int on_device) {
   if (!c || !x0) return fail(PCT_ERR_INVALID_ARG, "ctx or x0 is NULL");
+  pct::DeviceGuard device_guard_;
   PCT_CK(cudaSetDevice(c->device));
   PCT_CK(cudaMemcpyAsync(c->x, x0, (size_t)c->M * sizeof(float),
                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
@@ -713,6 +748,7 @@ pct_status pct_iterate(pct_ctx* c, int32_t n_sweeps) {
   if (!c) return fail(PCT_ERR_INVALID_ARG, "ctx is NULL");
   if (!c->loaded) return fail(PCT_ERR_STATE, "no histories loaded");
   if (n_sweeps < 0) return fail(PCT_ERR_INVALID_ARG, "n_sweeps < 0");
+  pct::DeviceGuard device_guard_;
   PCT_CK(cudaSetDevice(c->device));
   if (n_sweeps == 0) return PCT_OK;
   // the capture stream must not have pending work from another stream
@@ -740,9 +776,41 @@ pct_status pct_iterate(pct_ctx* c, int32_t n_sweeps) {
   return PCT_OK;
 }
 
+pct_status pct_block_partial(pct_ctx* c, int32_t block, float* delta_out, float* counts_out) {
+  if (!c || !delta_out) return fail(PCT_ERR_INVALID_ARG, "ctx or delta_out is NULL");
+  if (!c->loaded) return fail(PCT_ERR_STATE, "no histories loaded");
+  if (block < 0 || block >= c->cfg.n_blocks) return fail(PCT_ERR_INVALID_ARG, "block out of range");
+  pct::DeviceGuard device_guard_;
+  PCT_CK(cudaSetDevice(c->device));
+  const int64_t lo = block_lo(c, block), hi = block_lo(c, block + 1);
+  const size_t bytes = (size_t)c->M * sizeof(float);
+  PCT_CK(cudaMemsetAsync(delta_out, 0, bytes, c->stream));
+  if (counts_out) PCT_CK(cudaMemsetAsync(c->cnt, 0, (size_t)c->M * sizeof(unsigned int), c->stream));
+  PCT_CK(pct::launch_drop_fused(c->geo, c->rec, c->tab32, pct::hull_view(c), lo, hi - lo, c->x, delta_out,
+                                c->cfg.lambda, c->cfg.flags, c->cfg.cta_threads, c->stream,
+                                counts_out ? c->cnt : nullptr));
+  c->launches += 1;
+  if (counts_out) {
+    PCT_CK(pct::launch_counts_to_float(c->cnt, counts_out, c->M, c->stream));
+    c->launches += 1;
+  }
+  return PCT_OK;
+}
+
+pct_status pct_block_apply(pct_ctx* c, const float* delta, const float* counts) {
+  if (!c || !delta || !counts) return fail(PCT_ERR_INVALID_ARG, "ctx, delta or counts is NULL");
+  pct::DeviceGuard device_guard_;
+  PCT_CK(cudaSetDevice(c->device));
+  PCT_CK(pct::launch_apply_reduced(c->x, delta, counts, c->M, (c->cfg.flags & PCT_FLAG_CLAMP) != 0, c->cfg.clamp_min,
+                                   c->stream));
+  c->launches += 1;
+  return PCT_OK;
+}
+
 pct_status pct_last_sweep_times(pct_ctx* c, float* fused_ms, float* apply_ms) {
   if (!c) return fail(PCT_ERR_INVALID_ARG, "ctx is NULL");
   if (!c->ev || !c->swept) return fail(PCT_ERR_STATE, "profiling off or no sweep run yet");
+  pct::DeviceGuard device_guard_;
   PCT_CK(cudaSetDevice(c->device));
   pct_status st = sync_and_check(c);
   if (st != PCT_OK) return st;
@@ -758,6 +826,7 @@ pct_status pct_last_sweep_times(pct_ctx* c, float* fused_ms, float* apply_ms) {
 
 pct_status pct_get_rsp(pct_ctx* c, float* out, int to_device) {
   if (!c || !out) return fail(PCT_ERR_INVALID_ARG, "ctx or out is NULL");
+  pct::DeviceGuard device_guard_;
   PCT_CK(cudaSetDevice(c->device));
   if (to_device) {
     PCT_CK(cudaMemcpyAsync(out, c->x, (size_t)c->M * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
@@ -774,6 +843,7 @@ pct_status pct_get_rsp(pct_ctx* c, float* out, int to_device) {
 
 pct_status pct_sync(pct_ctx* c) {
   if (!c) return fail(PCT_ERR_INVALID_ARG, "ctx is NULL");
+  pct::DeviceGuard device_guard_;
   PCT_CK(cudaSetDevice(c->device));
   return sync_and_check(c);
 }

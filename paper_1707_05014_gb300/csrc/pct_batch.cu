@@ -353,6 +353,7 @@ pct_status pct_batch_create(pct_batch** out, pct_ctx* const* ctxs, int32_t n, co
   b->ctx.assign(ctxs, ctxs + n);
   for (int r = 0; r < n; ++r) b->gen.push_back(ctxs[r]->generation);
   if (cfg) b->cfg = *cfg;
+  pct::DeviceGuard device_guard_;
   pct_status st = PCT_OK;
   do {
     cudaError_t e = cudaSetDevice(b->device);
@@ -413,6 +414,7 @@ pct_status pct_batch_create(pct_batch** out, pct_ctx* const* ctxs, int32_t n, co
 
 pct_status pct_batch_destroy(pct_batch* b) {
   if (!b) return PCT_OK;
+  pct::DeviceGuard device_guard_;
   cudaSetDevice(b->device);
   if (b->own_stream) cudaStreamSynchronize(b->own_stream);
   free_plan(b);
@@ -435,6 +437,7 @@ pct_status pct_batch_iterate(pct_batch* b, int32_t n_sweeps, void* stream) {
   pct_status cs = check_contexts(b);
   if (cs != PCT_OK) return cs;
   if (n_sweeps == 0) return PCT_OK;
+  pct::DeviceGuard device_guard_;
   PCT_BCK(cudaSetDevice(b->device));
   cudaStream_t s = stream ? (cudaStream_t)stream : b->own_stream;
   // work a context queued on its own stream (a load's counting sweep, its own
@@ -473,6 +476,7 @@ pct_status pct_batch_iterate(pct_batch* b, int32_t n_sweeps, void* stream) {
 
 pct_status pct_batch_sync(pct_batch* b, void* stream) {
   if (!b) return bfail(PCT_ERR_INVALID_ARG, "batch is NULL");
+  pct::DeviceGuard device_guard_;
   PCT_BCK(cudaSetDevice(b->device));
   cudaStream_t s = stream ? (cudaStream_t)stream : b->own_stream;
   PCT_BCK(cudaStreamSynchronize(s));
@@ -484,6 +488,7 @@ pct_status pct_batch_autotune(pct_batch* b, pct_batch_config* chosen, float* bes
   if (!b) return bfail(PCT_ERR_INVALID_ARG, "batch is NULL");
   pct_status cs = check_contexts(b);
   if (cs != PCT_OK) return cs;
+  pct::DeviceGuard device_guard_;
   PCT_BCK(cudaSetDevice(b->device));
   cudaStream_t s = b->own_stream;
   for (auto* c : b->ctx) PCT_BCK(cudaStreamSynchronize(c->stream));  // the contexts' queued work first

@@ -96,6 +96,10 @@ cudaError_t launch_drop_fused(const Geo& g, const Rec& r, const float4* tab, con
                               unsigned int* cnt = nullptr);
 cudaError_t launch_drop_apply(float* x, float* delta, const float* inv_s, int64_t M, int clamp, float clamp_min,
                               cudaStream_t s);
+// x_j += delta_j / s_j where s_j = counts_j > 0 (else unchanged), optional
+// clamp; delta and counts are left as they are (a reduced block update).
+cudaError_t launch_apply_reduced(float* x, const float* delta, const float* counts, int64_t M, int clamp,
+                                 float clamp_min, cudaStream_t s);
 // CARP: add a string's swept copy xs to sum / touch where any of its nb
 // blocks (inv_s: nb x M) touches the voxel; then x = sum / touch where
 // touched, else x0, and sum = touch = 0.
@@ -120,6 +124,25 @@ cudaError_t launch_scan_rows(int64_t* row_ptr, int64_t count, cudaStream_t s);
 cudaError_t launch_row_fill(const Geo& g, const Rec& r, const float4* tab, const Hull& hull, int64_t first, int64_t count,
                             const int64_t* where, const int64_t* row_ptr, int32_t* vox, float* len, int32_t* nodes,
                             cudaStream_t s);
+
+// Saves the calling thread's current device and restores it when the entry
+// point returns: the library switches to a context's device for its work and
+// must not leave the caller (or a later call that uses the current device) on
+// another one.
+struct DeviceGuard {
+  int prev = -1;
+  DeviceGuard() {
+    if (cudaGetDevice(&prev) != cudaSuccess) {
+      (void)cudaGetLastError();
+      prev = -1;
+    }
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+  DeviceGuard(const DeviceGuard&) = delete;
+  DeviceGuard& operator=(const DeviceGuard&) = delete;
+};
 
 // Set the text that pct_last_error() returns on the calling thread.
 void set_error_text(const char* msg);

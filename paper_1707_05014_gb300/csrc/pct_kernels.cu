@@ -161,6 +161,19 @@ __global__ void drop_apply_kernel(float* __restrict__ x, float* __restrict__ del
   apply_voxel(x, delta, inv_s, j, clamp, clamp_min);
 }
 
+// DROP block update from a block's update buffer and run counts summed over
+// the ranks that share the block (Sec. 1 / 3.1: the data are distributed over
+// processors): the same arithmetic as apply_voxel with 1/s_j formed here.
+__global__ void apply_reduced_kernel(float* __restrict__ x, const float* __restrict__ delta,
+                                     const float* __restrict__ counts, int64_t M, int clamp, float clamp_min) {
+  int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= M) return;
+  const float s = counts[j];
+  float xv = __fmaf_rn(delta[j], s > 0.f ? 1.0f / s : 0.0f, x[j]);
+  if (clamp) xv = fmaxf(xv, clamp_min);
+  x[j] = xv;
+}
+
 // CARP (Sec. 2.2): after string s has swept its blocks on the working copy
 // x_s, add it to the per-voxel sum where the string touched the voxel (any of
 // its blocks has s_j > 0).
@@ -554,6 +567,12 @@ cudaError_t launch_residual(const Geo& g, const Rec& r, const float4* tab, const
 cudaError_t launch_drop_apply(float* x, float* delta, const float* inv_s, int64_t M, int clamp, float clamp_min,
                               cudaStream_t s) {
   drop_apply_kernel<<<grid_for(M, 256), 256, 0, s>>>(x, delta, inv_s, M, clamp, clamp_min);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_apply_reduced(float* x, const float* delta, const float* counts, int64_t M, int clamp,
+                                 float clamp_min, cudaStream_t s) {
+  apply_reduced_kernel<<<grid_for(M, 256), 256, 0, s>>>(x, delta, counts, M, clamp, clamp_min);
   return cudaGetLastError();
 }
 

@@ -594,6 +594,7 @@ pct_status pct_net_create(pct_net** out, int32_t nz, int32_t ny, int32_t nx, uin
       for (int ci = 0; ci < cin_real; ++ci)
         for (int co = 0; co < cout_real; ++co) p[ly.w_off + ((int64_t)t * ly.Cin + ci) * ly.Cout + co] = (float)(sd * nd(rng));
   }
+  pct::DeviceGuard device_guard_;
   pct_status st = PCT_OK;
   do {
     cudaError_t e = cudaSetDevice(device);
@@ -649,6 +650,7 @@ pct_status pct_net_create(pct_net** out, int32_t nz, int32_t ny, int32_t nx, uin
 
 pct_status pct_net_destroy(pct_net* nt) {
   if (!nt) return PCT_OK;
+  pct::DeviceGuard device_guard_;
   cudaSetDevice(nt->device);
   if (nt->own_stream) cudaStreamSynchronize(nt->own_stream);
   for (auto& a : nt->act) cudaFree(a.p);
@@ -673,6 +675,7 @@ int64_t pct_net_param_count(const pct_net* nt) { return nt ? nt->n_params : 0; }
 
 pct_status pct_net_get_params(pct_net* nt, float* out) {
   if (!nt || !out) return nfail(PCT_ERR_INVALID_ARG, "net or out is NULL");
+  pct::DeviceGuard device_guard_;
   NET_CK(cudaSetDevice(nt->device));
   NET_CK(cudaMemcpy(out, nt->params, nt->n_params * sizeof(float), cudaMemcpyDeviceToHost));
   return PCT_OK;
@@ -680,6 +683,7 @@ pct_status pct_net_get_params(pct_net* nt, float* out) {
 
 pct_status pct_net_set_params(pct_net* nt, const float* in) {
   if (!nt || !in) return nfail(PCT_ERR_INVALID_ARG, "net or in is NULL");
+  pct::DeviceGuard device_guard_;
   NET_CK(cudaSetDevice(nt->device));
   NET_CK(cudaMemcpy(nt->params, in, nt->n_params * sizeof(float), cudaMemcpyHostToDevice));
   pct_status st = refresh_weights(nt, nt->own_stream);
@@ -690,6 +694,7 @@ pct_status pct_net_set_params(pct_net* nt, const float* in) {
 
 pct_status pct_net_forward(pct_net* nt, const float* x1, float* x0, void* stream) {
   if (!nt || !x1 || !x0) return nfail(PCT_ERR_INVALID_ARG, "NULL argument");
+  pct::DeviceGuard device_guard_;
   NET_CK(cudaSetDevice(nt->device));
   return net_forward(nt, x1, x0, stream ? (cudaStream_t)stream : nt->own_stream);
 }
@@ -697,6 +702,7 @@ pct_status pct_net_forward(pct_net* nt, const float* x1, float* x0, void* stream
 pct_status pct_net_gradients(pct_net* nt, const float* x1, const float* target, float* x0_scratch, float* grads_host,
                              double* loss) {
   if (!nt || !x1 || !target || !x0_scratch) return nfail(PCT_ERR_INVALID_ARG, "NULL argument");
+  pct::DeviceGuard device_guard_;
   NET_CK(cudaSetDevice(nt->device));
   cudaStream_t s = nt->own_stream;
   pct_status st = net_forward(nt, x1, x0_scratch, s);
@@ -712,6 +718,7 @@ pct_status pct_net_train_step(pct_net* nt, const float* x1, const float* target,
                               double* loss, void* stream) {
   if (!nt || !x1 || !target || !x0_scratch) return nfail(PCT_ERR_INVALID_ARG, "NULL argument");
   if (!(lr > 0.f)) return nfail(PCT_ERR_INVALID_ARG, "lr must be > 0");
+  pct::DeviceGuard device_guard_;
   NET_CK(cudaSetDevice(nt->device));
   cudaStream_t s = stream ? (cudaStream_t)stream : nt->own_stream;
   pct_status st = net_forward(nt, x1, x0_scratch, s);

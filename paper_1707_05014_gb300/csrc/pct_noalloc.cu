@@ -9,8 +9,6 @@
 #include <math.h>
 #include <stdio.h>
 
-#include <mutex>
-
 #include "../../include/pct.h"
 #include "pct_walk.cuh"
 
@@ -37,12 +35,6 @@ constexpr size_t kOffFlag = kOffTab32 + kMaxNodes * sizeof(float4);
 constexpr size_t kScratchBytes = kOffFlag + 256;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
-
-// Device address of g_noalloc_scratch per device, looked up once per device
-// with that device current (the host-side symbol is only a stand-in).
-constexpr int kMaxDevices = 64;
-unsigned char* g_scratch_addr[kMaxDevices] = {};
-std::mutex g_scratch_mu;
 
 // Errors are reported through pct_last_error(), like every other entry point.
 pct_status noalloc_fail(pct_status code, const char* msg, cudaError_t e = cudaSuccess) {
@@ -138,22 +130,14 @@ extern "C" pct_status pct_drop_block_noalloc(const pct_grid* grid, const pct_con
   g.by = (float)(0.5 * Y);
   const Rec r{src[0], src[1], src[2], src[3], src[4], src[5], src[6], src[7], src[8], src[9], src[10]};
 
-  // scratch address of the current device (first call on a device)
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return noalloc_fail(PCT_ERR_CUDA, "cudaGetDevice", e);
-  if (dev < 0 || dev >= kMaxDevices) return noalloc_fail(PCT_ERR_INVALID_ARG, "device index >= 64");
+  // Device address of the scratch array in the current device's context. The
+  // host-side symbol is only a stand-in, so host code must ask for the address.
+  // It is looked up on every call (it allocates nothing), never cached: a
+  // cached address would go stale when the context is reset or another
+  // context is current on the same device.
   unsigned char* base = nullptr;
-  {
-    std::lock_guard<std::mutex> lk(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
-      void* ptr = nullptr;
-      e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-      if (e != cudaSuccess) return noalloc_fail(PCT_ERR_CUDA, "cudaGetSymbolAddress", e);
-      g_scratch_addr[dev] = (unsigned char*)ptr;
-    }
-    base = g_scratch_addr[dev];
-  }
+  cudaError_t e = cudaGetSymbolAddress((void**)&base, g_noalloc_scratch);
+  if (e != cudaSuccess) return noalloc_fail(PCT_ERR_CUDA, "cudaGetSymbolAddress", e);
   float* delta = (float*)(base + kOffDelta);
   float* inv_s = (float*)(base + kOffInv);
   double* tab64 = (double*)(base + kOffTab64);

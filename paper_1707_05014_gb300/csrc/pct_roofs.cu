@@ -110,6 +110,7 @@ extern "C" pct_status pct_measure_roofs(int device, int64_t array_bytes, pct_roo
     pct::set_error_text("array_bytes must give between 4 KB and 8 GB");
     return PCT_ERR_INVALID_ARG;
   }
+  pct::DeviceGuard device_guard_;
   cudaError_t e = cudaSetDevice(device);
   cudaDeviceProp prop{};
   if (e == cudaSuccess) e = cudaGetDeviceProperties(&prop, device);

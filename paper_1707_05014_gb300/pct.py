@@ -88,6 +88,8 @@ _SIGS = {
     "pct_get_rsp": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int],
     "pct_sync": [ctypes.c_void_p],
     "pct_last_sweep_times": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
+    "pct_block_partial": [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p],
+    "pct_block_apply": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
     "pct_batch_create": [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p), ctypes.c_int32,
                          ctypes.c_void_p],
     "pct_batch_destroy": [ctypes.c_void_p],
@@ -127,6 +129,8 @@ def load_library(path: str = LIB_PATH):
     L.pct_batch_launch_count.restype = ctypes.c_int64
     L.pct_net_param_count.argtypes = [ctypes.c_void_p]
     L.pct_net_param_count.restype = ctypes.c_int64
+    L.pct_debug_fail_alloc.argtypes = [ctypes.c_int64]
+    L.pct_debug_fail_alloc.restype = None
     if path == LIB_PATH:
         _lib = L
     return L
@@ -143,6 +147,12 @@ def measure_roofs(device: int = 0, array_bytes: int = 8 << 20) -> Dict[str, floa
     r = _Roofs()
     _check(L.pct_measure_roofs(int(device), int(array_bytes), ctypes.byref(r)))
     return {f: getattr(r, f) for f, _ in _Roofs._fields_}
+
+
+def debug_fail_alloc(k: int) -> None:
+    """Testing hook: the k-th device allocation of a context from now on fails
+    (PCT_ERR_NO_MEMORY); k <= 0 disarms it."""
+    load_library().pct_debug_fail_alloc(int(k))
 
 
 def _torch():
@@ -401,6 +411,24 @@ class Context:
         _check(self._L.pct_last_sweep_times(self._h, f.ctypes.data_as(ctypes.c_void_p),
                                             a.ctypes.data_as(ctypes.c_void_p)))
         return f, a
+
+    def block_partial(self, block: int, delta, counts=None) -> None:
+        """This context's part of DROP block `block` (pct_block_partial) into the
+        CUDA tensors delta (M floats) and, if given, counts (M floats)."""
+        _check_vector(delta, self.M, "delta", self.device)
+        if counts is not None:
+            _check_vector(counts, self.M, "counts", self.device)
+        self._bind_stream()
+        _check(self._L.pct_block_partial(self._h, int(block), ctypes.c_void_p(delta.data_ptr()),
+                                         ctypes.c_void_p(counts.data_ptr()) if counts is not None else None))
+
+    def block_apply(self, delta, counts) -> None:
+        """x += delta / counts where counts > 0 (pct_block_apply): the block
+        update from sums over the ranks that share the block."""
+        _check_vector(delta, self.M, "delta", self.device)
+        _check_vector(counts, self.M, "counts", self.device)
+        self._bind_stream()
+        _check(self._L.pct_block_apply(self._h, ctypes.c_void_p(delta.data_ptr()), ctypes.c_void_p(counts.data_ptr())))
 
     def sync(self) -> None:
         self._bind_stream()

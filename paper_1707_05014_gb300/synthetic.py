@@ -326,6 +326,16 @@ def head_workload(n: int = 50_000_000, seed: int = 2) -> Workload:
     return Workload(f"head160_{n}", g, n, seed, 90, g.radius, 40.0, 10, 10, "head")
 
 
+def head200_workload(n: int = 1_000_000_000, seed: int = 5, n_blocks: int = 50) -> Workload:
+    """200x200x48 grid of 1 x 1 x 2 mm voxels (1.92M voxels), a seeded random
+    head (outer semi-axes and inserts jittered by +-15 %), 90 projection
+    angles, vertical entry positions within +-46 mm; 1e9 histories and 50
+    blocks by default."""
+    g = Grid(200, 200, 48, 1.0, 1.0, 2.0)
+    return Workload(f"head200x200x48_{n}", g, n, seed, 90, g.radius, min(46.0, 0.5 * g.nz * g.hz - 2.0), n_blocks,
+                    10, "head", 0.15)
+
+
 def batch_workloads(n_recon: int = 32, seed: int = 4, n_min: int = 2_000_000, n_max: int = 40_000_000,
                     n_blocks: int = 10):
     """Independent reconstructions of uneven size: grids from 64x64x32 to

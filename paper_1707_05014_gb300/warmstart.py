@@ -30,7 +30,8 @@ def training_grid() -> S.Grid:
 
 
 def head_workload(grid: S.Grid, n: int, seed: int, n_blocks: int = 10) -> S.Workload:
-    """Seeded random head (outer semi-axes and inserts jittered by +-15 %)."""
+    """Seeded random head (outer semi-axes and inserts jittered by +-15 %), the
+    recipe of synthetic.head200_workload on `grid`."""
     return S.Workload(f"warm_head{seed}_{n}", grid, n, seed, 90, grid.radius,
                       min(46.0, 0.5 * grid.nz * grid.hz - 2.0), n_blocks, 10, "head", 0.15)
 

@@ -10,7 +10,9 @@ blocks, 8 sweeps), on a host-generated subset of its histories:
 * the image after the 8 sweeps against the FP64 oracle's, and both against
   the phantom.
 
-Test infrastructure (it runs the oracle); needs a GPU. Prints one JSON object.
+Test infrastructure (it runs the oracle); needs a GPU. tests/test_gpu_precision.py
+asserts the budget on a 200k-history subset; run as a script it prints one JSON
+object for a larger subset.
 
     python tests/precision_report.py [--subset 1000000] [--device 0]
 """
@@ -81,7 +83,7 @@ def report(ns: int = 1_000_000, local: int = 0) -> dict:
         c.iterate(wl.n_sweeps)
         xg = c.get_rsp().astype(np.float64)
     t0 = time.perf_counter()
-    xo = O.drop(g, sub, 40, wl.n_sweeps, mode=O.MODE_FP64)
+    xo = O.drop_threads(g, sub, 40, wl.n_sweeps, mode=O.MODE_FP64)
     t_or = time.perf_counter() - t0
     rel = np.abs(xg - xo) / np.maximum(np.abs(xo), 1.0)
     roi = S.interior_mask(x_true, g)

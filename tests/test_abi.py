@@ -158,3 +158,12 @@ def test_header_is_plain_c_and_links_against_the_library(tmp_path):
     assert r.returncode == 0, r.stderr
     out = subprocess.run([str(exe)], capture_output=True, text=True)
     assert out.returncode == 0 and int(out.stdout) == len(names)
+
+
+def test_shared_block_calls_check_arguments_before_the_gpu():
+    lib, pct = _lib_and_types()
+    assert lib.pct_block_partial(None, 0, None, None) == -1
+    assert "NULL" in lib.pct_last_error().decode()
+    assert lib.pct_block_apply(None, None, None) == -1
+    assert "NULL" in lib.pct_last_error().decode()
+    lib.pct_debug_fail_alloc(0)  # the testing hook is exported and disarms without a GPU

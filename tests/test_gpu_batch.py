@@ -1,6 +1,7 @@
 """Batched persistent launch: several reconstructions of uneven size advance in
-one launch per call; each result equals its own context's pct_iterate (the
-same DROP stages, Sec. 2.1 / Fig. 1) up to summation order, and a bounded wait
+one launch per call; each result equals its own context's pct_iterate and the
+FP64 oracle's DROP (the same stages, Sec. 2.1 / Fig. 1) up to summation order,
+element by element within the 0.1 % RSP bar, and a bounded wait
 that cannot be met ends the launch with PCT_ERR_TIMEOUT instead of a hang."""
 import numpy as np
 import pytest
@@ -34,10 +35,18 @@ def _workloads():
     ]
 
 
-@pytest.mark.parametrize("mode,chunk", [(1, 0), (1, 1000), (2, 0)])
-def test_batch_matches_individual_contexts(P, mode, chunk):
+@pytest.fixture(scope="module")
+def oracle_images(oracle):
+    """The FP64 oracle's DROP (FP32-order nodes) of every workload, 2 sweeps."""
     wls = _workloads()
     recs = [S.make_histories(w) for w, _ in wls]
+    return recs, [oracle.drop(w.grid, r, B, 2, mode=oracle.MODE_FP32) for (w, B), r in zip(wls, recs)]
+
+
+@pytest.mark.parametrize("mode,chunk", [(1, 0), (1, 1000), (2, 0)])
+def test_batch_matches_individual_contexts(P, oracle_images, mode, chunk):
+    wls = _workloads()
+    recs, oracle_x = oracle_images
     refs = []
     for (w, B), r in zip(wls, recs):
         with P.Context(w.grid, n_blocks=B) as c:
@@ -55,9 +64,12 @@ def test_batch_matches_individual_contexts(P, mode, chunk):
         b.sync()
         per_call = 1 if mode == 1 else sum(2 * B for _, B in wls)
         assert b.launches == 2 * per_call
-    for c, ref in zip(ctxs, refs):
+    for c, ref, xo in zip(ctxs, refs, oracle_x):
         x = c.get_rsp().astype(np.float64)
         err = np.abs(x - ref) / np.maximum(np.abs(ref), 1.0)
+        assert err.max() <= RSP_TOL, err.max()
+        # and element-wise against the oracle's DROP of the same blocks
+        err = np.abs(x - xo) / np.maximum(np.abs(xo), 1.0)
         assert err.max() <= RSP_TOL, err.max()
         c.close()
 

@@ -1,0 +1,50 @@
+"""Precision budget of the FP32 fused path against the FP64 oracle (the
+precision variant of the head workload: 160 x 160 x 64 grid of 1.25 mm, 40
+blocks, 8 sweeps) on a 200k-history subset, each result with its stated bar:
+
+* MLP nodes: FP32 contract order against FP64 nodes, max 1e-4 voxel;
+* index lists: >= 99 % identical to those of the FP64 nodes;
+* a_i.x: the compensated (Kahan) FP32 sum within 1e-6 of an FP64 sum over the
+  same rows, and closer to it than the plain FP32 sum; within 1e-3 (the RSP
+  bar) of the full FP64 oracle's a_i.x;
+* the image after the 8 sweeps: mean relative difference from the FP64
+  oracle's image within 1e-3, over all voxels and over the interior ROI.
+"""
+import pytest
+
+import precision_report
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def budget():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA GPU required for -m gpu tests")
+    return precision_report.report(200_000)
+
+
+def test_nodes_within_1e4_voxel_of_fp64(budget):
+    assert budget["node_error_voxels"]["max"] <= 1e-4, budget["node_error_voxels"]
+
+
+def test_index_lists_mostly_identical_to_fp64_nodes(budget):
+    assert budget["index_lists_identical_to_fp64_nodes"] >= 0.99
+
+
+def test_compensated_sum_beats_plain_sum(budget):
+    e = budget["ax_rel_error_vs_fp64_sum_same_rows"]
+    assert e["kahan"]["max"] <= 1e-6, e
+    assert e["kahan"]["max"] < e["plain"]["max"], e
+    assert e["kahan"]["mean"] < e["plain"]["mean"], e
+
+
+def test_projection_within_rsp_bar_of_fp64_oracle(budget):
+    assert budget["ax_rel_error_vs_fp64_oracle"]["max"] <= 1e-3, budget["ax_rel_error_vs_fp64_oracle"]
+
+
+def test_image_within_rsp_bar_of_fp64_oracle(budget):
+    e = budget["rsp_error_vs_fp64_oracle"]
+    assert e["mean"] <= 1e-3 and e["roi_mean"] <= 1e-3, e
