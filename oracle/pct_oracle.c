@@ -37,7 +37,12 @@
  *   - nodes are quantised to Q20 fixed point in grid units (round half even,
  *     clamped to +-1000 voxels) and walked by an exact integer DDA: voxels
  *     are half-open, tied face crossings step together, zero-length runs are
- *     never emitted, a run is a maximal stretch in one voxel.
+ *     never emitted, a run is a maximal stretch in one voxel. In the FP32
+ *     mode the grid coordinate is formed 16 voxels above its value
+ *     (fma(p, 1/h, n/2 + 16)) and the 16 voxels are taken off after the
+ *     rounding: every coordinate within 8 voxels of the grid is then at
+ *     least 8, where an FP32 value is already a whole multiple of 2^-20, so
+ *     the quantisation only rounds coordinates far outside the grid.
  *   - DROP: x <- x + lambda S_b^-1 sum_{i in b} a_i (b_i - a_i.x)/|a_i|^2 with
  *     S_b = diag(number of runs in voxel j over block b); block b holds
  *     protons [b N / B, (b+1) N / B).
@@ -306,10 +311,14 @@ static int32_t or_quant_d(double q) {
   return (int32_t)lrint(q * (double)OR_QONE); /* default mode: half to even */
 }
 
+/* FP32 mode: grid coordinates are formed OR_QOFF voxels above their value and
+ * the offset is removed after rounding (see the readings above). */
+#define OR_QOFF 16
+
 static int32_t or_quant_f(float q) {
   if (q < (float)-OR_QCLAMP) q = (float)-OR_QCLAMP;
   if (q > (float)OR_QCLAMP) q = (float)OR_QCLAMP;
-  return (int32_t)lrintf(q * 1048576.0f);
+  return (int32_t)lrintf(q * 1048576.0f) - (int32_t)(OR_QOFF * OR_QONE);
 }
 
 /*
@@ -341,9 +350,9 @@ static void or_quantise_f(const or_grid *g, const or_rec *r, int64_t i, float u,
   float x = fmaf(u, cp, -ts);
   float y = fmaf(u, sp, tc);
   float ihx = (float)(1.0 / g->hx), ihy = (float)(1.0 / g->hy), ihz = (float)(1.0 / g->hz);
-  Q[0] = or_quant_f(fmaf(x, ihx, 0.5f * (float)g->nx));
-  Q[1] = or_quant_f(fmaf(y, ihy, 0.5f * (float)g->ny));
-  Q[2] = or_quant_f(fmaf(v, ihz, 0.5f * (float)g->nz));
+  Q[0] = or_quant_f(fmaf(x, ihx, 0.5f * (float)g->nx + (float)OR_QOFF));
+  Q[1] = or_quant_f(fmaf(y, ihy, 0.5f * (float)g->ny + (float)OR_QOFF));
+  Q[2] = or_quant_f(fmaf(v, ihz, 0.5f * (float)g->nz + (float)OR_QOFF));
 }
 
 /* Lateral/vertical position at node k of the entry ray (exit = 0) or the

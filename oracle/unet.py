@@ -147,9 +147,12 @@ def forward_scale(p: np.ndarray, x1: np.ndarray, bf16: bool = False) -> np.ndarr
 
 def loss_and_grads(p: np.ndarray, x1: np.ndarray, target: np.ndarray, bf16: bool = False, scales: bool = False):
     """L1 loss mean|x0 - target| and its gradient w.r.t. p (flat, like p).
-    With scales=True also returns, per parameter, the sum of the magnitudes
-    of the terms of its gradient (sum |h| |g| for a weight, sum |g| for a
-    bias), the scale of an element-wise bound on the gradient."""
+    With scales=True also returns, per parameter, the scale of an element-wise
+    bound on its gradient: sum |h| G for a weight and sum G for a bias, where G
+    is the magnitude chain of the backward pass -- |dLoss/df| carried back
+    through every layer with |W| in place of W and the same ReLU masks -- so
+    that G bounds the sum of the magnitudes of all the terms that make up each
+    stored gradient element."""
     q = (lambda a: to_bf16(a)) if bf16 else (lambda a: a)
     x0, c = forward(p, x1, bf16)
     n = x0.size
@@ -160,6 +163,8 @@ def loss_and_grads(p: np.ndarray, x1: np.ndarray, target: np.ndarray, bf16: bool
     df = np.zeros(x0.shape + (16,))
     df[..., 0] = np.sign(x0 - target) / n
     gpre[nl - 1] = q(df)
+    gabs = [None] * nl
+    gabs[nl - 1] = np.abs(gpre[nl - 1])
     grads = []
     sgrads = []
     for li in range(nl - 1, -1, -1):
@@ -174,7 +179,7 @@ def loss_and_grads(p: np.ndarray, x1: np.ndarray, target: np.ndarray, bf16: bool
         else:
             dW = conv_wgrad(up2(h), g, 1)
         if scales:
-            ah, ag = np.abs(h), np.abs(g)
+            ah, ag = np.abs(h), gabs[li]
             if kind == "s1":
                 sW = conv_wgrad(ah, ag, 1)
             elif kind == "s2":
@@ -195,6 +200,18 @@ def loss_and_grads(p: np.ndarray, x1: np.ndarray, target: np.ndarray, bf16: bool
             if skip == li - 1:
                 dh = dh + gpre[u]
         gpre[li - 1] = q(dh * (acts[li - 1] > 0))
+        if scales:
+            aW = np.abs(W)
+            if kind == "s1":
+                da = conv_adjoint(h.shape, gabs[li], aW, 1)
+            elif kind == "s2":
+                da = conv_adjoint(h.shape, gabs[li], aW, 2)
+            else:
+                da = down2_sum(conv_adjoint(up2(h).shape, gabs[li], aW, 1))
+            for u, (_, _, _, skip) in enumerate(SPEC):
+                if skip == li - 1:
+                    da = da + gabs[u]
+            gabs[li - 1] = da * (acts[li - 1] > 0)
     off = []
     o = 0
     for ci, co, _, _ in SPEC:

@@ -7,6 +7,7 @@
 
 #include <atomic>
 #include <string>
+#include <vector>
 
 #include "../../include/pct.h"
 #include "pct_ctx.h"
@@ -220,25 +221,7 @@ pct_status pct_create(pct_ctx** out, const pct_grid* grid, const pct_config* cfg
       return fail(PCT_ERR_INVALID_ARG, "grid too large for the fixed-point node range (%.0f voxels)", qmax);
     }
   }
-  Geo& G = c->geo;
-  G.nx = g.nx;
-  G.ny = g.ny;
-  G.nz = g.nz;
-  G.K = c->K;
-  G.E = c->E;
-  G.du = (float)c->du;
-  G.u0 = (float)(-c->R);
-  G.hx = (float)g.hx;
-  G.hy = (float)g.hy;
-  G.hz = (float)g.hz;
-  G.ihx = (float)(1.0 / g.hx);
-  G.ihy = (float)(1.0 / g.hy);
-  G.ihz = (float)(1.0 / g.hz);
-  G.hnx = 0.5f * (float)g.nx;
-  G.hny = 0.5f * (float)g.ny;
-  G.hnz = 0.5f * (float)g.nz;
-  G.bx = (float)(0.5 * X);
-  G.by = (float)(0.5 * Y);
+  c->geo = pct::make_geo(g.nx, g.ny, g.nz, g.hx, g.hy, g.hz, c->R, c->du, c->K, c->E);
 
   pct::DeviceGuard device_guard_;
   pct_status st = PCT_OK;
@@ -272,6 +255,16 @@ pct_status pct_create(pct_ctx** out, const pct_grid* grid, const pct_config* cfg
         (e = cudaStreamSynchronize(c->stream)) != cudaSuccess) {
       st = fail(PCT_ERR_CUDA, "context set-up: %s", cudaGetErrorString(e));
       break;
+    }
+    {
+      // the table's largest node-to-node step bounds every MLP segment (the
+      // walk's per-history choice between its two forms)
+      std::vector<float4> th((size_t)c->K + 1);
+      if ((e = cudaMemcpy(th.data(), c->tab32, th.size() * sizeof(float4), cudaMemcpyDeviceToHost)) != cudaSuccess) {
+        st = fail(PCT_ERR_CUDA, "table read-back: %s", cudaGetErrorString(e));
+        break;
+      }
+      pct::set_table_bound(c->geo, th.data(), c->K);
     }
     c->launches += 1;
     if (c->cfg.flags & PCT_FLAG_CARP) {

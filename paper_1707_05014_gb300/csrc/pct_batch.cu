@@ -77,8 +77,13 @@ __device__ __noinline__ void run_chunk(const ReconDesc* __restrict__ R, int64_t 
   float* delta = R->delta;
   const float lambda = R->lambda;
   const int flags = R->flags;
-  for (int64_t p = threadIdx.x; p < count; p += kThreads)
-    pct::drop_history<true>(g, tab, load_rec_ptrs(R), first + p, x, delta, lambda, flags);
+  if (flags & 2) {
+    for (int64_t p = threadIdx.x; p < count; p += kThreads)
+      pct::drop_history<true, true>(g, tab, load_rec_ptrs(R), first + p, x, delta, lambda);
+  } else {
+    for (int64_t p = threadIdx.x; p < count; p += kThreads)
+      pct::drop_history<true, false>(g, tab, load_rec_ptrs(R), first + p, x, delta, lambda);
+  }
 }
 
 __global__ void __launch_bounds__(kThreads, 6) batch_kernel(const ReconDesc* __restrict__ recs,

@@ -19,62 +19,43 @@ __device__ __forceinline__ float ld_weak(const float* p) {
 }
 
 // MLP nodes -> walk -> compensated a_i.x and |a_i|^2 -> relaxed residual ->
-// scatter-add into delta. The walk keeps the row (voxel, chord) in
-// thread-local memory; the dot product and the scatter replay it. A row
-// longer than kRowCap runs (none for valid records on the supported grids) is
-// walked again for each of them instead. flags & 2: plain instead of
-// compensated summation.
+// scatter-add into delta. The walk gathers x for each run as it emits it
+// (a_i.x and |a_i|^2 are complete when the walk ends) and records the row
+// (voxel, chord) in thread-local memory; the scatter replays the record. A
+// row longer than kRowCap runs (none for valid records on the supported
+// grids) is walked again for the scatter instead.
 //
+// kPlain: plain instead of compensated summation (PCT_FLAG_NO_KAHAN).
 // kCoherent: x may change while the kernel runs (the batched persistent
 // kernel applies block updates between work items), so x is read with plain
 // weak loads instead of the read-only path (which assumes data that never
 // changes during the launch).
-template <bool kCoherent, class Walk>
+// cnt (kCount): also add every run to the block's run counts s_j (the first
+// sweep after a load forms the DROP weights this way).
+template <bool kCoherent, bool kPlain, bool kCount, class Walk>
 __device__ __forceinline__ void drop_history_core(const RecV& v, Walk&& walk, const float* __restrict__ x,
-                                                  float* __restrict__ delta, float lambda, int flags) {
+                                                  float* __restrict__ delta, float lambda,
+                                                  unsigned int* __restrict__ cnt = nullptr) {
   auto xload = [&](int j) { return kCoherent ? ld_weak(x + j) : __ldg(x + j); };
-  // The walk only records the row; the gather of x and the scatter run as two
-  // replays of the recorded row, outside the walk's divergent crossing loop.
   uint2 row[kRowCap];
   int nrow = 0;
+  float y = 0.f, c = 0.f, nn = 0.f;
   walk([&](int j, float l) {
+    const float xj = xload(j);
+    if (kPlain) {
+      y = __fmaf_rn(l, xj, y);
+    } else {
+      // Kahan-compensated sum of l * x_j: the true sum is y - c
+      const float term = __fsub_rn(__fmul_rn(l, xj), c);
+      const float t = __fadd_rn(y, term);
+      c = __fsub_rn(__fsub_rn(t, y), term);
+      y = t;
+    }
+    nn = __fmaf_rn(l, l, nn);
+    if (kCount) atomicAdd(cnt + j, 1u);
     if (nrow < kRowCap) row[nrow] = make_uint2((unsigned)j, __float_as_uint(l));
     ++nrow;
   });
-  float y = 0.f, c = 0.f, nn = 0.f;
-  if (nrow <= kRowCap) {
-    if (flags & 2) {
-      for (int q = 0; q < nrow; ++q) {
-        const uint2 e = row[q];
-        const float l = __uint_as_float(e.y);
-        y = __fmaf_rn(l, xload((int)e.x), y);
-        nn = __fmaf_rn(l, l, nn);
-      }
-    } else {
-      // Kahan-compensated sum of l * x_j: the true sum is y - c
-      for (int q = 0; q < nrow; ++q) {
-        const uint2 e = row[q];
-        const float l = __uint_as_float(e.y);
-        const float term = __fsub_rn(__fmul_rn(l, xload((int)e.x)), c);
-        const float t = __fadd_rn(y, term);
-        c = __fsub_rn(__fsub_rn(t, y), term);
-        y = t;
-        nn = __fmaf_rn(l, l, nn);
-      }
-    }
-  } else {
-    walk([&](int j, float l) {
-      if (flags & 2) {
-        y = __fmaf_rn(l, xload(j), y);
-      } else {
-        const float term = __fsub_rn(__fmul_rn(l, xload(j)), c);
-        const float t = __fadd_rn(y, term);
-        c = __fsub_rn(__fsub_rn(t, y), term);
-        y = t;
-      }
-      nn = __fmaf_rn(l, l, nn);
-    });
-  }
   if (!(nn > 0.f)) return;
   const float res = __fadd_rn(__fsub_rn(v.wepl, y), c);
   const float ri = lambda * res / nn;
@@ -88,105 +69,42 @@ __device__ __forceinline__ void drop_history_core(const RecV& v, Walk&& walk, co
   }
 }
 
-template <bool kCoherent = false>
+template <bool kCoherent = false, bool kPlain = false>
 __device__ __forceinline__ void drop_history(const Geo& g, const float4* __restrict__ tab, const Rec& r, int64_t i,
-                                             const float* __restrict__ x, float* __restrict__ delta, float lambda,
-                                             int flags) {
+                                             const float* __restrict__ x, float* __restrict__ delta, float lambda) {
   const RecV v = load_rec(r, i);
-  drop_history_core<kCoherent>(v, [&](auto&& visit) { walk_proton(g, tab, v, visit); }, x, delta, lambda, flags);
+  drop_history_core<kCoherent, kPlain, false>(v, [&](auto&& visit) { walk_proton(g, tab, v, visit); }, x, delta,
+                                              lambda);
 }
 
 // The same with an object hull (the MLP between the proton's hull nodes).
+template <bool kPlain = false>
 __device__ __forceinline__ void drop_history_hull(const Geo& g, const Hull& hull, const Rec& r, int64_t i,
-                                                  const float* __restrict__ x, float* __restrict__ delta, float lambda,
-                                                  int flags) {
+                                                  const float* __restrict__ x, float* __restrict__ delta, float lambda) {
   const RecV v = load_rec(r, i);
   const int32_t range = __ldg(hull.range + i);
-  drop_history_core<false>(v, [&](auto&& visit) { walk_proton_hull(g, hull.fam, range, v, visit); }, x, delta, lambda,
-                           flags);
+  drop_history_core<false, kPlain, false>(v, [&](auto&& visit) { walk_proton_hull(g, hull.fam, range, v, visit); },
+                                          x, delta, lambda);
 }
 
-// drop_history_core that also adds every run of the history to cnt (the
-// block's run counts s_j): the first sweep after a load forms the DROP
-// weights this way instead of in a separate counting pass. Kept as its own
-// copy so that the every-sweep path above compiles exactly as it is.
-template <class Walk>
-__device__ __forceinline__ void drop_history_core_count(const RecV& v, Walk&& walk, const float* __restrict__ x,
-                                                        float* __restrict__ delta, float lambda, int flags,
-                                                        unsigned int* __restrict__ cnt) {
-  auto xload = [&](int j) { return __ldg(x + j); };
-  // The walk only records the row; the gather of x and the scatter run as two
-  // replays of the recorded row, outside the walk's divergent crossing loop.
-  uint2 row[kRowCap];
-  int nrow = 0;
-  walk([&](int j, float l) {
-    if (nrow < kRowCap) row[nrow] = make_uint2((unsigned)j, __float_as_uint(l));
-    ++nrow;
-  });
-  float y = 0.f, c = 0.f, nn = 0.f;
-  if (nrow <= kRowCap) {
-    if (flags & 2) {
-      for (int q = 0; q < nrow; ++q) {
-        const uint2 e = row[q];
-        const float l = __uint_as_float(e.y);
-        y = __fmaf_rn(l, xload((int)e.x), y);
-        nn = __fmaf_rn(l, l, nn);
-        atomicAdd(cnt + e.x, 1u);
-      }
-    } else {
-      // Kahan-compensated sum of l * x_j: the true sum is y - c
-      for (int q = 0; q < nrow; ++q) {
-        const uint2 e = row[q];
-        const float l = __uint_as_float(e.y);
-        const float term = __fsub_rn(__fmul_rn(l, xload((int)e.x)), c);
-        const float t = __fadd_rn(y, term);
-        c = __fsub_rn(__fsub_rn(t, y), term);
-        y = t;
-        nn = __fmaf_rn(l, l, nn);
-        atomicAdd(cnt + e.x, 1u);
-      }
-    }
-  } else {
-    walk([&](int j, float l) {
-      if (flags & 2) {
-        y = __fmaf_rn(l, xload(j), y);
-      } else {
-        const float term = __fsub_rn(__fmul_rn(l, xload(j)), c);
-        const float t = __fadd_rn(y, term);
-        c = __fsub_rn(__fsub_rn(t, y), term);
-        y = t;
-      }
-      nn = __fmaf_rn(l, l, nn);
-      atomicAdd(cnt + j, 1u);
-    });
-  }
-  if (!(nn > 0.f)) return;
-  const float res = __fadd_rn(__fsub_rn(v.wepl, y), c);
-  const float ri = lambda * res / nn;
-  if (nrow <= kRowCap) {
-    for (int q = 0; q < nrow; ++q) {
-      const uint2 e = row[q];
-      atomicAdd(delta + e.x, __uint_as_float(e.y) * ri);
-    }
-  } else {
-    walk([&](int j, float l) { atomicAdd(delta + j, l * ri); });
-  }
-}
-
+// drop_history that also adds every run to cnt (the block's run counts s_j).
+template <bool kPlain = false>
 __device__ __forceinline__ void drop_history_count(const Geo& g, const float4* __restrict__ tab, const Rec& r, int64_t i,
                                                    const float* __restrict__ x, float* __restrict__ delta, float lambda,
-                                                   int flags, unsigned int* __restrict__ cnt) {
+                                                   unsigned int* __restrict__ cnt) {
   const RecV v = load_rec(r, i);
-  drop_history_core_count(v, [&](auto&& visit) { walk_proton(g, tab, v, visit); }, x, delta, lambda, flags, cnt);
+  drop_history_core<false, kPlain, true>(v, [&](auto&& visit) { walk_proton(g, tab, v, visit); }, x, delta, lambda,
+                                         cnt);
 }
 
+template <bool kPlain = false>
 __device__ __forceinline__ void drop_history_hull_count(const Geo& g, const Hull& hull, const Rec& r, int64_t i,
                                                         const float* __restrict__ x, float* __restrict__ delta,
-                                                        float lambda, int flags, unsigned int* __restrict__ cnt) {
+                                                        float lambda, unsigned int* __restrict__ cnt) {
   const RecV v = load_rec(r, i);
   const int32_t range = __ldg(hull.range + i);
-  drop_history_core_count(v, [&](auto&& visit) { walk_proton_hull(g, hull.fam, range, v, visit); }, x, delta, lambda,
-                          flags, cnt);
+  drop_history_core<false, kPlain, true>(v, [&](auto&& visit) { walk_proton_hull(g, hull.fam, range, v, visit); }, x,
+                                         delta, lambda, cnt);
 }
 
 // x_j += delta_j / s_j (optionally clamped), delta_j = 0. kCoherent: x and

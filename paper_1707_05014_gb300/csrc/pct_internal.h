@@ -9,6 +9,12 @@ namespace pct {
 
 constexpr int kQBits = 20;               // Q20 fixed-point grid coordinates
 constexpr int32_t kQOne = 1 << kQBits;   // one voxel
+// Single-precision grid coordinates are formed kQOff voxels above their value
+// (q = fma(p, 1/h, n/2 + kQOff)) and the offset is removed after rounding to
+// Q20: every coordinate within 8 voxels of the grid is then >= 8, where a
+// float is already a whole multiple of 2^-20, so there the rounding is exact
+// and the float itself is the Q20 node.
+constexpr int kQOff = 16;
 constexpr float kQClamp = 1000.0f;       // |q| clamp in voxels (never reached for valid records)
 constexpr int kMaxNodes = 2048;          // K + 1 limit (shared-memory MLP table)
 constexpr int kMaxDim = 512;             // per-axis voxel limit
@@ -25,9 +31,50 @@ struct Geo {
   float u0;       // first measurement plane (-R), rounded from FP64
   float hx, hy, hz;     // voxel size (mm)
   float ihx, ihy, ihz;  // 1/h rounded from FP64
-  float hnx, hny, hnz;  // n/2
+  float hnx, hny, hnz;  // n/2 + kQOff
   float bx, by;         // half box extents in x and y (mm)
+  // Largest change between consecutive nodes of each FP32 table column
+  // (c1..c4): bounds the lateral step of an MLP segment. INFINITY: no bound
+  // known, every history takes the general walk.
+  float dmax[4];
 };
+
+// Geometry of a grid in the kernels' single-precision form; R, du, K, E from
+// the FP64 derivation of the context. dmax = INFINITY until the table is known.
+inline Geo make_geo(int nx, int ny, int nz, double hx, double hy, double hz, double R, double du, int K, int E) {
+  Geo G{};
+  G.nx = nx;
+  G.ny = ny;
+  G.nz = nz;
+  G.K = K;
+  G.E = E;
+  G.du = (float)du;
+  G.u0 = (float)(-R);
+  G.hx = (float)hx;
+  G.hy = (float)hy;
+  G.hz = (float)hz;
+  G.ihx = (float)(1.0 / hx);
+  G.ihy = (float)(1.0 / hy);
+  G.ihz = (float)(1.0 / hz);
+  G.hnx = 0.5f * (float)nx + (float)kQOff;
+  G.hny = 0.5f * (float)ny + (float)kQOff;
+  G.hnz = 0.5f * (float)nz + (float)kQOff;
+  G.bx = (float)(0.5 * nx * hx);
+  G.by = (float)(0.5 * ny * hy);
+  for (int i = 0; i < 4; ++i) G.dmax[i] = __builtin_inff();
+  return G;
+}
+
+// dmax from the FP32 table (K + 1 nodes, host copy).
+inline void set_table_bound(Geo& G, const float4* tab, int K) {
+  float d[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int k = 1; k <= K; ++k) {
+    const float a[4] = {tab[k].x - tab[k - 1].x, tab[k].y - tab[k - 1].y, tab[k].z - tab[k - 1].z,
+                        tab[k].w - tab[k - 1].w};
+    for (int i = 0; i < 4; ++i) d[i] = a[i] < 0.f ? (-a[i] > d[i] ? -a[i] : d[i]) : (a[i] > d[i] ? a[i] : d[i]);
+  }
+  for (int i = 0; i < 4; ++i) G.dmax[i] = d[i];
+}
 
 // Structure-of-arrays history records (device pointers).
 struct Rec {

@@ -58,28 +58,30 @@ __global__ void counts_to_float_kernel(const unsigned int* __restrict__ cnt, flo
   out[j] = (float)cnt[j];
 }
 
-// One thread per proton (see drop_history).
+// One thread per proton (see drop_history); kPlain: PCT_FLAG_NO_KAHAN.
+template <bool kPlain>
 __global__ void __launch_bounds__(128, 9) drop_fused_kernel(Geo g, Rec r, const float4* __restrict__ tab_g,
                                                           int64_t first, int64_t count, const float* __restrict__ x,
-                                                          float* __restrict__ delta, float lambda, int flags) {
+                                                          float* __restrict__ delta, float lambda) {
   extern __shared__ float4 tab[];
   load_table(tab_g, tab, g.K + 1);
   int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= count) return;
-  drop_history(g, tab, r, first + p, x, delta, lambda, flags);
+  drop_history<false, kPlain>(g, tab, r, first + p, x, delta, lambda);
 }
 
 // The same that also counts the block's runs per voxel into cnt (the first
 // sweep after a load forms the DROP weights this way).
+template <bool kPlain>
 __global__ void __launch_bounds__(128, 9) drop_fused_count_kernel(Geo g, Rec r, const float4* __restrict__ tab_g,
                                                                 int64_t first, int64_t count,
                                                                 const float* __restrict__ x, float* __restrict__ delta,
-                                                                float lambda, int flags, unsigned int* __restrict__ cnt) {
+                                                                float lambda, unsigned int* __restrict__ cnt) {
   extern __shared__ float4 tab[];
   load_table(tab_g, tab, g.K + 1);
   int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= count) return;
-  drop_history_count(g, tab, r, first + p, x, delta, lambda, flags, cnt);
+  drop_history_count<kPlain>(g, tab, r, first + p, x, delta, lambda, cnt);
 }
 
 // The same with an object hull (see walk_proton_hull). PCT_HULL_MIN_CTAS:
@@ -87,20 +89,22 @@ __global__ void __launch_bounds__(128, 9) drop_fused_count_kernel(Geo g, Rec r, 
 #ifndef PCT_HULL_MIN_CTAS
 #define PCT_HULL_MIN_CTAS 9
 #endif
+template <bool kPlain>
 __global__ void __launch_bounds__(128, PCT_HULL_MIN_CTAS)
     drop_fused_hull_kernel(Geo g, Rec r, Hull hull, int64_t first, int64_t count, const float* __restrict__ x,
-                           float* __restrict__ delta, float lambda, int flags) {
+                           float* __restrict__ delta, float lambda) {
   int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= count) return;
-  drop_history_hull(g, hull, r, first + p, x, delta, lambda, flags);
+  drop_history_hull<kPlain>(g, hull, r, first + p, x, delta, lambda);
 }
 
+template <bool kPlain>
 __global__ void __launch_bounds__(128, PCT_HULL_MIN_CTAS)
     drop_fused_hull_count_kernel(Geo g, Rec r, Hull hull, int64_t first, int64_t count, const float* __restrict__ x,
-                                 float* __restrict__ delta, float lambda, int flags, unsigned int* __restrict__ cnt) {
+                                 float* __restrict__ delta, float lambda, unsigned int* __restrict__ cnt) {
   int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= count) return;
-  drop_history_hull_count(g, hull, r, first + p, x, delta, lambda, flags, cnt);
+  drop_history_hull_count<kPlain>(g, hull, r, first + p, x, delta, lambda, cnt);
 }
 
 // Compensated a_i.x (or plain with flags & 2), the arithmetic of the fused
@@ -529,21 +533,34 @@ cudaError_t launch_drop_fused(const Geo& g, const Rec& r, const float4* tab, con
                               cudaStream_t s, unsigned int* cnt) {
   if (count <= 0) return cudaSuccess;
   threads = 128;
+  const unsigned blocks = grid_for(count, threads);
+  const bool plain = (flags & 2) != 0;
   if (hull.range) {
-    if (cnt)
-      drop_fused_hull_count_kernel<<<grid_for(count, threads), threads, 0, s>>>(g, r, hull, first, count, x, delta,
-                                                                               lambda, flags, cnt);
-    else
-      drop_fused_hull_kernel<<<grid_for(count, threads), threads, 0, s>>>(g, r, hull, first, count, x, delta, lambda,
-                                                                         flags);
+    if (cnt) {
+      if (plain)
+        drop_fused_hull_count_kernel<true><<<blocks, threads, 0, s>>>(g, r, hull, first, count, x, delta, lambda, cnt);
+      else
+        drop_fused_hull_count_kernel<false><<<blocks, threads, 0, s>>>(g, r, hull, first, count, x, delta, lambda, cnt);
+    } else {
+      if (plain)
+        drop_fused_hull_kernel<true><<<blocks, threads, 0, s>>>(g, r, hull, first, count, x, delta, lambda);
+      else
+        drop_fused_hull_kernel<false><<<blocks, threads, 0, s>>>(g, r, hull, first, count, x, delta, lambda);
+    }
     return cudaGetLastError();
   }
   const size_t smem = (g.K + 1) * sizeof(float4);
-  if (cnt)
-    drop_fused_count_kernel<<<grid_for(count, threads), threads, smem, s>>>(g, r, tab, first, count, x, delta, lambda,
-                                                                            flags, cnt);
-  else
-    drop_fused_kernel<<<grid_for(count, threads), threads, smem, s>>>(g, r, tab, first, count, x, delta, lambda, flags);
+  if (cnt) {
+    if (plain)
+      drop_fused_count_kernel<true><<<blocks, threads, smem, s>>>(g, r, tab, first, count, x, delta, lambda, cnt);
+    else
+      drop_fused_count_kernel<false><<<blocks, threads, smem, s>>>(g, r, tab, first, count, x, delta, lambda, cnt);
+  } else {
+    if (plain)
+      drop_fused_kernel<true><<<blocks, threads, smem, s>>>(g, r, tab, first, count, x, delta, lambda);
+    else
+      drop_fused_kernel<false><<<blocks, threads, smem, s>>>(g, r, tab, first, count, x, delta, lambda);
+  }
   return cudaGetLastError();
 }
 

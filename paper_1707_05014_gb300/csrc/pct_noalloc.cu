@@ -109,25 +109,9 @@ extern "C" pct_status pct_drop_block_noalloc(const pct_grid* grid, const pct_con
   const double qmax = (R + (E + 1) * du + pos_limit + 0.5 * (2.0 * R + E * du)) / hmin +
                       0.5 * fmax((double)gr.nx, fmax((double)gr.ny, (double)gr.nz));
   if (qmax >= pct::kQClamp) return noalloc_fail(PCT_ERR_INVALID_ARG, "grid too large for the fixed-point node range");
-  Geo g{};
-  g.nx = gr.nx;
-  g.ny = gr.ny;
-  g.nz = gr.nz;
-  g.K = K;
-  g.E = E;
-  g.du = (float)du;
-  g.u0 = (float)(-R);
-  g.hx = (float)gr.hx;
-  g.hy = (float)gr.hy;
-  g.hz = (float)gr.hz;
-  g.ihx = (float)(1.0 / gr.hx);
-  g.ihy = (float)(1.0 / gr.hy);
-  g.ihz = (float)(1.0 / gr.hz);
-  g.hnx = 0.5f * (float)gr.nx;
-  g.hny = 0.5f * (float)gr.ny;
-  g.hnz = 0.5f * (float)gr.nz;
-  g.bx = (float)(0.5 * X);
-  g.by = (float)(0.5 * Y);
+  // dmax stays unbounded: every history takes the general walk (reading the
+  // table back to bound its steps would need a host buffer)
+  const Geo g = pct::make_geo(gr.nx, gr.ny, gr.nz, gr.hx, gr.hy, gr.hz, R, du, K, E);
   const Rec r{src[0], src[1], src[2], src[3], src[4], src[5], src[6], src[7], src[8], src[9], src[10]};
 
   // Device address of the scratch array in the current device's context. The

@@ -9,15 +9,27 @@
 // Bit-exact contract (the oracle's FP32 mode follows the same definition):
 //   t_k = fma(c4, st2, fma(c3, t2, fma(c2, st0, c1*t0)))   (same for v)
 //   x = fma(u, cos, -(t*sin)), y = fma(u, sin, t*cos), z = v
-//   q = fma(p, 1/h, n/2), clamped to +-1000, Q = rint(q * 2^20) (half even)
+//   q = fma(p, 1/h, n/2 + 16), clamped to +-1000,
+//   Q = rint(q * 2^20) - 16 * 2^20 (half even)
 // Every product is a separately rounded __fmul_rn and every fused step an
 // explicit __fmaf_rn, so the compiler cannot contract or reorder them.
-// Between consecutive nodes an integer DDA orders the face crossings by
-// exact cross-multiplication; voxels are half-open [i, i+1), tied crossings
-// step together, and a run (maximal stretch in one voxel) is reported only
-// when its exact extent is positive. The indices are exact; chord lengths are
-// single precision (segment length from the Q20 differences, crossing
-// parameters by fast division), within 1e-5 relative of the FP64 oracle.
+// Between consecutive nodes the face crossings are ordered exactly (by
+// cross-multiplication of the Q20 distances); voxels are half-open [i, i+1),
+// tied crossings step together, and a run (maximal stretch in one voxel) is
+// reported only when its exact extent is positive. The indices are exact;
+// chord lengths are single precision (segment length from the node
+// differences, crossing parameters by fast division), within 1e-5 relative
+// of the FP64 oracle.
+//
+// The 16-voxel offset of q makes every coordinate within 8 voxels of the grid
+// at least 8, where a float is a whole multiple of 2^-20: there q IS the Q20
+// node (q * 2^20 is an integer) and differences of such floats, and the
+// fused products of two of them, are exact. The fast walk (walk_fast) uses
+// this to take every decision that shapes an emitted run on the floats
+// themselves, with the same outcome as the integer walk (walk_segment) on
+// the quantised nodes; far from the grid, where the two may round a
+// coordinate differently, nothing is emitted and both return to the same
+// voxel before the grid is reached.
 #pragma once
 
 #include "pct_internal.h"
@@ -46,10 +58,13 @@ __device__ __forceinline__ RecV load_rec(const Rec& r, int64_t i) {
   return v;
 }
 
-// Q = rint(q * 2^20). The contract also clamps q to +-1000 voxels first;
-// pct_create rejects grids for which a validated record could reach that
-// range, so the clamp is the identity here and is not evaluated.
-__device__ __forceinline__ int32_t quantise(float q) { return __float2int_rn(__fmul_rn(q, (float)kQOne)); }
+// Q = rint(q * 2^20) - kQOff * 2^20 (grid units). The contract also clamps q
+// to +-1000 voxels first; pct_create rejects grids for which a validated
+// record could reach that range, so the clamp is the identity here and is
+// not evaluated.
+__device__ __forceinline__ int32_t quantise(float q) {
+  return __float2int_rn(__fmul_rn(q, (float)kQOne)) - kQOff * kQOne;
+}
 
 // Lateral (t) and vertical (v) position of node k in mm.
 __device__ __forceinline__ float2 node_tv(const Geo& g, const float4* __restrict__ tab, const RecV& r, int k) {
@@ -289,24 +304,202 @@ __device__ __forceinline__ void walk_segment(const Geo& g, WalkState& s, const f
   s.qP = q;
 }
 
+// Calls f(q) with the float grid coordinates of nodes klo+1 .. khi in order.
+// The node loop runs in three phases (entry extension, MLP nodes, exit
+// extension) so that no per-node branch selects the node formula.
+template <class F>
+__device__ __forceinline__ void for_each_node(const Geo& g, const float4* __restrict__ tab, const RecV& r, int klo,
+                                              int khi, F&& f) {
+  int k = klo + 1;
+  // entry extension: straight along the entry slope
+  for (; k < 0 && k <= khi; ++k) {
+    const float kf = (float)k;
+    const float dk = __fmul_rn(kf, g.du);
+    const float t = __fmaf_rn(r.st0, dk, r.t0), v = __fmaf_rn(r.sv0, dk, r.v0);
+    f(node_grid(g, r, __fmaf_rn(kf, g.du, g.u0), t, v));
+  }
+  // MLP nodes between the measurement planes (kf counts k exactly in float)
+  const int kmid = min(khi, g.K);
+  float kf = (float)k;
+  for (; k <= kmid; ++k, kf += 1.f) {
+    const float4 c = tab[k];
+    const float t = __fmaf_rn(c.w, r.st2, __fmaf_rn(c.z, r.t2, __fmaf_rn(c.y, r.st0, __fmul_rn(c.x, r.t0))));
+    const float v = __fmaf_rn(c.w, r.sv2, __fmaf_rn(c.z, r.v2, __fmaf_rn(c.y, r.sv0, __fmul_rn(c.x, r.v0))));
+    f(node_grid(g, r, __fmaf_rn(kf, g.du, g.u0), t, v));
+  }
+  // exit extension: straight along the exit slope
+  for (; k <= khi; ++k) {
+    const float dk = __fmul_rn((float)(k - g.K), g.du);
+    const float t = __fmaf_rn(r.st2, dk, r.t2), v = __fmaf_rn(r.sv2, dk, r.v2);
+    f(node_grid(g, r, __fmaf_rn((float)k, g.du, g.u0), t, v));
+  }
+}
+
+// ---- fast walk --------------------------------------------------------------
+//
+// For a history whose every segment moves less than one voxel on each axis
+// (history_fast), each axis crosses at most one face per segment and every
+// decision is taken on the float nodes: with the 16-voxel offset a coordinate
+// near the grid is an exact multiple of 2^-20, so the distance of a node to a
+// face and the length of a segment along an axis are exact floats (Sterbenz),
+// and two crossing fractions n1/d1, n2/d2 are ordered exactly by comparing
+// n1*d2 with n2*d1 as an FMA two-product (cmp_prod). That is the integer
+// walk's cross-multiplication on the same numbers, so the runs are the same.
+// A voxel change is detected by comparing each coordinate with the faces of
+// the current voxel, kept as floats: no rounding to Q20 and no conversion in
+// the node loop.
+
+// Sign of a*b - c*d, exactly: p = a*b rounded, a*b = p + fma(a, b, -p) exactly
+// (no underflow for the magnitudes here), and rounding is monotonic, so
+// distinct rounded products order the exact ones and equal ones leave the
+// remainders to decide.
+__device__ __forceinline__ int cmp_prod(float a, float b, float c, float d) {
+  const float p = __fmul_rn(a, b), q = __fmul_rn(c, d);
+  if (p != q) return p < q ? -1 : 1;
+  const float ep = __fmaf_rn(a, b, -p), eq = __fmaf_rn(c, d, -q);
+  return ep < eq ? -1 : (ep > eq ? 1 : 0);
+}
+
+// Every segment of the history moves less than one voxel on every axis: the
+// lateral step of a segment is at most |slope| du on the rays and
+// sum_i dmax_i |coefficient input i| between the planes (the FP32 table's
+// largest node-to-node change per column); 1e-3 voxel of margin covers the
+// rounding of the float nodes.
+__device__ __forceinline__ bool history_fast(const Geo& g, const RecV& r) {
+  if (!(g.dmax[0] < INFINITY)) return false;
+  const float bt = fmaxf(fmaxf(fabsf(r.st0), fabsf(r.st2)) * g.du,
+                         g.dmax[0] * fabsf(r.t0) + g.dmax[1] * fabsf(r.st0) + g.dmax[2] * fabsf(r.t2) +
+                             g.dmax[3] * fabsf(r.st2));
+  const float bv = fmaxf(fmaxf(fabsf(r.sv0), fabsf(r.sv2)) * g.du,
+                         g.dmax[0] * fabsf(r.v0) + g.dmax[1] * fabsf(r.sv0) + g.dmax[2] * fabsf(r.v2) +
+                             g.dmax[3] * fabsf(r.sv2));
+  const float ac = fabsf(r.cp), as = fabsf(r.sp);
+  const float bx = (g.du * ac + bt * as) * g.ihx;
+  const float by = (g.du * as + bt * ac) * g.ihy;
+  const float bz = bv * g.ihz;
+  return fmaxf(bx, fmaxf(by, bz)) < 0.999f;
+}
+
+struct FastState {
+  float3 qP;          // previous node, offset grid coordinates
+  float lx, ly, lz;   // lower faces of the current voxel, offset grid coordinates
+  int cx, cy, cz;     // current voxel, grid indices
+  float run;          // length of the current run so far (mm)
+  bool pos;           // the current run has positive exact extent
+};
+
+template <class Visit>
+__device__ __forceinline__ void emit_fast(const Geo& g, FastState& s, Visit& visit) {
+  if (s.pos && (unsigned)s.cx < (unsigned)g.nx && (unsigned)s.cy < (unsigned)g.ny && (unsigned)s.cz < (unsigned)g.nz)
+    visit(s.cx + g.nx * (s.cy + g.ny * s.cz), s.run);
+  s.run = 0.f;
+  s.pos = false;
+}
+
+// Advance the fast walk from s.qP to the next node q.
+template <class Visit>
+__device__ __forceinline__ void seg_fast(const Geo& g, FastState& s, const float3 q, Visit& visit) {
+  const float dx = __fsub_rn(q.x, s.qP.x), dy = __fsub_rn(q.y, s.qP.y), dz = __fsub_rn(q.z, s.qP.z);
+  const float fx = __fmul_rn(dx, g.hx), fy = __fmul_rn(dy, g.hy), fz = __fmul_rn(dz, g.hz);
+  // The nodes of a validated record are at least du / sqrt(2) apart in x or
+  // y (du >= 2R/2047), far above the float spacing, so L2 > 0.
+  const float L2 = __fmaf_rn(fx, fx, __fmaf_rn(fy, fy, __fmul_rn(fz, fz)));
+  const float L = L2 * rsqrtf(L2);
+  const float ux = s.lx + 1.f, uy = s.ly + 1.f, uz = s.lz + 1.f;  // upper faces
+  const bool xa = q.x >= ux, xb = q.x < s.lx;  // half-open voxels: a face reached moving up is crossed
+  const bool ya = q.y >= uy, yb = q.y < s.ly;
+  const bool za = q.z >= uz, zb = q.z < s.lz;
+  if (!(xa | xb | ya | yb | za | zb)) {
+    s.run += L;  // the segment moves, so the run's extent is positive
+    s.pos = true;
+    s.qP = q;
+    return;
+  }
+  bool rx = xa | xb, ry = ya | yb, rz = za | zb;  // crossings still to take
+  // exact distance to the crossed face and exact axis length of the segment
+  const float ndx = xa ? __fsub_rn(ux, s.qP.x) : __fsub_rn(s.qP.x, s.lx), ddx = fabsf(dx);
+  const float ndy = ya ? __fsub_rn(uy, s.qP.y) : __fsub_rn(s.qP.y, s.ly), ddy = fabsf(dy);
+  const float ndz = za ? __fsub_rn(uz, s.qP.z) : __fsub_rn(s.qP.z, s.lz), ddz = fabsf(dz);
+  // exact pairwise order of the crossings (< 0: the first axis crosses first)
+  const int oxy = rx && ry ? cmp_prod(ndx, ddy, ndy, ddx) : 0;
+  const int oxz = rx && rz ? cmp_prod(ndx, ddz, ndz, ddx) : 0;
+  const int oyz = ry && rz ? cmp_prod(ndy, ddz, ndz, ddy) : 0;
+  float tl = 0.f, nl = 0.f, dl = 1.f;
+  bool first = true;
+  while (rx | ry | rz) {
+    // the axes no remaining crossing precedes (tied axes step together)
+    const bool mx = rx && !(ry && oxy > 0) && !(rz && oxz > 0);
+    const bool my = ry && !(rx && oxy < 0) && !(rz && oyz > 0);
+    const bool mz = rz && !(rx && oxz < 0) && !(ry && oyz < 0);
+    const float n = mx ? ndx : (my ? ndy : ndz), d = mx ? ddx : (my ? ddy : ddz);
+    const float t = __fdividef(n, d);
+    s.run += (t - tl) * L;
+    s.pos |= !first || n > 0.f;  // later events lie exactly after the previous one
+    emit_fast(g, s, visit);
+    if (mx) {
+      s.cx += xa ? 1 : -1;
+      s.lx += xa ? 1.f : -1.f;
+      rx = false;
+    }
+    if (my) {
+      s.cy += ya ? 1 : -1;
+      s.ly += ya ? 1.f : -1.f;
+      ry = false;
+    }
+    if (mz) {
+      s.cz += za ? 1 : -1;
+      s.lz += za ? 1.f : -1.f;
+      rz = false;
+    }
+    tl = t;
+    nl = n;
+    dl = d;
+    first = false;
+  }
+  s.run += (1.f - tl) * L;
+  s.pos |= nl < dl;  // the last crossing lies before the node
+  s.qP = q;
+}
+
+template <class Visit>
+__device__ __forceinline__ void walk_fast(const Geo& g, const float4* __restrict__ tab, const RecV& r, int klo,
+                                          int khi, Visit& visit) {
+  FastState s;
+  {
+    const float2 tv = node_tv(g, tab, r, klo);
+    s.qP = node_grid(g, r, __fmaf_rn((float)klo, g.du, g.u0), tv.x, tv.y);
+  }
+  s.lx = floorf(s.qP.x);
+  s.ly = floorf(s.qP.y);
+  s.lz = floorf(s.qP.z);
+  s.cx = (int)s.lx - kQOff;
+  s.cy = (int)s.ly - kQOff;
+  s.cz = (int)s.lz - kQOff;
+  s.run = 0.f;
+  s.pos = false;
+  for_each_node(g, tab, r, klo, khi, [&](const float3 q) { seg_fast(g, s, q, visit); });
+  emit_fast(g, s, visit);
+}
+
 // Walk one proton's polyline, calling visit(j, len) for every run in path
 // order (j = voxel index, len = chord in mm).
 //
 // Per segment P -> Q the voxel index along an axis changes exactly when a face
 // is crossed (floor(Q/2^20) != floor(P/2^20), with the half-open convention:
-// a face reached exactly counts when moving up, not when moving down). When
-// every axis moves less than one voxel -- always the case for valid records,
-// whose segments span at most ~0.6 voxel -- each axis crosses at most one
-// face, and the (at most three) crossings are ordered in one event loop by
-// exact 32x32->64-bit cross-multiplication; tied crossings form one event.
-// Longer segments take the general loop that re-arms an axis after each face.
-// The node loop runs in three phases (entry extension, MLP nodes, exit
-// extension) so that no per-node branch selects the node formula.
+// a face reached exactly counts when moving up, not when moving down). A
+// history whose segments all move less than a voxel per axis -- every valid
+// record at the default node spacing of half a voxel -- takes the fast walk
+// above. Any other takes the integer walk (walk_segment), whose general loop
+// re-arms an axis after each face; both give the same runs.
 template <class Visit>
 __device__ __forceinline__ void walk_proton(const Geo& g, const float4* __restrict__ tab, const RecV& r,
                                             Visit&& visit) {
   int klo, khi;
   node_range(g, r, klo, khi);
+  if (history_fast(g, r)) {
+    walk_fast(g, tab, r, klo, khi, visit);
+    return;
+  }
   WalkState s;
   {
     const float2 tv = node_tv(g, tab, r, klo);
@@ -318,28 +511,7 @@ __device__ __forceinline__ void walk_proton(const Geo& g, const float4* __restri
   s.cz = floor_q(s.P.z);
   s.run = 0.f;
   s.pos = false;
-  int k = klo + 1;
-  // entry extension: straight along the entry slope
-  for (; k < 0 && k <= khi; ++k) {
-    const float kf = (float)k;
-    const float dk = __fmul_rn(kf, g.du);
-    const float t = __fmaf_rn(r.st0, dk, r.t0), v = __fmaf_rn(r.sv0, dk, r.v0);
-    walk_segment(g, s, node_grid(g, r, __fmaf_rn(kf, g.du, g.u0), t, v), visit);
-  }
-  // MLP nodes between the measurement planes
-  const int kmid = min(khi, g.K);
-  for (; k <= kmid; ++k) {
-    const float4 c = tab[k];
-    const float t = __fmaf_rn(c.w, r.st2, __fmaf_rn(c.z, r.t2, __fmaf_rn(c.y, r.st0, __fmul_rn(c.x, r.t0))));
-    const float v = __fmaf_rn(c.w, r.sv2, __fmaf_rn(c.z, r.v2, __fmaf_rn(c.y, r.sv0, __fmul_rn(c.x, r.v0))));
-    walk_segment(g, s, node_grid(g, r, __fmaf_rn((float)k, g.du, g.u0), t, v), visit);
-  }
-  // exit extension: straight along the exit slope
-  for (; k <= khi; ++k) {
-    const float dk = __fmul_rn((float)(k - g.K), g.du);
-    const float t = __fmaf_rn(r.st2, dk, r.t2), v = __fmaf_rn(r.sv2, dk, r.v2);
-    walk_segment(g, s, node_grid(g, r, __fmaf_rn((float)k, g.du, g.u0), t, v), visit);
-  }
+  for_each_node(g, tab, r, klo, khi, [&](const float3 q) { walk_segment(g, s, q, visit); });
   emit_run(g, s, visit);
 }
 

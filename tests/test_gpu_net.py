@@ -8,10 +8,15 @@ sides differ by FP32 summation order, plus the rare stored value that lies
 within that summation difference of a BF16 rounding boundary and so rounds to
 the neighbouring BF16 value: a change of at most one BF16 ulp, 2^-7 of the
 value. A sum of terms each of which changes by at most a relative e changes by
-at most e times the sum of the terms' magnitudes. Every output and every
-gradient element is held to BF16_BOUND = 2^-6 (two ulps: both factors of a
-product may have moved) times that magnitude sum, which the reference computes
-per element (forward_scale; loss_and_grads(scales=True)), plus FP32 rounding."""
+at most e times the sum of the terms' magnitudes. Every output element is held
+to BF16_BOUND = 2^-6 (two ulps: both factors of a product may have moved)
+times that magnitude sum (forward_scale), plus FP32 rounding. A gradient
+element of layer L is the end of a chain of nl - L stored gradients, each of
+which may have moved by one ulp of its own magnitude chain, plus the stored
+activation it multiplies: it is held to 2^-7 (nl - L + 1) times its magnitude
+chain (loss_and_grads(scales=True)). The loss gradient sign(x0 - target)/n is
+itself a decision: the test's targets sit at least 0.05 from the reference's
+x0, far outside the forward bound, so that both sides take the same sign."""
 import numpy as np
 import pytest
 
@@ -85,12 +90,17 @@ def test_forward_matches_reference(P, seed):
     assert _rel(f_gpu, (ref64 - x1).ravel()) < 5e-2
 
 
-def test_gradients_match_reference(P):
+@pytest.mark.parametrize("seed", [2, 5])
+def test_gradients_match_reference(P, seed):
     import torch
 
-    x1, target, p = _data(2)
+    x1, _, p = _data(seed)
     x1 = x1.astype(np.float32).astype(np.float64)
-    target = target.astype(np.float32).astype(np.float64)
+    # targets away from the reference output: the loss gradient's sign is the same on both sides
+    rng = np.random.Generator(np.random.Philox(100 + seed))
+    x0_ref, _ = U.forward(p, x1, bf16=True)
+    sgn = np.where(rng.random(SHAPE) < 0.5, -1.0, 1.0)
+    target = (x0_ref + sgn * (0.05 + 0.2 * rng.random(SHAPE))).astype(np.float32).astype(np.float64)
     with P.Net(*SHAPE) as net:
         net.set_params(p)
         loss, g = net.gradients(torch.tensor(x1.ravel(), dtype=torch.float32, device="cuda"),
@@ -98,13 +108,16 @@ def test_gradients_match_reference(P):
     rloss, rg, sg = U.loss_and_grads(p, x1, target, bf16=True, scales=True)
     assert abs(loss - rloss) < 1e-3 * rloss
     off = 0
+    nl = len(U.SPEC)
+    worst = []
     for li, (ci, co, _, _) in enumerate(U.SPEC):
         n = 27 * ci * co + co
         a, b, s = g[off:off + n].astype(np.float64), rg[off:off + n], sg[off:off + n]
         # every weight and bias gradient of the layer, element by element
-        bad = np.abs(a - b) > (BF16_BOUND + FP32_FLOOR) * s + 1e-30
-        assert not bad.any(), (li, int(bad.sum()), float(np.max(np.abs(a - b) / np.maximum(s, 1e-30))))
+        bound = (2.0**-7 * (nl - li + 1) + FP32_FLOOR) * s + 1e-30
+        worst.append(float(np.max(np.abs(a - b) / bound)))
         off += n
+    assert max(worst) <= 1.0, worst
 
 
 def test_training_lowers_the_loss(P):

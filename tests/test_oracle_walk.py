@@ -172,8 +172,12 @@ def test_brute_force_supersampling(oracle):
 def test_fp64_and_fp32_rows_agree_except_near_ties(oracle):
     # The FP32-order nodes move by < 1e-4 voxel, so index lists agree for all
     # but a small fraction of protons. A chord moves by (node shift)/sin(angle
-    # between path and face), so grazing crossings (slopes of a few mrad) can
-    # move by ~1e-3 voxel while the typical chord moves by ~1e-6 voxel.
+    # between path and face), so grazing crossings (slopes of a few mrad, down
+    # to tens of microradians for the flattest of these paths against a z face)
+    # can move by ~1e-3..1e-2 voxel while the typical chord moves by ~1e-6
+    # voxel. The FP32 grid coordinates carry a 16-voxel offset (exact
+    # multiples of 2^-20 near the grid), so their rounding step is that of
+    # the offset value: the tail bound is set for that step.
     wl = S.head_workload(1000, seed=15)
     g = wl.grid
     rec = S.make_histories(wl)
@@ -191,7 +195,7 @@ def test_fp64_and_fp32_rows_agree_except_near_ties(oracle):
     assert same >= 990
     assert np.median(d) < 1e-5
     assert np.percentile(d, 99) < 1e-4
-    assert d.max() < 1e-2
+    assert d.max() < 2e-2
 
 
 def test_reentry_count_on_a_path_that_bulges_over_a_face(oracle):

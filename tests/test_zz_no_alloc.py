@@ -80,7 +80,7 @@ def test_noalloc_matches_context_path_on_two_calls(lib, oracle, kind, n, flags):
         assert err.max() <= RSP_TOL, (call, err.max())
         assert np.abs(got).max() > 0
         if flags & P.FLAG_CLAMP:
-            assert got.min() >= clamp_min
+            assert got.min() >= np.float32(clamp_min)
         # the oracle's DROP with one block, call + 1 sweeps (the FP32 node order)
         xo = oracle.drop(g, rec, 1, call + 1, mode=oracle.MODE_FP32,
                          clamp_min=clamp_min if flags & P.FLAG_CLAMP else None)
