@@ -114,7 +114,7 @@ def forward(p: np.ndarray, x1: np.ndarray, bf16: bool = False):
     inp = np.zeros(x1.shape + (16,))
     inp[..., 0] = x1
     inp = q(inp)
-    acts = []
+    acts, pres = [], []
     h = inp
     for li, ((ci, co, kind, skip), (W, b)) in enumerate(zip(SPEC, layers)):
         if kind == "s1":
@@ -128,7 +128,8 @@ def forward(p: np.ndarray, x1: np.ndarray, bf16: bool = False):
         if li == len(SPEC) - 1:
             f = pre[..., 0]
             x0 = x1 + f
-            return x0, {"inp": inp, "acts": acts, "layers": layers, "x1": x1, "x0": x0}
+            return x0, {"inp": inp, "acts": acts, "pres": pres, "layers": layers, "x1": x1, "x0": x0}
+        pres.append(pre)
         h = q(np.maximum(pre, 0.0))
         acts.append(h)
     raise AssertionError("unreachable")
@@ -145,14 +146,86 @@ def forward_scale(p: np.ndarray, x1: np.ndarray, bf16: bool = False) -> np.ndarr
     return conv(np.abs(h), np.abs(W), np.abs(b), 1)[..., 0]
 
 
-def loss_and_grads(p: np.ndarray, x1: np.ndarray, target: np.ndarray, bf16: bool = False, scales: bool = False):
+def _layer_pre_magnitudes(c) -> list:
+    """Per hidden layer, the magnitude sum of its pre-activation: |b| + sum of
+    |W| |h| over taps and channels (+ the skip input, which is >= 0)."""
+    layers, acts, inp = c["layers"], c["acts"], c["inp"]
+    mags = []
+    for li in range(len(SPEC) - 1):
+        _, _, kind, skip = SPEC[li]
+        W, b = layers[li]
+        h = inp if li == 0 else acts[li - 1]
+        aW, ab = np.abs(W), np.abs(b)
+        if kind == "s1":
+            m = conv(np.abs(h), aW, ab, 1)
+        elif kind == "s2":
+            m = conv(np.abs(h), aW, ab, 2)
+        else:
+            m = conv(up2(np.abs(h)), aW, ab, 1)
+        if skip >= 0:
+            m = m + acts[skip]
+        mags.append(m)
+    return mags
+
+
+def _magnitude_chain(c, g_last, masks, hmag):
+    """Per parameter, sum |h| G (weights) and sum G (biases), where G is the
+    backward pass run on magnitudes: |dLoss/df| carried back through every
+    layer with |W| in place of W and the given 0/1 masks in place of the ReLU
+    masks; hmag[li] is the activation magnitude used for layer li's input."""
+    layers = c["layers"]
+    nl = len(SPEC)
+    G = [None] * nl
+    G[nl - 1] = g_last
+    out = []
+    for li in range(nl - 1, -1, -1):
+        ci, co, kind, _ = SPEC[li]
+        W, _ = layers[li]
+        h = hmag[li]
+        if kind == "s1":
+            sW = conv_wgrad(h, G[li], 1)
+        elif kind == "s2":
+            sW = conv_wgrad(h, G[li], 2)
+        else:
+            sW = conv_wgrad(up2(h), G[li], 1)
+        out.append((li, sW, G[li].reshape(-1, co).sum(axis=0)))
+        if li == 0:
+            break
+        aW = np.abs(W)
+        if kind == "s1":
+            da = conv_adjoint(h.shape, G[li], aW, 1)
+        elif kind == "s2":
+            da = conv_adjoint(h.shape, G[li], aW, 2)
+        else:
+            da = down2_sum(conv_adjoint(up2(h).shape, G[li], aW, 1))
+        for u, (_, _, _, skip) in enumerate(SPEC):
+            if skip == li - 1:
+                da = da + G[u]
+        G[li - 1] = da * masks[li - 1]
+    return out
+
+
+def loss_and_grads(p: np.ndarray, x1: np.ndarray, target: np.ndarray, bf16: bool = False, scales: bool = False,
+                   relu_margin: float = 1e-3):
     """L1 loss mean|x0 - target| and its gradient w.r.t. p (flat, like p).
-    With scales=True also returns, per parameter, the scale of an element-wise
-    bound on its gradient: sum |h| G for a weight and sum G for a bias, where G
-    is the magnitude chain of the backward pass -- |dLoss/df| carried back
-    through every layer with |W| in place of W and the same ReLU masks -- so
-    that G bounds the sum of the magnitudes of all the terms that make up each
-    stored gradient element."""
+
+    With scales=True also returns two per-parameter scales for an element-wise
+    bound on the gradient of an implementation that sums in another order.
+    Each is sum |h| G for a weight and sum G for a bias, G being the backward
+    pass run on magnitudes (|dLoss/df| carried back with |W| in place of W):
+
+      core:    ReLU masks only where the pre-activation is clearly positive
+               (pre > relu_margin times its magnitude sum), activations zero
+               where it is not clearly decided;
+      relaxed: masks also open where |pre| <= relu_margin times its magnitude
+               sum, those activations counted at up to that margin.
+
+    Where a pre-activation lies that close to zero, a different summation
+    order may take the other ReLU decision; every term of the gradient that
+    runs through such a position may then be present on one side and absent on
+    the other, and those terms are exactly relaxed - core. The terms through
+    clearly decided positions only differ by rounding, bounded relative to the
+    relaxed scale. Returns (loss, grads, core, relaxed)."""
     q = (lambda a: to_bf16(a)) if bf16 else (lambda a: a)
     x0, c = forward(p, x1, bf16)
     n = x0.size
@@ -163,10 +236,7 @@ def loss_and_grads(p: np.ndarray, x1: np.ndarray, target: np.ndarray, bf16: bool
     df = np.zeros(x0.shape + (16,))
     df[..., 0] = np.sign(x0 - target) / n
     gpre[nl - 1] = q(df)
-    gabs = [None] * nl
-    gabs[nl - 1] = np.abs(gpre[nl - 1])
     grads = []
-    sgrads = []
     for li in range(nl - 1, -1, -1):
         ci, co, kind, _ = SPEC[li]
         W, _ = layers[li]
@@ -178,15 +248,6 @@ def loss_and_grads(p: np.ndarray, x1: np.ndarray, target: np.ndarray, bf16: bool
             dW = conv_wgrad(h, g, 2)
         else:
             dW = conv_wgrad(up2(h), g, 1)
-        if scales:
-            ah, ag = np.abs(h), gabs[li]
-            if kind == "s1":
-                sW = conv_wgrad(ah, ag, 1)
-            elif kind == "s2":
-                sW = conv_wgrad(ah, ag, 2)
-            else:
-                sW = conv_wgrad(up2(ah), ag, 1)
-            sgrads.append((li, sW, ag.reshape(-1, co).sum(axis=0)))
         grads.append((li, dW, g.reshape(-1, co).sum(axis=0)))
         if li == 0:
             break
@@ -200,18 +261,6 @@ def loss_and_grads(p: np.ndarray, x1: np.ndarray, target: np.ndarray, bf16: bool
             if skip == li - 1:
                 dh = dh + gpre[u]
         gpre[li - 1] = q(dh * (acts[li - 1] > 0))
-        if scales:
-            aW = np.abs(W)
-            if kind == "s1":
-                da = conv_adjoint(h.shape, gabs[li], aW, 1)
-            elif kind == "s2":
-                da = conv_adjoint(h.shape, gabs[li], aW, 2)
-            else:
-                da = down2_sum(conv_adjoint(up2(h).shape, gabs[li], aW, 1))
-            for u, (_, _, _, skip) in enumerate(SPEC):
-                if skip == li - 1:
-                    da = da + gabs[u]
-            gabs[li - 1] = da * (acts[li - 1] > 0)
     off = []
     o = 0
     for ci, co, _, _ in SPEC:
@@ -226,9 +275,18 @@ def loss_and_grads(p: np.ndarray, x1: np.ndarray, target: np.ndarray, bf16: bool
             flat[off[li] + 27 * ci * co:off[li] + 27 * ci * co + co] = db
         return flat
 
-    if scales:
-        return loss, pack(grads), pack(sgrads)
-    return loss, pack(grads)
+    if not scales:
+        return loss, pack(grads)
+    mags = _layer_pre_magnitudes(c)
+    pres = c["pres"]
+    amb = [np.abs(pres[li]) <= relu_margin * mags[li] for li in range(nl - 1)]
+    sure = [(pres[li] > 0) & ~amb[li] for li in range(nl - 1)]
+    g_last = np.abs(gpre[nl - 1])
+    h_core = [np.abs(inp)] + [np.abs(acts[li]) * sure[li] for li in range(nl - 1)]
+    h_rel = [np.abs(inp)] + [np.abs(acts[li]) + relu_margin * mags[li] * amb[li] for li in range(nl - 1)]
+    core = _magnitude_chain(c, g_last, [m.astype(np.float64) for m in sure], h_core)
+    rel = _magnitude_chain(c, g_last, [((acts[li] > 0) | amb[li]).astype(np.float64) for li in range(nl - 1)], h_rel)
+    return loss, pack(grads), pack(core), pack(rel)
 
 
 def init_params(seed: int = 0) -> np.ndarray:

@@ -10,12 +10,22 @@ the neighbouring BF16 value: a change of at most one BF16 ulp, 2^-7 of the
 value. A sum of terms each of which changes by at most a relative e changes by
 at most e times the sum of the terms' magnitudes. Every output element is held
 to BF16_BOUND = 2^-6 (two ulps: both factors of a product may have moved)
-times that magnitude sum (forward_scale), plus FP32 rounding. A gradient
-element of layer L is the end of a chain of nl - L stored gradients, each of
-which may have moved by one ulp of its own magnitude chain, plus the stored
-activation it multiplies: it is held to 2^-7 (nl - L + 1) times its magnitude
-chain (loss_and_grads(scales=True)). The loss gradient sign(x0 - target)/n is
-itself a decision: the test's targets sit at least 0.05 from the reference's
+times that magnitude sum (forward_scale), plus FP32 rounding.
+
+Gradients. A ReLU decision on a pre-activation within rounding of zero may go
+either way on the two sides (a float32 re-run of the reference itself flips a
+few dozen per layer), and every gradient term that runs through such a position
+is then present on one side only. loss_and_grads(scales=True) returns two
+magnitude chains (|dLoss/df| carried back with |W| in place of W): `core`
+through the clearly decided positions only, `relaxed` also through every
+position whose pre-activation is within RELU_MARGIN = 2^-6 of its magnitude sum
+of zero (the forward bound's own margin). A gradient element of layer L is
+held to 2^-7 (nl - L + 1) times the relaxed chain (one ulp per stored gradient
+on the way back, plus the stored activation it multiplies) plus relaxed - core
+(the terms that a flipped decision may add or remove). Near the output the
+chains coincide and the bound is tight; towards the input the flipped terms
+fan out and the bound loosens accordingly. The loss gradient sign(x0 - target)/n
+is itself a decision: the test's targets sit at least 0.05 from the reference's
 x0, far outside the forward bound, so that both sides take the same sign."""
 import numpy as np
 import pytest
@@ -66,6 +76,7 @@ def test_param_layout_matches_reference(P):
 
 BF16_BOUND = 2.0**-6
 FP32_FLOOR = 1e-6  # FP32 rounding of the sums, relative to their magnitude sum
+RELU_MARGIN = 2.0**-6  # a pre-activation this close to zero (relative) may take either ReLU decision
 
 
 @pytest.mark.parametrize("seed", [1, 3])
@@ -105,16 +116,17 @@ def test_gradients_match_reference(P, seed):
         net.set_params(p)
         loss, g = net.gradients(torch.tensor(x1.ravel(), dtype=torch.float32, device="cuda"),
                                 torch.tensor(target.ravel(), dtype=torch.float32, device="cuda"))
-    rloss, rg, sg = U.loss_and_grads(p, x1, target, bf16=True, scales=True)
+    rloss, rg, core, rel = U.loss_and_grads(p, x1, target, bf16=True, scales=True, relu_margin=RELU_MARGIN)
     assert abs(loss - rloss) < 1e-3 * rloss
     off = 0
     nl = len(U.SPEC)
     worst = []
     for li, (ci, co, _, _) in enumerate(U.SPEC):
         n = 27 * ci * co + co
-        a, b, s = g[off:off + n].astype(np.float64), rg[off:off + n], sg[off:off + n]
+        a, b = g[off:off + n].astype(np.float64), rg[off:off + n]
+        sc, sr = core[off:off + n], rel[off:off + n]
         # every weight and bias gradient of the layer, element by element
-        bound = (2.0**-7 * (nl - li + 1) + FP32_FLOOR) * s + 1e-30
+        bound = (2.0**-7 * (nl - li + 1) + FP32_FLOOR) * sr + (sr - sc) + 1e-30
         worst.append(float(np.max(np.abs(a - b) / bound)))
         off += n
     assert max(worst) <= 1.0, worst

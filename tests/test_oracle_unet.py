@@ -78,3 +78,29 @@ def test_bf16_rounding_is_round_half_even():
     r = U.to_bf16(v)
     assert r[0] == 1.0 and r[1] == 1.0  # tie to even
     assert r[2] == 1.0 + 2**-7 and r[3] == -2.5
+
+
+def test_gradient_bound_scales_bound_the_gradient():
+    """The magnitude chains of loss_and_grads(scales=True): core <= relaxed
+    everywhere, the two coincide when no position is ambiguous (margin 0 on
+    FP64 data, where no pre-activation is exactly zero), and each gradient
+    element is at most its relaxed chain (|sum of terms| <= sum of |terms|;
+    BF16 storage may round a stored gradient up by 2^-9 of itself per layer)."""
+    rng = np.random.Generator(np.random.Philox(12))
+    p = U.init_params(5)
+    off = 0
+    for ci, co, _, _ in U.SPEC:
+        off += 27 * ci * co
+        p[off:off + co] = 0.05 * rng.standard_normal(co)
+        off += co
+    x1 = rng.random((8, 8, 16))
+    target = x1 + 0.3 * rng.standard_normal(x1.shape)
+    for bf16 in (False, True):
+        loss, g, core, rel = U.loss_and_grads(p, x1, target, bf16=bf16, scales=True, relu_margin=2.0**-6)
+        assert np.all(core >= 0) and np.all(core <= rel)
+        slack = (1.0 + 2.0**-8) ** len(U.SPEC) if bf16 else 1.0 + 1e-12
+        assert np.all(np.abs(g) <= rel * slack + 1e-300)
+        assert (rel > core).any()  # some positions are ambiguous at this margin
+        _, g0, core0, rel0 = U.loss_and_grads(p, x1, target, bf16=bf16, scales=True, relu_margin=0.0)
+        assert np.array_equal(g0, g)
+        assert np.allclose(core0, rel0, rtol=1e-12, atol=0)
