@@ -1,10 +1,12 @@
 """Benchmark: proton-iterations/s of the fused MLP + DROP projection on GB300.
 
-Default workload: the head-sized reconstruction -- 160x160x64 grid of
-1.25 mm voxels (1.64M voxels), ellipsoid head phantom, 50M synthetic histories
-over 90 projection angles, 10 DROP blocks. One step = one DROP sweep over all
-50M histories (every block's fused MLP + projection kernel and its apply);
-value = histories x sweeps / time with the records resident in HBM.
+Default workload: 1e9 synthetic histories on a 200x200x48 grid of
+1 x 1 x 2 mm voxels (1.92M voxels), a seeded random head phantom, 90
+projection angles, 50 DROP blocks (``--workload head200``). ``--workload
+head`` is the 50M-history head on a 160x160x64 grid of 1.25 mm voxels (1.64M
+voxels), 10 blocks. One step = one DROP sweep over all histories (every
+block's fused MLP + projection kernel and its apply); value = histories x
+sweeps / time with the records resident in HBM.
 e2e = the same metric for a full 10-sweep reconstruction through the public
 API from pinned host buffers (load + validation + block counts + 10 sweeps +
 copy of x back to the host).
@@ -173,7 +175,7 @@ def run_reference(args):
         return 0
     from paper_1707_05014_gb300 import synthetic as S
 
-    wl = S.head_workload(args.n)
+    wl = main_workload(args)
     rec = oracle_sample(wl, args.ref_sample)
     rates = []
     cores = 1
@@ -190,13 +192,28 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_t / len(rates),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": wl.name, "grid": "160x160x64x1.25mm", "histories": wl.n, "n_blocks": wl.n_blocks,
+        "config": {"workload": wl.name, "grid": grid_text(wl.grid), "histories": wl.n, "n_blocks": wl.n_blocks,
                    "sample_histories": args.ref_sample},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def main_workload(args, rank: int = 0):
+    """The throughput workload: head200 (1e9 histories, 200x200x48 @ 1x1x2 mm,
+    50 blocks) or head (50M histories, 160x160x64 @ 1.25 mm, 10 blocks); each
+    rank draws its own reconstruction (weak scaling)."""
+    from paper_1707_05014_gb300 import synthetic as S
+
+    if args.workload == "head":
+        return S.head_workload(args.n or 50_000_000, seed=2 + rank)
+    return S.head200_workload(args.n or 1_000_000_000, seed=5 + rank)
+
+
+def grid_text(g) -> str:
+    return f"{g.nx}x{g.ny}x{g.nz} @ {g.hx:g}x{g.hy:g}x{g.hz:g} mm ({g.m / 1e6:.2f}M voxels)"
 
 
 def max_over_ranks(ms: float, device=None) -> float:
@@ -311,7 +328,7 @@ def run_precision(args):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     B.build()
-    n_full = args.n if args.n != 50_000_000 else 250_000_000
+    n_full = args.n or 250_000_000
     base = S.head_workload(n_full, seed=3)
     wl = S.Workload(f"head160_precision_{n_full}", base.grid, n_full, 3, 90, base.t_range, base.v_range, 40, 8,
                     "head")
@@ -352,36 +369,32 @@ def run_precision(args):
     return 0
 
 
-def run_warmstart(args):
-    """Learned warm start: 200 plain-solver reconstructions of seeded random
-    heads (200x200x48 grid, 1x1x2 mm) train the network; on held-out heads with
-    1e9 histories, time to <= 1 % mean RSP error of the warm-started solve
-    against the plain solver (CUDA events on the GPU work; the error check
-    against the known phantom is outside the timed region)."""
+def time_to_image(args, local: int, log) -> dict:
+    """Learned warm start against the plain solver: 200 plain-solver
+    reconstructions of seeded random heads (200x200x48 grid, 1x1x2 mm) train
+    the network; on held-out heads with 1e9 histories, the time to <= 1 % mean
+    RSP error of the warm-started solve and of the plain solver (CUDA events on
+    the GPU work; the error check against the known phantom is outside the
+    timed region). Every step runs in the library's kernels."""
     import numpy as np
     import torch
 
-    from paper_1707_05014_gb300 import build as B
     from paper_1707_05014_gb300 import pct as P
     from paper_1707_05014_gb300 import synthetic as S
     from paper_1707_05014_gb300 import warmstart as W
 
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    B.build()
     g = W.training_grid()
-    log = lambda m: print(m, file=sys.stderr, flush=True)  # noqa: E731
     tuning = None
     if args.ws_tune_blocks:  # blocks-per-update picked on a training head (seed 999), then used throughout
         t0 = time.time()
         args.ws_blocks, trials = W.tune_blocks(g, args.ws_test_n, 999, args.ws_target, args.ws_max_sweeps,
-                                               device=local)
+                                               device=local, lanes=args.lanes)
         tuning = {"chosen": args.ws_blocks, "ms_to_target": {str(b): ms for b, ms in trials.items()},
                   "tuning_s": time.time() - t0}
         log(f"blocks per update: {tuning}")
     t0 = time.time()
     pairs = W.make_training_pairs(g, args.ws_pairs, args.ws_train_n, args.ws_train_sweeps, device=local, log=log,
-                                  blocks=args.ws_blocks)
+                                  blocks=args.ws_blocks, lanes=args.lanes)
     t_data = time.time() - t0
     net = P.Net(g.nz, g.ny, g.nx, seed=7, device=local)
     t0 = time.time()
@@ -395,7 +408,7 @@ def run_warmstart(args):
         wl = W.head_workload(g, args.ws_test_n, 5000 + k, n_blocks=args.ws_blocks)
         x_true = S.voxelize(wl.phantom(), g, ss=2)
         rec = S.make_histories_device(wl, device=f"cuda:{local}")
-        ctx = P.Context(g, n_blocks=wl.n_blocks, device=local)
+        ctx = P.Context(g, n_blocks=wl.n_blocks, device=local, lanes=args.lanes)
         ctx.load(rec)
         del rec
         torch.cuda.empty_cache()
@@ -407,22 +420,40 @@ def run_warmstart(args):
             log(f"test {k} {name}: {r[name]}")
         ctx.close()
         results.append(r)
+    net.close()
     plain_ms = [r["plain"]["ms"] for r in results if r["plain"]["reached"]]
     warm_ms = [r["warm"]["ms"] for r in results if r["warm"]["reached"]]
-    line = {
-        "metric": "time-to-image at <=1% mean RSP error", "value": statistics.mean(warm_ms) / 1e3 if warm_ms else None,
-        "unit": "s", "n_gpus": 1, "higher_is_better": False, "data": "synthetic", "dtype": "f32",
+    return {
+        "metric": "time-to-image at <=1% mean RSP error", "unit": "s", "higher_is_better": False,
+        "warm_seconds": statistics.mean(warm_ms) / 1e3 if warm_ms else None,
+        "plain_seconds": statistics.mean(plain_ms) / 1e3 if plain_ms else None,
+        "speedup": (statistics.mean(plain_ms) / statistics.mean(warm_ms)) if plain_ms and warm_ms else None,
         "config": {"workload": f"warmstart_head200x200x48_{args.ws_test_n}", "grid": "200x200x48 @ 1x1x2 mm",
                    "test_histories": args.ws_test_n, "n_blocks": args.ws_blocks, "target_error": args.ws_target,
                    "training_pairs": args.ws_pairs, "training_histories": args.ws_train_n,
-                   "training_target": f"plain solver after {args.ws_train_sweeps} sweeps", "epochs": args.ws_epochs},
-        "plain_seconds": statistics.mean(plain_ms) / 1e3 if plain_ms else None,
-        "speedup": (statistics.mean(plain_ms) / statistics.mean(warm_ms)) if plain_ms and warm_ms else None,
+                   "training_target": f"plain solver after {args.ws_train_sweeps} sweeps", "epochs": args.ws_epochs,
+                   "lanes_per_history": args.lanes},
         "tests": results, "train_loss": hist, "training_data_s": t_data, "training_s": t_train,
         "blocks_tuning": tuning,
     }
+
+
+def run_warmstart(args):
+    """The time-to-image leg alone (see time_to_image), as its own JSON line."""
+    import torch
+
+    from paper_1707_05014_gb300 import build as B
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    B.build()
+    log = lambda m: print(m, file=sys.stderr, flush=True)  # noqa: E731
+    tti = time_to_image(args, local, log)
+    line = {"metric": tti["metric"], "value": tti["warm_seconds"], "unit": "s", "n_gpus": 1,
+            "higher_is_better": False, "data": "synthetic", "dtype": "f32", "config": tti["config"],
+            "plain_seconds": tti["plain_seconds"], "speedup": tti["speedup"],
+            **{k: tti[k] for k in ("tests", "train_loss", "training_data_s", "training_s", "blocks_tuning")}}
     print(json.dumps(line), flush=True)
-    net.close()
     return 0
 
 
@@ -485,13 +516,13 @@ def run_ours(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     B.build()
-    wl = S.head_workload(args.n, seed=2 + rank)  # weak scaling: each rank its own reconstruction
+    wl = main_workload(args, rank)  # weak scaling: each rank its own reconstruction
     g = wl.grid
     rec = S.make_histories_device(wl, device=f"cuda:{local}")
     torch.cuda.synchronize()
 
     flags = P.FLAG_PROFILE | (P.FLAG_NO_SORT if args.no_sort else 0)
-    ctx = P.Context(g, n_blocks=wl.n_blocks, flags=flags, node_step=args.node_step, device=local)
+    ctx = P.Context(g, n_blocks=wl.n_blocks, flags=flags, node_step=args.node_step, device=local, lanes=args.lanes)
     ctx.load(rec, borrow=True)
     hull = None
     if args.hull:  # object hull carved from the data (untimed set-up, like the load)
@@ -563,7 +594,8 @@ def run_ours(args):
     }
     for k in ("l2_atomic", "l2_gather", "alu_issue"):
         measured[k]["frac"] = measured[k]["achieved"] / measured[k]["peak"]
-    roof = {"kernel": "drop_fused_hull_kernel" if args.hull else "drop_fused_kernel", "bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
+    kname = "drop_fused_hull_kernel" if args.hull else ("drop_group_kernel" if args.lanes > 1 else "drop_fused_kernel")
+    roof = {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
             "frac": achieved / alu_peak, "traffic": traffic,
             "peak_source": f"{ALU_LANES_PER_SM} lanes x {N_SMS} SMs x {sm_mhz:.0f} MHz",
             "ops_per_history": ops_per_history, "runs_per_history": runs_per_history, "mlp_nodes": ctx.K + 1,
@@ -576,11 +608,14 @@ def run_ours(args):
     # end to end through the public API from pinned host buffers
     e2e = None
     if args.e2e_steps > 0:
-        host = {k: v.cpu().pin_memory() for k, v in rec.items()}
+        host = {}
+        for k, v in rec.items():  # pinned host copies, one field at a time
+            host[k] = torch.empty(v.shape, dtype=v.dtype, pin_memory=True)
+            host[k].copy_(v)
         del rec
         torch.cuda.empty_cache()
         ctx.close()
-        ctx2 = P.Context(g, n_blocks=wl.n_blocks, node_step=args.node_step, device=local)
+        ctx2 = P.Context(g, n_blocks=wl.n_blocks, node_step=args.node_step, device=local, lanes=args.lanes)
         xs = []
         times = []
         for i in range(1 + args.e2e_steps):
@@ -603,6 +638,21 @@ def run_ours(args):
     else:
         ctx.close()
 
+    tti = None
+    if rank == 0 and args.time_to_image:
+        # second half of the metric: time to <= 1 % mean RSP error, warm start
+        # against the plain solver, the network trained in this run
+        host = rec = None  # the throughput leg's records (host and device) are no longer needed
+        torch.cuda.empty_cache()
+        log = lambda m: print(m, file=sys.stderr, flush=True)  # noqa: E731
+        full = time_to_image(args, local, log)
+        tti = {k: full[k] for k in ("metric", "unit", "higher_is_better", "warm_seconds", "plain_seconds", "speedup",
+                                    "config", "training_data_s", "training_s")}
+        tti["tests"] = [{"seed": r["seed"], **{m: {"seconds": r[m]["ms"] / 1e3, "sweeps": r[m]["sweeps"],
+                                                   "reached": r[m]["reached"], "errors": r[m]["errors"],
+                                                   **({"net_used": r[m]["net_used"]} if m == "warm" else {})}
+                                               for m in ("plain", "warm")}} for r in full["tests"]]
+
     cpu = None
     if rank == 0 and args.cpu_sample > 0:
         crec = oracle_sample(wl, args.cpu_sample)
@@ -620,14 +670,16 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": wl.name + ("_hull" if args.hull else "") + (f"_step{args.node_step:g}mm" if args.node_step > 0 else ""),
-                       "grid": "160x160x64 @ 1.25 mm (1.64M voxels)",
+                       "grid": grid_text(g),
                        "mlp_node_step_mm": args.node_step if args.node_step > 0 else min(g.hx, g.hy, g.hz) / 2,
+                       "lanes_per_history": args.lanes,
                        "histories_per_gpu": wl.n, "angles": 90, "n_blocks": wl.n_blocks,
                        "step": "one DROP sweep over all histories", "parallelism": f"replicas{world}",
-                       "l2": "records 2.2 GB per sweep > 129 MB L2 (no flush needed); x and delta L2-resident",
+                       "l2": f"records {44 * wl.n / 1e9:.1f} GB per sweep > 129 MB L2 (no flush needed); x and delta L2-resident",
                        "hull": (f"carved from the data: rows of histories with WEPL <= {args.hull_wepl} mm are air, "
                                 f"hull dilated by {args.hull_dilate} voxel") if args.hull else "none (MLP between the planes)"},
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "time_to_image": tti, "gpu_launches": launches,
+            "clocks": clk,
             "host_threads": _cpu_threads(),
         }
         print(json.dumps(line), flush=True)
@@ -642,22 +694,26 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=int, default=50_000_000, help="histories per GPU")
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--n", type=int, default=None, help="histories per GPU (default: the workload's own)")
+    ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--e2e-sweeps", type=int, default=10)
     ap.add_argument("--cpu-sample", type=int, default=1_000_000)
     ap.add_argument("--ref-sample", type=int, default=1_000_000)
+    ap.add_argument("--lanes", type=int, default=1, help="lanes per history in the fused kernel (1, 8, 16, 32)")
     ap.add_argument("--no-sort", action="store_true", help="keep each block in load order (A/B of the ordering)")
     ap.add_argument("--hull", action="store_true", help="head / table2: MLP inside a hull carved from the data")
     ap.add_argument("--node-step", type=float, default=0.0, help="head: MLP node spacing in mm (default min(h)/2)")
     ap.add_argument("--hull-wepl", type=float, default=1.0, help="carving: histories with WEPL <= this (mm) are air")
     ap.add_argument("--hull-dilate", type=int, default=1, help="carving: 6-neighbour growth steps of the hull")
-    ap.add_argument("--workload", default="head", choices=["head", "batched", "precision", "warmstart", "table2"])
+    ap.add_argument("--workload", default="head200",
+                    choices=["head200", "head", "batched", "precision", "warmstart", "table2"])
     ap.add_argument("--t2-n", type=int, default=200_000_000)
     ap.add_argument("--t2-blocks", type=int, default=600, help="DROP blocks; CARP: blocks split over the strings")
     ap.add_argument("--t2-strings", type=int, default=60)
     ap.add_argument("--t2-sweeps", type=int, default=10)
     ap.add_argument("--t2-tvs", type=float, default=0.02)
+    ap.add_argument("--no-time-to-image", dest="time_to_image", action="store_false",
+                    help="skip the time-to-image leg of the default run")
     ap.add_argument("--ws-pairs", type=int, default=200)
     ap.add_argument("--ws-train-n", type=int, default=50_000_000)
     ap.add_argument("--ws-train-sweeps", type=int, default=3)

@@ -65,7 +65,11 @@ typedef struct pct_config {
   double node_step_mm;      /* MLP node spacing request; <= 0: min(h)/2        */
   int32_t flags;            /* PCT_FLAG_*                                      */
   float clamp_min;          /* lower clamp of x after each block (with flag)   */
-  int32_t threads_per_proton; /* 1 (reserved for 2, 4, 8)                      */
+  int32_t threads_per_proton; /* lanes per history in the fused kernel and the
+                               row export: 1 (0 = 1) or 8, 16, 32 (the group
+                               walk: the lanes split the history's MLP
+                               segments; same runs, in the same order). With an
+                               object hull the one-lane kernels run.          */
   int32_t cta_threads;      /* threads per CTA of the load-time count kernel;
                              * 0 = 128 (the fused kernel always runs 128)    */
   /* Total-variation superiorization (Sec. 4.2), off when tvs_beta0 <= 0:

@@ -178,14 +178,15 @@ pct_status pct_create(pct_ctx** out, const pct_grid* grid, const pct_config* cfg
     return fail(PCT_ERR_INVALID_ARG, "voxel sizes must be finite and > 0");
   if (cfg->n_blocks < 1) return fail(PCT_ERR_INVALID_ARG, "n_blocks must be >= 1");
   if (!(cfg->lambda > 0.f && cfg->lambda < 2.f)) return fail(PCT_ERR_INVALID_ARG, "lambda must be in (0, 2)");
-  if (cfg->threads_per_proton != 0 && cfg->threads_per_proton != 1)
-    return fail(PCT_ERR_INVALID_ARG, "threads_per_proton must be 1");
+  if (cfg->threads_per_proton != 0 && cfg->threads_per_proton != 1 && !pct::group_lanes_supported(cfg->threads_per_proton))
+    return fail(PCT_ERR_INVALID_ARG, "threads_per_proton must be 1, 8, 16 or 32");
 
   pct_ctx* c = new pct_ctx();
   c->device = device;
   c->grid = g;
   c->cfg = *cfg;
   if (c->cfg.cta_threads <= 0) c->cfg.cta_threads = 128;
+  if (c->cfg.threads_per_proton <= 0) c->cfg.threads_per_proton = 1;
   if (c->cfg.tvs_alpha <= 0.f) c->cfg.tvs_alpha = 0.99f;
   if (c->cfg.tvs_eps <= 0.f) c->cfg.tvs_eps = 1e-4f;
   if (c->cfg.tvs_tries <= 0) c->cfg.tvs_tries = 4;
@@ -252,6 +253,7 @@ pct_status pct_create(pct_ctx** out, const pct_grid* grid, const pct_config* cfg
     if ((e = cudaMemsetAsync(c->x, 0, M * sizeof(float), c->stream)) != cudaSuccess ||
         (e = cudaMemsetAsync(c->delta, 0, M * sizeof(float), c->stream)) != cudaSuccess ||
         (e = pct::launch_mlp_table(c->R, c->du, c->K, c->tab64, c->tab32, c->stream)) != cudaSuccess ||
+        (c->cfg.threads_per_proton > 1 && (e = pct::prepare_drop_group(c->cfg.threads_per_proton, c->K)) != cudaSuccess) ||
         (e = cudaStreamSynchronize(c->stream)) != cudaSuccess) {
       st = fail(PCT_ERR_CUDA, "context set-up: %s", cudaGetErrorString(e));
       break;
@@ -606,7 +608,7 @@ pct_status pct_mlp_rows(pct_ctx* c, int64_t first, int64_t count, int64_t* row_p
   pct::DeviceGuard device_guard_;
   PCT_CK(cudaSetDevice(c->device));
   PCT_CK(pct::launch_row_counts(c->geo, c->rec, c->tab32, pct::hull_view(c), first, count, c->where, row_ptr,
-                                c->stream));
+                                c->cfg.threads_per_proton, c->stream));
   PCT_CK(pct::launch_scan_rows(row_ptr, count, c->stream));
   c->launches += 2;
   int64_t total = 0;
@@ -616,8 +618,7 @@ pct_status pct_mlp_rows(pct_ctx* c, int64_t first, int64_t count, int64_t* row_p
   if (total > cap) return fail(PCT_ERR_CAPACITY, "rows need %lld runs, capacity %lld", (long long)total,
                                (long long)cap);
   PCT_CK(pct::launch_row_fill(c->geo, c->rec, c->tab32, pct::hull_view(c), first, count, c->where, row_ptr, vox,
-                              len, nodes,
-                              c->stream));
+                              len, nodes, c->cfg.threads_per_proton, c->stream));
   c->launches += 1;
   return sync_and_check(c);
 }
@@ -706,7 +707,7 @@ static pct_status build_sweep_graph(pct_ctx* c, bool counting, cudaGraphExec_t* 
       if (err == cudaSuccess && c->ev) err = cudaEventRecordWithFlags(c->ev[3 * b], s, cudaEventRecordExternal);
       if (err == cudaSuccess)
         err = pct::launch_drop_fused(c->geo, c->rec, c->tab32, pct::hull_view(c), lo, hi - lo, c->x, c->delta,
-                                     c->cfg.lambda, c->cfg.flags, c->cfg.cta_threads, s, counting ? c->cnt : nullptr);
+                                     c->cfg.lambda, c->cfg.flags, c->cfg.threads_per_proton, s, counting ? c->cnt : nullptr);
       if (err == cudaSuccess && c->ev) err = cudaEventRecordWithFlags(c->ev[3 * b + 1], s, cudaEventRecordExternal);
       if (err == cudaSuccess && counting) err = pct::launch_inv_counts(c->cnt, c->inv_s + (size_t)b * c->M, c->M, s);
       if (err == cudaSuccess)
@@ -780,7 +781,7 @@ pct_status pct_block_partial(pct_ctx* c, int32_t block, float* delta_out, float*
   PCT_CK(cudaMemsetAsync(delta_out, 0, bytes, c->stream));
   if (counts_out) PCT_CK(cudaMemsetAsync(c->cnt, 0, (size_t)c->M * sizeof(unsigned int), c->stream));
   PCT_CK(pct::launch_drop_fused(c->geo, c->rec, c->tab32, pct::hull_view(c), lo, hi - lo, c->x, delta_out,
-                                c->cfg.lambda, c->cfg.flags, c->cfg.cta_threads, c->stream,
+                                c->cfg.lambda, c->cfg.flags, c->cfg.threads_per_proton, c->stream,
                                 counts_out ? c->cnt : nullptr));
   c->launches += 1;
   if (counts_out) {

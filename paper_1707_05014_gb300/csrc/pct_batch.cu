@@ -280,7 +280,7 @@ pct_status enqueue_branches(pct_batch* b, int n_sweeps, cudaStream_t s) {
       for (int blk = 0; blk < c->cfg.n_blocks; ++blk) {
         const int64_t lo = pct::block_first(c, blk), hi = pct::block_first(c, blk + 1);
         PCT_BCK(pct::launch_drop_fused(c->geo, c->rec, c->tab32, pct::Hull{}, lo, hi - lo, c->x, c->delta,
-                                       c->cfg.lambda, c->cfg.flags, c->cfg.cta_threads, bs));
+                                       c->cfg.lambda, c->cfg.flags, c->cfg.threads_per_proton, bs));
         PCT_BCK(pct::launch_drop_apply(c->x, c->delta, c->inv_s + (size_t)blk * c->M, c->M, clamp,
                                        c->cfg.clamp_min, bs));
         b->launches += 2;

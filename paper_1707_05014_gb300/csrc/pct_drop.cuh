@@ -19,11 +19,12 @@ __device__ __forceinline__ float ld_weak(const float* p) {
 }
 
 // MLP nodes -> walk -> compensated a_i.x and |a_i|^2 -> relaxed residual ->
-// scatter-add into delta. The walk gathers x for each run as it emits it
-// (a_i.x and |a_i|^2 are complete when the walk ends) and records the row
-// (voxel, chord) in thread-local memory; the scatter replays the record. A
-// row longer than kRowCap runs (none for valid records on the supported
-// grids) is walked again for the scatter instead.
+// scatter-add into delta. The walk only records the row (voxel, chord) in
+// thread-local memory; the gather of x for a_i.x and the scatter replay the
+// record, outside the walk's divergent crossing loop, so no lane waits on a
+// global load inside the walk. A row longer than kRowCap runs (none for valid
+// records on the supported grids) is walked again for the gather and for the
+// scatter instead.
 //
 // kPlain: plain instead of compensated summation (PCT_FLAG_NO_KAHAN).
 // kCoherent: x may change while the kernel runs (the batched persistent
@@ -39,8 +40,13 @@ __device__ __forceinline__ void drop_history_core(const RecV& v, Walk&& walk, co
   auto xload = [&](int j) { return kCoherent ? ld_weak(x + j) : __ldg(x + j); };
   uint2 row[kRowCap];
   int nrow = 0;
-  float y = 0.f, c = 0.f, nn = 0.f;
   walk([&](int j, float l) {
+    if (kCount) atomicAdd(cnt + j, 1u);
+    if (nrow < kRowCap) row[nrow] = make_uint2((unsigned)j, __float_as_uint(l));
+    ++nrow;
+  });
+  float y = 0.f, c = 0.f, nn = 0.f;
+  auto gather = [&](int j, float l) {
     const float xj = xload(j);
     if (kPlain) {
       y = __fmaf_rn(l, xj, y);
@@ -52,10 +58,15 @@ __device__ __forceinline__ void drop_history_core(const RecV& v, Walk&& walk, co
       y = t;
     }
     nn = __fmaf_rn(l, l, nn);
-    if (kCount) atomicAdd(cnt + j, 1u);
-    if (nrow < kRowCap) row[nrow] = make_uint2((unsigned)j, __float_as_uint(l));
-    ++nrow;
-  });
+  };
+  if (nrow <= kRowCap) {
+    for (int q = 0; q < nrow; ++q) {
+      const uint2 e = row[q];
+      gather((int)e.x, __uint_as_float(e.y));
+    }
+  } else {
+    walk(gather);
+  }
   if (!(nn > 0.f)) return;
   const float res = __fadd_rn(__fsub_rn(v.wepl, y), c);
   const float ri = lambda * res / nn;

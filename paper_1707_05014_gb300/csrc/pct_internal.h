@@ -21,6 +21,7 @@ constexpr int kMaxDim = 512;             // per-axis voxel limit
 constexpr int kSortAngles = 256;         // load-time ordering: gantry-angle bins
 constexpr int kSortLateral = 4096;       // load-time ordering: mid-path lateral-position bins
 constexpr int kRowCap = 512;             // runs kept per history between the fused kernel's two passes
+constexpr int kGroupRowCap = 384;        // runs kept in shared memory per history by the group kernel
 
 // Grid and node geometry in the single-precision form the kernels use.
 struct Geo {
@@ -137,10 +138,24 @@ cudaError_t launch_count(const Geo& g, const Rec& r, const float4* tab, const Hu
                          unsigned int* cnt, int threads, cudaStream_t s);
 cudaError_t launch_inv_counts(const unsigned int* cnt, float* inv_s, int64_t M, cudaStream_t s);
 cudaError_t launch_counts_to_float(const unsigned int* cnt, float* out, int64_t M, cudaStream_t s);
-// cnt non-null: also count the block's runs per voxel into cnt (zeroed by the caller).
+// cnt non-null: also count the block's runs per voxel into cnt (zeroed by the
+// caller). lanes: lanes per history, 1 (one thread per history) or, without
+// a hull, 8, 16 or 32 (the group walk).
 cudaError_t launch_drop_fused(const Geo& g, const Rec& r, const float4* tab, const Hull& hull, int64_t first, int64_t count,
-                              const float* x, float* delta, float lambda, int flags, int threads, cudaStream_t s,
+                              const float* x, float* delta, float lambda, int flags, int lanes, cudaStream_t s,
                               unsigned int* cnt = nullptr);
+// The group walk (T lanes per history, T in {8, 16, 32}; no hull): the fused
+// kernel and the row export. prepare_drop_group sets the fused kernels'
+// shared-memory limit for K + 1 table nodes; call it outside stream capture
+// before the first launch for that K.
+bool group_lanes_supported(int T);
+cudaError_t prepare_drop_group(int T, int K);
+cudaError_t launch_drop_group(int T, const Geo& g, const Rec& r, const float4* tab, int64_t first, int64_t count,
+                              const float* x, float* delta, float lambda, int flags, cudaStream_t s,
+                              unsigned int* cnt = nullptr);
+cudaError_t launch_rows_group(int T, const Geo& g, const Rec& r, const float4* tab, int64_t first, int64_t count,
+                              const int64_t* where, int64_t* row_ptr, int32_t* vox, float* len, int32_t* nodes,
+                              bool fill, cudaStream_t s);
 cudaError_t launch_drop_apply(float* x, float* delta, const float* inv_s, int64_t M, int clamp, float clamp_min,
                               cudaStream_t s);
 // x_j += delta_j / s_j where s_j = counts_j > 0 (else unchanged), optional
@@ -166,11 +181,11 @@ cudaError_t launch_project(const Geo& g, const Rec& r, const float4* tab, const 
 cudaError_t launch_residual(const Geo& g, const Rec& r, const float4* tab, const Hull& hull, int64_t n, int64_t stride, const float* x,
                             int flags, double* acc, cudaStream_t s);
 cudaError_t launch_row_counts(const Geo& g, const Rec& r, const float4* tab, const Hull& hull, int64_t first, int64_t count,
-                              const int64_t* where, int64_t* row_ptr, cudaStream_t s);
+                              const int64_t* where, int64_t* row_ptr, int lanes, cudaStream_t s);
 cudaError_t launch_scan_rows(int64_t* row_ptr, int64_t count, cudaStream_t s);
 cudaError_t launch_row_fill(const Geo& g, const Rec& r, const float4* tab, const Hull& hull, int64_t first, int64_t count,
                             const int64_t* where, const int64_t* row_ptr, int32_t* vox, float* len, int32_t* nodes,
-                            cudaStream_t s);
+                            int lanes, cudaStream_t s);
 
 // Saves the calling thread's current device and restores it when the entry
 // point returns: the library switches to a context's device for its work and

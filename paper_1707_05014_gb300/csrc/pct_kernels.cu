@@ -529,10 +529,11 @@ cudaError_t launch_counts_to_float(const unsigned int* cnt, float* out, int64_t 
 }
 
 cudaError_t launch_drop_fused(const Geo& g, const Rec& r, const float4* tab, const Hull& hull, int64_t first,
-                              int64_t count, const float* x, float* delta, float lambda, int flags, int threads,
+                              int64_t count, const float* x, float* delta, float lambda, int flags, int lanes,
                               cudaStream_t s, unsigned int* cnt) {
   if (count <= 0) return cudaSuccess;
-  threads = 128;
+  if (lanes > 1 && !hull.range) return launch_drop_group(lanes, g, r, tab, first, count, x, delta, lambda, flags, s, cnt);
+  const int threads = 128;
   const unsigned blocks = grid_for(count, threads);
   const bool plain = (flags & 2) != 0;
   if (hull.range) {
@@ -621,8 +622,10 @@ cudaError_t launch_tvs(float* x, int nx, int ny, int nz, const TvsParams& p, flo
 }
 
 cudaError_t launch_row_counts(const Geo& g, const Rec& r, const float4* tab, const Hull& hull, int64_t first,
-                              int64_t count, const int64_t* where, int64_t* row_ptr, cudaStream_t s) {
+                              int64_t count, const int64_t* where, int64_t* row_ptr, int lanes, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
+  if (lanes > 1 && !hull.range)
+    return launch_rows_group(lanes, g, r, tab, first, count, where, row_ptr, nullptr, nullptr, nullptr, false, s);
   row_count_kernel<<<grid_for(count, 128), 128, (g.K + 1) * sizeof(float4), s>>>(g, r, tab, hull, first, count,
                                                                                   where, row_ptr);
   return cudaGetLastError();
@@ -635,8 +638,11 @@ cudaError_t launch_scan_rows(int64_t* row_ptr, int64_t count, cudaStream_t s) {
 
 cudaError_t launch_row_fill(const Geo& g, const Rec& r, const float4* tab, const Hull& hull, int64_t first,
                             int64_t count, const int64_t* where, const int64_t* row_ptr, int32_t* vox, float* len,
-                            int32_t* nodes, cudaStream_t s) {
+                            int32_t* nodes, int lanes, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
+  if (lanes > 1 && !hull.range)
+    return launch_rows_group(lanes, g, r, tab, first, count, where, const_cast<int64_t*>(row_ptr), vox, len, nodes,
+                             true, s);
   row_fill_kernel<<<grid_for(count, 128), 128, (g.K + 1) * sizeof(float4), s>>>(g, r, tab, hull, first, count,
                                                                                  where, row_ptr, vox, len, nodes);
   return cudaGetLastError();

@@ -203,12 +203,15 @@ class Context:
 
     def __init__(self, grid, n_blocks: int = 10, lam: float = 1.0, node_step: float = 0.0, flags: int = 0,
                  clamp_min: float = 0.0, device: int = 0, cta_threads: int = 128, tvs_beta0: float = 0.0,
-                 tvs_alpha: float = 0.99, tvs_eps: float = 1e-4, tvs_tries: int = 4, carp_strings: int = 0):
+                 tvs_alpha: float = 0.99, tvs_eps: float = 1e-4, tvs_tries: int = 4, carp_strings: int = 0,
+                 lanes: int = 1):
         L = load_library()
         self._L = L
         self.grid = grid
+        self.lanes = int(lanes)
         g = _Grid(int(grid.nx), int(grid.ny), int(grid.nz), float(grid.hx), float(grid.hy), float(grid.hz))
-        c = _Config(int(n_blocks), float(lam), float(node_step), int(flags), float(clamp_min), 1, int(cta_threads),
+        c = _Config(int(n_blocks), float(lam), float(node_step), int(flags), float(clamp_min), int(lanes),
+                    int(cta_threads),
                     float(tvs_beta0), float(tvs_alpha), float(tvs_eps), int(tvs_tries), int(carp_strings))
         h = ctypes.c_void_p()
         _check(L.pct_create(ctypes.byref(h), ctypes.byref(g), ctypes.byref(c), int(device)))

@@ -36,12 +36,12 @@ def head_workload(grid: S.Grid, n: int, seed: int, n_blocks: int = 10) -> S.Work
                       min(46.0, 0.5 * grid.nz * grid.hz - 2.0), n_blocks, 10, "head", 0.15)
 
 
-def plain_pair(wl: S.Workload, sweeps: int, device: int = 0, lam: float = 1.0):
+def plain_pair(wl: S.Workload, sweeps: int, device: int = 0, lam: float = 1.0, lanes: int = 1):
     """(x1, x_sweeps) of one plain-solver reconstruction, as CUDA tensors."""
     import torch
 
     rec = S.make_histories_device(wl, device=f"cuda:{device}")
-    with P.Context(wl.grid, n_blocks=wl.n_blocks, lam=lam, device=device) as ctx:
+    with P.Context(wl.grid, n_blocks=wl.n_blocks, lam=lam, device=device, lanes=lanes) as ctx:
         ctx.load(rec)
         del rec
         ctx.iterate(1)
@@ -53,11 +53,13 @@ def plain_pair(wl: S.Workload, sweeps: int, device: int = 0, lam: float = 1.0):
 
 
 def make_training_pairs(grid: S.Grid, n_pairs: int, n_histories: int, sweeps: int, seed0: int = 1000,
-                        device: int = 0, log: Optional[Callable[[str], None]] = None, blocks: int = 10):
+                        device: int = 0, log: Optional[Callable[[str], None]] = None, blocks: int = 10,
+                        lanes: int = 1):
     pairs = []
     t0 = time.time()
     for k in range(n_pairs):
-        pairs.append(plain_pair(head_workload(grid, n_histories, seed0 + k, n_blocks=blocks), sweeps, device))
+        pairs.append(plain_pair(head_workload(grid, n_histories, seed0 + k, n_blocks=blocks), sweeps, device,
+                                lanes=lanes))
         if log and (k + 1) % 25 == 0:
             log(f"training pairs {k + 1}/{n_pairs} ({time.time() - t0:.0f} s)")
     return pairs
@@ -161,7 +163,7 @@ def pick_blocks(trial: Callable[[int, Optional[float]], Optional[float]], candid
 
 
 def tune_blocks(grid: S.Grid, n: int, seed: int, target: float, max_sweeps: int,
-                candidates: Sequence[int] = (10, 20, 50, 100), device: int = 0) -> Tuple[int, Dict]:
+                candidates: Sequence[int] = (10, 20, 50, 100), device: int = 0, lanes: int = 1) -> Tuple[int, Dict]:
     """pick_blocks on one seeded training head: for each B, a plain
     reconstruction from x = 0 timed to the target mean RSP error (the known
     phantom of a training case decides; held-out cases are never used)."""
@@ -171,7 +173,7 @@ def tune_blocks(grid: S.Grid, n: int, seed: int, target: float, max_sweeps: int,
         wl = head_workload(grid, n, seed, n_blocks=b)
         x_true = S.voxelize(wl.phantom(), grid, ss=2)
         rec = S.make_histories_device(wl, device=f"cuda:{device}")
-        with P.Context(grid, n_blocks=b, device=device) as ctx:
+        with P.Context(grid, n_blocks=b, device=device, lanes=lanes) as ctx:
             ctx.load(rec)
             del rec
             torch.cuda.empty_cache()
