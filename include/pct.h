@@ -329,6 +329,10 @@ typedef struct pct_batch_config {
   int32_t debug_unreachable_wait; /* test hook: non-zero makes every block-update wait
                                      unreachable, so the bound runs out and the call
                                      reports PCT_ERR_TIMEOUT (the GPU stays usable)        */
+  int32_t lanes;                  /* graph-branch mode: lanes per history of the fused
+                                     kernels (1, 8, 16 or 32, as threads_per_proton);
+                                     <= 0: each context's own threads_per_proton. The
+                                     persistent kernel always takes one lane per history  */
 } pct_batch_config;
 
 /* Group n loaded contexts (same device) for batched sweeps. cfg may be NULL

@@ -436,7 +436,7 @@ pct_status pct_load_histories(pct_ctx* c, const pct_histories* h, int flags, int
     c->where = c->where_buf;
     PCT_GROW(c->sort_key, c->key_cap, max_blk);
     PCT_GROW(c->sort_order, c->order_cap, max_blk);
-    PCT_GROW(c->sort_hist, c->hist_cap, (int64_t)pct::kSortAngles * pct::kSortLateral);
+    PCT_GROW(c->sort_hist, c->hist_cap, pct::kSortHistEntries);
   }
   if (flags == PCT_LOAD_HOST) PCT_GROW(c->staging, c->staging_cap, max_blk * 11);
 

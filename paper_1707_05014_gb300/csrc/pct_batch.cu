@@ -265,6 +265,19 @@ pct_status enqueue(pct_batch* b, int n_sweeps, cudaStream_t s, long long spin_li
   return PCT_OK;
 }
 
+// Lanes per history of a context's fused kernels in graph-branch mode.
+int lanes_of(const pct_batch* b, const pct_ctx* c) { return b->cfg.lanes > 0 ? b->cfg.lanes : c->cfg.threads_per_proton; }
+
+// The group kernels' shared-memory limit for every context's table, set
+// outside stream capture.
+pct_status prepare_lanes(pct_batch* b) {
+  for (auto* c : b->ctx) {
+    const int T = lanes_of(b, c);
+    if (T > 1) PCT_BCK(pct::prepare_drop_group(T, c->K));
+  }
+  return PCT_OK;
+}
+
 // Graph-branch mode: each reconstruction's stages as a chain of the per-block
 // kernels (fused, then apply, per block), chains spread over branch streams
 // that fork from and join into s, so that independent chains overlap.
@@ -280,7 +293,7 @@ pct_status enqueue_branches(pct_batch* b, int n_sweeps, cudaStream_t s) {
       for (int blk = 0; blk < c->cfg.n_blocks; ++blk) {
         const int64_t lo = pct::block_first(c, blk), hi = pct::block_first(c, blk + 1);
         PCT_BCK(pct::launch_drop_fused(c->geo, c->rec, c->tab32, pct::Hull{}, lo, hi - lo, c->x, c->delta,
-                                       c->cfg.lambda, c->cfg.flags, c->cfg.threads_per_proton, bs));
+                                       c->cfg.lambda, c->cfg.flags, lanes_of(b, c), bs));
         PCT_BCK(pct::launch_drop_apply(c->x, c->delta, c->inv_s + (size_t)blk * c->M, c->M, clamp,
                                        c->cfg.clamp_min, bs));
         b->launches += 2;
@@ -387,6 +400,11 @@ pct_status pct_batch_create(pct_batch** out, pct_ctx* const* ctxs, int32_t n, co
       break;
     }
     if (b->cfg.ctas_per_sm <= 0 || b->cfg.ctas_per_sm > b->max_ctas_per_sm) b->cfg.ctas_per_sm = b->max_ctas_per_sm;
+    if (b->cfg.lanes < 0) b->cfg.lanes = 0;
+    if (b->cfg.lanes > 1 && !pct::group_lanes_supported(b->cfg.lanes)) {
+      st = bfail(PCT_ERR_INVALID_ARG, "lanes must be 1, 8, 16 or 32");
+      break;
+    }
     std::vector<ReconDesc> rd(n);
     for (int r = 0; r < n; ++r) {
       pct_ctx* c = b->ctx[r];
@@ -455,6 +473,10 @@ pct_status pct_batch_iterate(pct_batch* b, int32_t n_sweeps, void* stream) {
     b->graph = nullptr;
     cudaGraph_t g = nullptr;
     PCT_BCK(cudaStreamSynchronize(s));
+    if (b->cfg.mode != PCT_BATCH_PERSISTENT) {
+      const pct_status ps = prepare_lanes(b);
+      if (ps != PCT_OK) return ps;
+    }
     PCT_BCK(cudaStreamBeginCapture(b->own_stream, cudaStreamCaptureModeThreadLocal));
     const int64_t l0 = b->launches;
     pct_status st = enqueue_any(b, n_sweeps, b->own_stream, spin_limit_of(b));
@@ -504,15 +526,16 @@ pct_status pct_batch_autotune(pct_batch* b, pct_batch_config* chosen, float* bes
     off += c->M;
   }
   struct Cand {
-    int mode, chunk, ctas, branches;
+    int mode, chunk, ctas, branches, lanes;
   };
   std::vector<Cand> cands;
-  for (int nb : {1, 4, 8})
-    if (nb <= (int)b->branch.size() && (nb == 1 || nb <= (int)b->ctx.size()))
-      cands.push_back({PCT_BATCH_GRAPH_BRANCHES, b->cfg.chunk, b->cfg.ctas_per_sm, nb});
+  for (int lanes : {1, 16, 32})
+    for (int nb : {1, 4, 8})
+      if (nb <= (int)b->branch.size() && (nb == 1 || nb <= (int)b->ctx.size()))
+        cands.push_back({PCT_BATCH_GRAPH_BRANCHES, b->cfg.chunk, b->cfg.ctas_per_sm, nb, lanes});
   for (int ch : {2048, 4096, 8192})
     for (int v : {b->max_ctas_per_sm, b->max_ctas_per_sm - 1, b->max_ctas_per_sm / 2})
-      if (v >= 1) cands.push_back({PCT_BATCH_PERSISTENT, ch, v, b->cfg.branches});
+      if (v >= 1) cands.push_back({PCT_BATCH_PERSISTENT, ch, v, b->cfg.branches, 1});
   cudaEvent_t e0, e1;
   PCT_BCK(cudaEventCreate(&e0));
   PCT_BCK(cudaEventCreate(&e1));
@@ -524,7 +547,9 @@ pct_status pct_batch_autotune(pct_batch* b, pct_batch_config* chosen, float* bes
     b->cfg.chunk = cd.chunk;
     b->cfg.ctas_per_sm = cd.ctas;
     b->cfg.branches = cd.branches;
+    b->cfg.lanes = cd.lanes;
     if ((st = build_plan(b)) != PCT_OK) break;
+    if (cd.mode != PCT_BATCH_PERSISTENT && (st = prepare_lanes(b)) != PCT_OK) break;
     float t = 0.f;
     if (cudaEventRecord(e0, s) != cudaSuccess || (st = enqueue_any(b, 1, s, spin_limit_of(b))) != PCT_OK ||
         cudaEventRecord(e1, s) != cudaSuccess || (st = read_status(b, s)) != PCT_OK ||

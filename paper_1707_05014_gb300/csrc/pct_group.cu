@@ -131,6 +131,46 @@ __device__ __forceinline__ SegEv seg_events(const float3 P, const float3 Q) {
   return e;
 }
 
+// The same by the float fractions, for segments whose crossing fractions are
+// at least kTieWindow apart and from 1 (near = false): then the float order
+// is the exact order and there are no ties. near = true: the caller takes
+// seg_events.
+__device__ __forceinline__ SegEv seg_events_float(const float3 P, const float3 Q, bool& near) {
+  SegEv e;
+  const float bPx = __fadd_rd(P.x, kFloorBias), bPy = __fadd_rd(P.y, kFloorBias), bPz = __fadd_rd(P.z, kFloorBias);
+  const float bQx = __fadd_rd(Q.x, kFloorBias), bQy = __fadd_rd(Q.y, kFloorBias), bQz = __fadd_rd(Q.z, kFloorBias);
+  e.ix = vox_of(bPx);
+  e.iy = vox_of(bPy);
+  e.iz = vox_of(bPz);
+  const bool cx = bQx != bPx, cy = bQy != bPy, cz = bQz != bPz;
+  const bool ux = bQx > bPx, uy = bQy > bPy, uz = bQz > bPz;
+  const float ndx = fabsf(__fsub_rn(__fsub_rn(ux ? bQx : bPx, kFloorBias), P.x));
+  const float ndy = fabsf(__fsub_rn(__fsub_rn(uy ? bQy : bPy, kFloorBias), P.y));
+  const float ndz = fabsf(__fsub_rn(__fsub_rn(uz ? bQz : bPz, kFloorBias), P.z));
+  const float tx = cx ? __fdividef(ndx, fabsf(__fsub_rn(Q.x, P.x))) : INFINITY;
+  const float ty = cy ? __fdividef(ndy, fabsf(__fsub_rn(Q.y, P.y))) : INFINITY;
+  const float tz = cz ? __fdividef(ndz, fabsf(__fsub_rn(Q.z, P.z))) : INFINITY;
+  const float tmax = fmaxf(cx ? tx : 0.f, fmaxf(cy ? ty : 0.f, cz ? tz : 0.f));
+  near = fabsf(tx - ty) < kTieWindow || fabsf(tx - tz) < kTieWindow || fabsf(ty - tz) < kTieWindow ||
+         tmax > 1.f - kTieWindow;
+  e.m = (int)cx + (int)cy + (int)cz;
+  e.t0 = fminf(tx, fminf(ty, tz));
+  e.t1 = fmaxf(fminf(tx, ty), fminf(fmaxf(tx, ty), tz));  // the median: the second event when m >= 2
+  e.t2 = tmax;
+  e.n0 = e.t0;  // > 0 exactly when the distance to the first face is
+  e.tpos = true;
+  const int sx = ux ? 1 : -1, sy = uy ? 1 : -1, sz = uz ? 1 : -1;
+  const bool ex0 = tx == e.t0, ey0 = !ex0 && ty == e.t0, ez0 = !ex0 && !ey0;
+  const bool ex1 = tx == e.t1, ey1 = !ex1 && ty == e.t1, ez1 = !ex1 && !ey1;
+  e.s0x = ex0 ? sx : 0;
+  e.s0y = ey0 ? sy : 0;
+  e.s0z = ez0 && cz ? sz : 0;
+  e.s1x = ex1 ? sx : 0;
+  e.s1y = ey1 ? sy : 0;
+  e.s1z = ez1 && cz ? sz : 0;
+  return e;
+}
+
 __device__ __forceinline__ bool in_grid(const Geo& g, int ix, int iy, int iz) {
   return (unsigned)ix < (unsigned)g.nx && (unsigned)iy < (unsigned)g.ny && (unsigned)iz < (unsigned)g.nz;
 }
@@ -170,7 +210,9 @@ __device__ __forceinline__ int group_walk_fast(const Group<T>& G, const Geo& g, 
                 fz = __fmul_rn(__fsub_rn(Q.z, P.z), g.hz);
     const float L2 = __fmaf_rn(fx, fx, __fmaf_rn(fy, fy, __fmul_rn(fz, fz)));
     const float L = act ? L2 * rsqrtf(L2) : 0.f;
-    SegEv e = seg_events(P, Q);
+    bool near;
+    SegEv e = seg_events_float(P, Q, near);
+    if (G.ballot(act && near)) e = seg_events(P, Q);  // a near tie somewhere in the step: exact order
     if (!act) e.m = 0;
     const float tl = e.m == 1 ? e.t0 : (e.m == 2 ? e.t1 : e.t2);
     const float w = e.m > 0 ? (1.f - tl) * L : L;  // the piece after the last event (or the whole segment)

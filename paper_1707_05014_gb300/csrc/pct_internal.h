@@ -20,6 +20,8 @@ constexpr int kMaxNodes = 2048;          // K + 1 limit (shared-memory MLP table
 constexpr int kMaxDim = 512;             // per-axis voxel limit
 constexpr int kSortAngles = 256;         // load-time ordering: gantry-angle bins
 constexpr int kSortLateral = 4096;       // load-time ordering: mid-path lateral-position bins
+// entries of the ordering's bin array: the bins, then one sum per scan tile
+constexpr int64_t kSortHistEntries = (int64_t)kSortAngles * kSortLateral + 1024;
 constexpr int kRowCap = 512;             // runs kept per history between the fused kernel's two passes
 constexpr int kGroupRowCap = 384;        // runs kept in shared memory per history by the group kernel
 
@@ -129,7 +131,8 @@ cudaError_t launch_validate(const Rec& r, int64_t n, int64_t base, float pos_lim
                             cudaStream_t s);
 // Order n records of one block by (angle bin, entry lateral bin) into
 // dst_rec[base .. base+n); where[base + i] receives the stored position of
-// input record i (where may be null). key/order: n entries; hist: bins.
+// input record i (where may be null). key/order: n entries; hist:
+// kSortHistEntries (the bins and the scan's tile sums).
 cudaError_t launch_sort_block(const Rec& src, int64_t n, int64_t base, float lat_lim, Rec dst_rec, int64_t* where,
                               unsigned* key, unsigned* hist, unsigned* order, cudaStream_t s);
 // Copy n records into dst_rec[base ..) in input order (where as above).

@@ -411,31 +411,87 @@ __global__ void histogram_kernel(const unsigned* __restrict__ key, int64_t n, un
   atomicAdd(hist + key[i], 1u);
 }
 
-// exclusive scan of hist[0..nb) in place, one CTA of 1024 threads
-__global__ void __launch_bounds__(1024) scan_bins_kernel(unsigned* __restrict__ hist, int nb) {
-  __shared__ unsigned sums[1024];
-  const int t = threadIdx.x;
-  const int per = (nb + 1023) / 1024;
-  const int lo = min(t * per, nb), hi = min(lo + per, nb);
-  unsigned s = 0;
-  for (int i = lo; i < hi; ++i) s += hist[i];
-  sums[t] = s;
+// Exclusive scan of hist[0..nb) in place, in three launches: every CTA sums
+// one tile of kScanTile bins (coalesced), one CTA scans the tile sums, and
+// every CTA scans its tile from its offset. kScanThreads threads, each
+// holding kScanTile / kScanThreads consecutive bins.
+constexpr int kScanThreads = 256;
+constexpr int kScanPer = 16;
+constexpr int kScanTile = kScanThreads * kScanPer;  // 4096 bins
+constexpr int kScanMaxTiles = 1024;                 // nb <= 4M bins
+
+__device__ __forceinline__ unsigned block_excl_scan(unsigned v, unsigned* sh, unsigned& total) {
+  // Hillis-Steele over the warp, then over the warp sums
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  unsigned x = v;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const unsigned y = __shfl_up_sync(0xffffffffu, x, d);
+    if (lane >= d) x += y;
+  }
+  if (lane == 31) sh[w] = x;
   __syncthreads();
-  if (t == 0) {
-    unsigned acc = 0;
-    for (int q = 0; q < 1024; ++q) {
-      unsigned w = sums[q];
-      sums[q] = acc;
-      acc += w;
+  if (w == 0) {
+    const int nw = blockDim.x >> 5;
+    unsigned s = lane < nw ? sh[lane] : 0u;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const unsigned y = __shfl_up_sync(0xffffffffu, s, d);
+      if (lane >= d) s += y;
     }
+    if (lane < nw) sh[lane] = s;
   }
   __syncthreads();
-  unsigned acc = sums[t];
-  for (int i = lo; i < hi; ++i) {
-    unsigned w = hist[i];
-    hist[i] = acc;
-    acc += w;
+  total = sh[(blockDim.x >> 5) - 1];
+  const unsigned before = w > 0 ? sh[w - 1] : 0u;
+  __syncthreads();
+  return before + x - v;
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_tile_sums_kernel(const unsigned* __restrict__ hist, int nb,
+                                                                      unsigned* __restrict__ tile_sum) {
+  __shared__ unsigned sh[32];
+  const int base = blockIdx.x * kScanTile;
+  unsigned s = 0;
+  for (int q = threadIdx.x; q < kScanTile; q += kScanThreads)
+    if (base + q < nb) s += hist[base + q];
+  unsigned total;
+  block_excl_scan(s, sh, total);
+  if (threadIdx.x == 0) tile_sum[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(kScanMaxTiles) scan_tile_offsets_kernel(unsigned* __restrict__ tile_sum, int nt) {
+  __shared__ unsigned sh[32];
+  const unsigned v = threadIdx.x < nt ? tile_sum[threadIdx.x] : 0u;
+  unsigned total;
+  const unsigned ex = block_excl_scan(v, sh, total);
+  if (threadIdx.x < nt) tile_sum[threadIdx.x] = ex;
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_tiles_kernel(unsigned* __restrict__ hist, int nb,
+                                                                  const unsigned* __restrict__ tile_off) {
+  __shared__ unsigned tile[kScanTile];
+  __shared__ unsigned sh[32];
+  const int base = blockIdx.x * kScanTile;
+  for (int q = threadIdx.x; q < kScanTile; q += kScanThreads) tile[q] = base + q < nb ? hist[base + q] : 0u;
+  __syncthreads();
+  unsigned v[kScanPer];
+  unsigned s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanPer; ++k) {
+    v[k] = tile[threadIdx.x * kScanPer + k];
+    s += v[k];
   }
+  unsigned total;
+  unsigned acc = tile_off[blockIdx.x] + block_excl_scan(s, sh, total);
+#pragma unroll
+  for (int k = 0; k < kScanPer; ++k) {
+    tile[threadIdx.x * kScanPer + k] = acc;
+    acc += v[k];
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < kScanTile; q += kScanThreads)
+    if (base + q < nb) hist[base + q] = tile[q];
 }
 
 __global__ void scatter_kernel(const unsigned* __restrict__ key, int64_t n, unsigned* __restrict__ offs,
@@ -483,7 +539,15 @@ cudaError_t launch_sort_block(const Rec& src, int64_t n, int64_t base, float lat
   if (e != cudaSuccess) return e;
   sort_key_kernel<<<grid_for(n, 256), 256, 0, s>>>(src, n, n_ang, n_lat, lat_lim, key);
   histogram_kernel<<<grid_for(n, 256), 256, 0, s>>>(key, n, hist);
-  scan_bins_kernel<<<1, 1024, 0, s>>>(hist, n_ang * n_lat);
+  {
+    const int nb = n_ang * n_lat, nt = (nb + kScanTile - 1) / kScanTile;
+    static_assert((kSortAngles * kSortLateral + kScanTile - 1) / kScanTile <= kScanMaxTiles, "bins exceed the scan");
+    unsigned* tile_sum = hist + nb;  // nt entries past the bins (the array holds kSortHistEntries)
+    static_assert(kSortHistEntries >= (int64_t)kSortAngles * kSortLateral + kScanMaxTiles, "bin array too small");
+    scan_tile_sums_kernel<<<nt, kScanThreads, 0, s>>>(hist, nb, tile_sum);
+    scan_tile_offsets_kernel<<<1, kScanMaxTiles, 0, s>>>(tile_sum, nt);
+    scan_tiles_kernel<<<nt, kScanThreads, 0, s>>>(hist, nb, tile_sum);
+  }
   scatter_kernel<<<grid_for(n, 256), 256, 0, s>>>(key, n, hist, order);
   RecOut d{const_cast<float*>(dst_rec.t0), const_cast<float*>(dst_rec.v0), const_cast<float*>(dst_rec.st0),
            const_cast<float*>(dst_rec.sv0), const_cast<float*>(dst_rec.t2), const_cast<float*>(dst_rec.v2),

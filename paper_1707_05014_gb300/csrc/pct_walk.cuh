@@ -396,30 +396,14 @@ __device__ __forceinline__ void emit_fast(const Geo& g, FastState& s, Visit& vis
   s.pos = false;
 }
 
-// Advance the fast walk from s.qP to the next node q.
+// Crossings of one fast-walk segment ordered exactly (two-product
+// comparisons; tied axes step together). rx/ry/rz: the axes that cross, xa..:
+// crossing upwards; nd*: exact distance to the crossed face, dd*: exact axis
+// length of the segment.
 template <class Visit>
-__device__ __forceinline__ void seg_fast(const Geo& g, FastState& s, const float3 q, Visit& visit) {
-  const float dx = __fsub_rn(q.x, s.qP.x), dy = __fsub_rn(q.y, s.qP.y), dz = __fsub_rn(q.z, s.qP.z);
-  const float fx = __fmul_rn(dx, g.hx), fy = __fmul_rn(dy, g.hy), fz = __fmul_rn(dz, g.hz);
-  // The nodes of a validated record are at least du / sqrt(2) apart in x or
-  // y (du >= 2R/2047), far above the float spacing, so L2 > 0.
-  const float L2 = __fmaf_rn(fx, fx, __fmaf_rn(fy, fy, __fmul_rn(fz, fz)));
-  const float L = L2 * rsqrtf(L2);
-  const float ux = s.lx + 1.f, uy = s.ly + 1.f, uz = s.lz + 1.f;  // upper faces
-  const bool xa = q.x >= ux, xb = q.x < s.lx;  // half-open voxels: a face reached moving up is crossed
-  const bool ya = q.y >= uy, yb = q.y < s.ly;
-  const bool za = q.z >= uz, zb = q.z < s.lz;
-  if (!(xa | xb | ya | yb | za | zb)) {
-    s.run += L;  // the segment moves, so the run's extent is positive
-    s.pos = true;
-    s.qP = q;
-    return;
-  }
-  bool rx = xa | xb, ry = ya | yb, rz = za | zb;  // crossings still to take
-  // exact distance to the crossed face and exact axis length of the segment
-  const float ndx = xa ? __fsub_rn(ux, s.qP.x) : __fsub_rn(s.qP.x, s.lx), ddx = fabsf(dx);
-  const float ndy = ya ? __fsub_rn(uy, s.qP.y) : __fsub_rn(s.qP.y, s.ly), ddy = fabsf(dy);
-  const float ndz = za ? __fsub_rn(uz, s.qP.z) : __fsub_rn(s.qP.z, s.lz), ddz = fabsf(dz);
+__device__ __forceinline__ void seg_fast_exact(const Geo& g, FastState& s, float L, bool rx, bool ry, bool rz, bool xa,
+                                            bool ya, bool za, float ndx, float ndy, float ndz, float ddx, float ddy,
+                                            float ddz, Visit& visit) {
   // exact pairwise order of the crossings (< 0: the first axis crosses first)
   const int oxy = rx && ry ? cmp_prod(ndx, ddy, ndy, ddx) : 0;
   const int oxz = rx && rz ? cmp_prod(ndx, ddz, ndz, ddx) : 0;
@@ -458,6 +442,79 @@ __device__ __forceinline__ void seg_fast(const Geo& g, FastState& s, const float
   }
   s.run += (1.f - tl) * L;
   s.pos |= nl < dl;  // the last crossing lies before the node
+}
+
+// Crossing fractions closer than this to each other (or to the segment's
+// end) are ordered by the exact comparison: __fdividef is within 2 ulp
+// (< 1.2e-7 on [0, 1]), so fractions further apart order as the exact ones.
+constexpr float kTieWindow = 4e-7f;
+
+// Advance the fast walk from s.qP to the next node q.
+template <class Visit>
+__device__ __forceinline__ void seg_fast(const Geo& g, FastState& s, const float3 q, Visit& visit) {
+  const float dx = __fsub_rn(q.x, s.qP.x), dy = __fsub_rn(q.y, s.qP.y), dz = __fsub_rn(q.z, s.qP.z);
+  const float fx = __fmul_rn(dx, g.hx), fy = __fmul_rn(dy, g.hy), fz = __fmul_rn(dz, g.hz);
+  // The nodes of a validated record are at least du / sqrt(2) apart in x or
+  // y (du >= 2R/2047), far above the float spacing, so L2 > 0.
+  const float L2 = __fmaf_rn(fx, fx, __fmaf_rn(fy, fy, __fmul_rn(fz, fz)));
+  const float L = L2 * rsqrtf(L2);
+  const float ux = s.lx + 1.f, uy = s.ly + 1.f, uz = s.lz + 1.f;  // upper faces
+  const bool xa = q.x >= ux, xb = q.x < s.lx;  // half-open voxels: a face reached moving up is crossed
+  const bool ya = q.y >= uy, yb = q.y < s.ly;
+  const bool za = q.z >= uz, zb = q.z < s.lz;
+  if (!(xa | xb | ya | yb | za | zb)) {
+    s.run += L;  // the segment moves, so the run's extent is positive
+    s.pos = true;
+    s.qP = q;
+    return;
+  }
+  const bool rx = xa | xb, ry = ya | yb, rz = za | zb;  // crossings to take
+  // exact distance to the crossed face and exact axis length of the segment
+  const float ndx = xa ? __fsub_rn(ux, s.qP.x) : __fsub_rn(s.qP.x, s.lx), ddx = fabsf(dx);
+  const float ndy = ya ? __fsub_rn(uy, s.qP.y) : __fsub_rn(s.qP.y, s.ly), ddy = fabsf(dy);
+  const float ndz = za ? __fsub_rn(uz, s.qP.z) : __fsub_rn(s.qP.z, s.lz), ddz = fabsf(dz);
+  float tx = rx ? __fdividef(ndx, ddx) : INFINITY;
+  float ty = ry ? __fdividef(ndy, ddy) : INFINITY;
+  float tz = rz ? __fdividef(ndz, ddz) : INFINITY;
+  // near ties, and crossings at the node itself, take the exact order
+  const float tmax = fmaxf(rx ? tx : 0.f, fmaxf(ry ? ty : 0.f, rz ? tz : 0.f));
+  const bool near = fabsf(tx - ty) < kTieWindow || fabsf(tx - tz) < kTieWindow || fabsf(ty - tz) < kTieWindow ||
+                    tmax > 1.f - kTieWindow;
+  if (near) {
+    seg_fast_exact(g, s, L, rx, ry, rz, xa, ya, za, ndx, ndy, ndz, ddx, ddy, ddz, visit);
+    s.qP = q;
+    return;
+  }
+  // distinct fractions: the float order is the exact order, one axis per event
+  float tl = 0.f;
+  bool first = true;
+  for (;;) {
+    const float m = fminf(tx, fminf(ty, tz));
+    if (m == INFINITY) break;
+    s.run += (m - tl) * L;
+    s.pos |= !first || m > 0.f;  // m > 0 exactly when the distance to the face is
+    emit_fast(g, s, visit);
+    const bool mx = tx == m, my = !mx && ty == m, mz = !mx && !my;
+    if (mx) {
+      s.cx += xa ? 1 : -1;
+      s.lx += xa ? 1.f : -1.f;
+      tx = INFINITY;
+    }
+    if (my) {
+      s.cy += ya ? 1 : -1;
+      s.ly += ya ? 1.f : -1.f;
+      ty = INFINITY;
+    }
+    if (mz) {
+      s.cz += za ? 1 : -1;
+      s.lz += za ? 1.f : -1.f;
+      tz = INFINITY;
+    }
+    tl = m;
+    first = false;
+  }
+  s.run += (1.f - tl) * L;
+  s.pos = true;  // the last crossing lies more than the tie window before the node
   s.qP = q;
 }
 

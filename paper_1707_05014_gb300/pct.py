@@ -448,7 +448,8 @@ BATCH_GRAPH_BRANCHES = 2
 
 class BatchConfig(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("branches", ctypes.c_int32), ("chunk", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("apply_tiles", ctypes.c_int32),
-                ("wait_limit_s", ctypes.c_double), ("debug_unreachable_wait", ctypes.c_int32)]
+                ("wait_limit_s", ctypes.c_double), ("debug_unreachable_wait", ctypes.c_int32),
+                ("lanes", ctypes.c_int32)]
 
 
 class Batch:
@@ -457,13 +458,13 @@ class Batch:
 
     def __init__(self, contexts, mode: int = BATCH_GRAPH_BRANCHES, branches: int = 0, chunk: int = 0,
                  ctas_per_sm: int = 0, apply_tiles: int = 0, wait_limit_s: float = 0.0,
-                 debug_unreachable_wait: bool = False):
+                 debug_unreachable_wait: bool = False, lanes: int = 0):
         L = load_library()
         self._L = L
         self.contexts = list(contexts)
         arr = (ctypes.c_void_p * len(self.contexts))(*[c._h.value for c in self.contexts])
         self.cfg = BatchConfig(int(mode), int(branches), int(chunk), int(ctas_per_sm), int(apply_tiles),
-                               float(wait_limit_s), 1 if debug_unreachable_wait else 0)
+                               float(wait_limit_s), 1 if debug_unreachable_wait else 0, int(lanes))
         h = ctypes.c_void_p()
         _check(L.pct_batch_create(ctypes.byref(h), arr, len(self.contexts), ctypes.byref(self.cfg)))
         self._h = h
@@ -497,7 +498,7 @@ class Batch:
         _check(self._L.pct_batch_autotune(self._h, ctypes.byref(chosen), ctypes.byref(ms)))
         return {"mode": "persistent" if chosen.mode == BATCH_PERSISTENT else "graph_branches",
                 "branches": chosen.branches, "chunk": chosen.chunk, "ctas_per_sm": chosen.ctas_per_sm,
-                "apply_tiles": chosen.apply_tiles, "sweep_ms": ms.value}
+                "apply_tiles": chosen.apply_tiles, "lanes": chosen.lanes, "sweep_ms": ms.value}
 
     @property
     def launches(self) -> int:

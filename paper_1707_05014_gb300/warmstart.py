@@ -116,23 +116,74 @@ def solve_to_target(ctx: P.Context, x_true: np.ndarray, grid: S.Grid, target: fl
     timed(lambda: ctx.iterate(1))
     sweeps = 1
     if net is not None:
-        def warm():
-            x1 = ctx.get_rsp(device=True)
-            r1 = ctx.residual(check_stride)  # a 1/64 sample of the histories
-            x0 = net.forward(x1)
-            ctx.set_x0(x0)
-            r0 = ctx.residual(check_stride)
-            if r0 > r1:  # fallback: the plain solver's image is better
-                ctx.set_x0(x1)
-                return False
-            return True
-        used_net = timed(warm)
+        used_net = timed(lambda: warm_start(ctx, net, check_stride))
     errs.append(err())
     while errs[-1] > target and sweeps < max_sweeps:
         timed(lambda: ctx.iterate(1))
         sweeps += 1
         errs.append(err())
     return {"reached": errs[-1] <= target, "sweeps": sweeps, "ms": t_ms, "errors": errs, "net_used": used_net}
+
+
+def warm_start(ctx: P.Context, net: P.Net, check_stride: int = 64) -> bool:
+    """Steps 2-3 of the solve on one context after its first sweep: x0 = x1 +
+    f(x1), kept only if its data residual on every check_stride-th history is
+    not larger than that of x1. Returns whether the network's image is kept."""
+    x1 = ctx.get_rsp(device=True)
+    r1 = ctx.residual(check_stride)
+    ctx.set_x0(net.forward(x1))
+    r0 = ctx.residual(check_stride)
+    if r0 > r1:  # fallback: the plain solver's image is better
+        ctx.set_x0(x1)
+        return False
+    return True
+
+
+def solve_batch_to_target(batch: P.Batch, ctxs: Sequence[P.Context], x_trues: Sequence[np.ndarray],
+                          grid: S.Grid, target: float, max_sweeps: int, net: Optional[P.Net] = None,
+                          check_stride: int = 64) -> Dict:
+    """solve_to_target for several reconstructions advanced together by one
+    batch (pct_batch_iterate): every sweep is one batched call over all of
+    them; with a network, each reconstruction is warm-started (with its own
+    residual fallback) after the first sweep. Sweeps continue until every
+    reconstruction's mean RSP error is <= target. Times the GPU work with CUDA
+    events; the error evaluation is outside the timed region."""
+    import torch
+
+    stream = torch.cuda.current_stream()
+    t_ms = 0.0
+
+    def timed(fn):
+        nonlocal t_ms
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_ms += e0.elapsed_time(e1)
+        return out
+
+    def errs_now():
+        return [S.mean_rsp_error(c.get_rsp().astype(np.float64), xt, grid) for c, xt in zip(ctxs, x_trues)]
+
+    def sweep():
+        batch.iterate(1)
+        batch.sync()
+
+    timed(sweep)
+    sweeps = 1
+    used = [False] * len(ctxs)
+    if net is not None:
+        used = timed(lambda: [warm_start(c, net, check_stride) for c in ctxs])
+    errs = [errs_now()]
+    while max(errs[-1]) > target and sweeps < max_sweeps:
+        timed(sweep)
+        sweeps += 1
+        errs.append(errs_now())
+    per = [next((k + 1 for k, e in enumerate(errs) if e[r] <= target), None) for r in range(len(ctxs))]
+    return {"reached": max(errs[-1]) <= target, "sweeps": sweeps, "ms": t_ms, "sweeps_to_target": per,
+            "errors": [[e[r] for e in errs] for r in range(len(ctxs))], "net_used": used}
 
 
 def pick_blocks(trial: Callable[[int, Optional[float]], Optional[float]], candidates: Sequence[int]) -> Tuple[int, Dict]:

@@ -1,5 +1,6 @@
 """Batched persistent launch: several reconstructions of uneven size advance in
-one launch per call; each result equals its own context's pct_iterate and the
+one launch per call (or as graph branches of per-block kernels, with one lane
+or a group of lanes per history); each result equals its own context's pct_iterate and the
 FP64 oracle's DROP (the same stages, Sec. 2.1 / Fig. 1) up to summation order,
 element by element within the 0.1 % RSP bar, and a bounded wait
 that cannot be met ends the launch with PCT_ERR_TIMEOUT instead of a hang."""
@@ -43,8 +44,8 @@ def oracle_images(oracle):
     return recs, [oracle.drop(w.grid, r, B, 2, mode=oracle.MODE_FP32) for (w, B), r in zip(wls, recs)]
 
 
-@pytest.mark.parametrize("mode,chunk", [(1, 0), (1, 1000), (2, 0)])
-def test_batch_matches_individual_contexts(P, oracle_images, mode, chunk):
+@pytest.mark.parametrize("mode,chunk,lanes", [(1, 0, 0), (1, 1000, 0), (2, 0, 0), (2, 0, 32), (2, 0, 8)])
+def test_batch_matches_individual_contexts(P, oracle_images, mode, chunk, lanes):
     wls = _workloads()
     recs, oracle_x = oracle_images
     refs = []
@@ -58,7 +59,7 @@ def test_batch_matches_individual_contexts(P, oracle_images, mode, chunk):
         c = P.Context(w.grid, n_blocks=B)
         c.load(r)
         ctxs.append(c)
-    with P.Batch(ctxs, mode=mode, chunk=chunk) as b:
+    with P.Batch(ctxs, mode=mode, chunk=chunk, lanes=lanes) as b:
         b.iterate(1)
         b.iterate(1)
         b.sync()
@@ -84,6 +85,7 @@ def test_batch_autotune_keeps_results(P):
     with P.Batch(ctxs) as b:
         choice = b.autotune()
         assert choice["mode"] in ("persistent", "graph_branches") and choice["sweep_ms"] > 0
+        assert choice["lanes"] in (1, 16, 32)
         for c in ctxs:  # autotuning restores x
             assert float(np.abs(c.get_rsp()).max()) == 0.0
         b.iterate(1)

@@ -24,29 +24,71 @@ def mods():
     return pct, warmstart
 
 
-def test_warm_start_beats_plain_solver(mods):
+GRID = S.Grid(64, 64, 32, 3.125, 3.125, 3.125)
+N_HIST, SWEEPS = 3_000_000, 8
+
+
+@pytest.fixture(scope="module")
+def trained(mods):
     P, W = mods
-    g = S.Grid(64, 64, 32, 3.125, 3.125, 3.125)
-    n, sweeps = 3_000_000, 8
-    pairs = W.make_training_pairs(g, 32, n, sweeps, seed0=500)
-    with P.Net(g.nz, g.ny, g.nx, seed=1) as net:
-        hist = W.train(net, pairs, epochs=40, lr=2e-3)
-        assert hist[-1] < hist[0]
-        gains = []
-        for seed in (900, 901):
-            wl = W.head_workload(g, n, seed)
-            x_true = S.voxelize(wl.phantom(), g, ss=2)
-            rec = S.make_histories(wl)
-            res = {}
-            for name, use in (("plain", None), ("warm", net)):
-                with P.Context(g, n_blocks=wl.n_blocks) as ctx:
-                    ctx.load(rec)
-                    res[name] = W.solve_to_target(ctx, x_true, g, 0.0, sweeps, net=use)
-            plain, warm = res["plain"]["errors"], res["warm"]["errors"]
-            print(seed, "plain", np.round(plain, 4), "warm", np.round(warm, 4), res["warm"]["net_used"])
-            # the warm-started solve stays ahead of the plain solver sweep by
-            # sweep, and its first image is about as good as two plain sweeps
-            assert all(w < p for w, p in zip(warm[:4], plain[:4]))
-            assert warm[0] <= 1.15 * plain[1]
-            gains.append((plain[:4], warm[:4]))
+    pairs = W.make_training_pairs(GRID, 32, N_HIST, SWEEPS, seed0=500)
+    net = P.Net(GRID.nz, GRID.ny, GRID.nx, seed=1)
+    hist = W.train(net, pairs, epochs=40, lr=2e-3)
+    yield net, hist
+    net.close()
+
+
+def test_warm_start_beats_plain_solver(mods, trained):
+    P, W = mods
+    g = GRID
+    n, sweeps = N_HIST, SWEEPS
+    net, hist = trained
+    assert hist[-1] < hist[0]
+    gains = []
+    for seed in (900, 901):
+        wl = W.head_workload(g, n, seed)
+        x_true = S.voxelize(wl.phantom(), g, ss=2)
+        rec = S.make_histories(wl)
+        res = {}
+        for name, use in (("plain", None), ("warm", net)):
+            with P.Context(g, n_blocks=wl.n_blocks) as ctx:
+                ctx.load(rec)
+                res[name] = W.solve_to_target(ctx, x_true, g, 0.0, sweeps, net=use)
+        plain, warm = res["plain"]["errors"], res["warm"]["errors"]
+        print(seed, "plain", np.round(plain, 4), "warm", np.round(warm, 4), res["warm"]["net_used"])
+        # the warm-started solve stays ahead of the plain solver sweep by
+        # sweep, and its first image is about as good as two plain sweeps
+        assert all(w < p for w, p in zip(warm[:4], plain[:4]))
+        assert warm[0] <= 1.15 * plain[1]
+        gains.append((plain[:4], warm[:4]))
     print("warm-start gains:", gains)
+
+
+def test_batched_warm_start_reaches_the_target_in_fewer_sweeps(mods, trained):
+    """Several reconstructions of uneven size advanced by one batch: with the
+    network (each with its own residual fallback) every one reaches the plain
+    batch's three-sweep error in fewer sweeps than the plain batch takes."""
+    P, W = mods
+    net, _ = trained
+    g = GRID
+    wls = [W.head_workload(g, n, seed) for n, seed in ((3_000_000, 910), (1_500_000, 911), (800_000, 912))]
+    recs = [S.make_histories(w) for w in wls]
+    truths = [S.voxelize(w.phantom(), g, ss=2) for w in wls]
+    runs = {}
+    for name, use in (("plain", None), ("warm", net)):
+        ctxs = []
+        for w, r in zip(wls, recs):
+            c = P.Context(g, n_blocks=w.n_blocks)
+            c.load(r)
+            ctxs.append(c)
+        with P.Batch(ctxs, mode=P.BATCH_GRAPH_BRANCHES) as b:
+            runs[name] = W.solve_batch_to_target(b, ctxs, truths, g, 0.0, 4, net=use)
+        for c in ctxs:
+            c.close()
+    plain, warm = runs["plain"], runs["warm"]
+    print("plain", np.round(plain["errors"], 4), "warm", np.round(warm["errors"], 4), warm["net_used"])
+    assert all(warm["net_used"])
+    for r in range(len(wls)):
+        target = plain["errors"][r][2]  # the plain batch after three sweeps
+        reach = next(k for k, e in enumerate(warm["errors"][r]) if e <= target)
+        assert reach < 2, (r, warm["errors"][r], target)  # within two sweeps with the network
