@@ -260,6 +260,24 @@ def run_batched(args):
         total += w.n
         ctxs.append(c)
     torch.cuda.empty_cache()
+
+    def sweep_ms(**kw):
+        """ms per batched sweep (after one warm-up sweep) of one batch mode."""
+        with P.Batch(ctxs, **kw) as bb:
+            bb.iterate(1)
+            bb.sync()
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            a0.record(torch.cuda.current_stream())
+            bb.iterate(2)
+            a1.record(torch.cuda.current_stream())
+            bb.sync()
+            return a0.elapsed_time(a1) / 2
+
+    # both modes at their defaults, measured side by side (the sweeps change x,
+    # which does not change the work of a sweep)
+    modes = {"persistent_ms": sweep_ms(mode=P.BATCH_PERSISTENT), "graph_branches_ms": sweep_ms(mode=P.BATCH_GRAPH_BRANCHES),
+             "graph_branches_32_lanes_ms": sweep_ms(mode=P.BATCH_GRAPH_BRANCHES, lanes=32)}
     batch = P.Batch(ctxs)
     tune = batch.autotune()
     stream = torch.cuda.current_stream()
@@ -304,7 +322,7 @@ def run_batched(args):
                        "parallelism": f"replicas{world}"},
             "roofline": {"kernel": "batch_kernel", "bound": "alu", "achieved": achieved, "peak": alu_peak,
                          "unit": "Tops/s", "frac": achieved / alu_peak, "traffic": None},
-            "autotune": tune, "sequential_contexts_value": total / (seq_ms / 1e3),
+            "autotune": tune, "modes_ms_per_sweep": modes, "sequential_contexts_value": total / (seq_ms / 1e3),
             "gpu_launches": launches, "clocks": clk,
         }
         print(json.dumps(line), flush=True)
@@ -420,10 +438,41 @@ def time_to_image(args, local: int, log) -> dict:
             log(f"test {k} {name}: {r[name]}")
         ctx.close()
         results.append(r)
+    # the warm-started, batched form: several held-out heads of uneven size
+    # advanced by one batch (graph branches), plain against warm-started
+    batched = None
+    sizes = [int(float(v)) for v in args.ws_batch.split(",") if v.strip()] if args.ws_batch else []
+    if sizes:
+        wls = [W.head_workload(g, n, 6000 + k, n_blocks=args.ws_blocks) for k, n in enumerate(sizes)]
+        truths = [S.voxelize(w.phantom(), g, ss=2) for w in wls]
+        ctxs = []
+        for w in wls:
+            rec = S.make_histories_device(w, device=f"cuda:{local}")
+            c = P.Context(g, n_blocks=w.n_blocks, device=local, lanes=args.lanes)
+            c.load(rec)
+            del rec
+            torch.cuda.empty_cache()
+            ctxs.append(c)
+        zero = np.zeros(g.m, dtype=np.float32)
+        batched = {"histories": sizes}
+        with P.Batch(ctxs, mode=P.BATCH_GRAPH_BRANCHES) as b:
+            for name, use in (("plain", None), ("warm", net)):
+                for c in ctxs:
+                    c.set_x0(zero)
+                batched[name] = W.solve_batch_to_target(b, ctxs, truths, g, args.ws_target, args.ws_max_sweeps,
+                                                        net=use)
+                log(f"batch {name}: {batched[name]}")
+        for c in ctxs:
+            c.close()
+        for name in ("plain", "warm"):
+            batched[name + "_seconds"] = batched[name]["ms"] / 1e3 if batched[name]["reached"] else None
+        if batched["plain_seconds"] and batched["warm_seconds"]:
+            batched["speedup"] = batched["plain_seconds"] / batched["warm_seconds"]
     net.close()
     plain_ms = [r["plain"]["ms"] for r in results if r["plain"]["reached"]]
     warm_ms = [r["warm"]["ms"] for r in results if r["warm"]["reached"]]
     return {
+        "batched": batched,
         "metric": "time-to-image at <=1% mean RSP error", "unit": "s", "higher_is_better": False,
         "warm_seconds": statistics.mean(warm_ms) / 1e3 if warm_ms else None,
         "plain_seconds": statistics.mean(plain_ms) / 1e3 if plain_ms else None,
@@ -452,7 +501,8 @@ def run_warmstart(args):
     line = {"metric": tti["metric"], "value": tti["warm_seconds"], "unit": "s", "n_gpus": 1,
             "higher_is_better": False, "data": "synthetic", "dtype": "f32", "config": tti["config"],
             "plain_seconds": tti["plain_seconds"], "speedup": tti["speedup"],
-            **{k: tti[k] for k in ("tests", "train_loss", "training_data_s", "training_s", "blocks_tuning")}}
+            **{k: tti[k] for k in ("tests", "train_loss", "training_data_s", "training_s", "blocks_tuning",
+                                   "batched")}}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -647,7 +697,7 @@ def run_ours(args):
         log = lambda m: print(m, file=sys.stderr, flush=True)  # noqa: E731
         full = time_to_image(args, local, log)
         tti = {k: full[k] for k in ("metric", "unit", "higher_is_better", "warm_seconds", "plain_seconds", "speedup",
-                                    "config", "training_data_s", "training_s")}
+                                    "config", "training_data_s", "training_s", "batched")}
         tti["tests"] = [{"seed": r["seed"], **{m: {"seconds": r[m]["ms"] / 1e3, "sweeps": r[m]["sweeps"],
                                                    "reached": r[m]["reached"], "errors": r[m]["errors"],
                                                    **({"net_used": r[m]["net_used"]} if m == "warm" else {})}
@@ -725,6 +775,8 @@ def main():
     ap.add_argument("--ws-test-n", type=int, default=1_000_000_000)
     ap.add_argument("--ws-target", type=float, default=0.01)
     ap.add_argument("--ws-max-sweeps", type=int, default=10)
+    ap.add_argument("--ws-batch", default="1e9,5e8,2.5e8",
+                    help="histories of the held-out heads solved together as one batch ('' to skip)")
     ap.add_argument("--n-recon", type=int, default=32, help="reconstructions of the batched workload")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -400,6 +400,33 @@ PCT_API pct_status pct_net_gradients(pct_net *net, const float *x1, const float 
 PCT_API pct_status pct_net_train_step(pct_net *net, const float *x1, const float *target, float *x0_scratch,
                                       float lr, double *loss, void *stream);
 
+/* One layer of the network on the caller's DEVICE data, through the same
+ * kernels as pct_net_forward / pct_net_gradients (for checking them layer by
+ * layer). Layer l (0..14) has Cin, Cout channels and input / output grids at
+ * the levels of the topology above (level 0: nz x ny x nx, each further level
+ * halves every dimension); activations and gradients are BF16 (uint16 bit
+ * patterns), channels last: [voxel][channel]. Weights and biases are the
+ * net's current parameters.
+ *   PCT_NET_FORWARD (l = 0..13): out[vox_out][Cout] = bf16(relu(conv(in) +
+ *     bias + skip)); skip is the [vox_out][Cout] input of the additive skip of
+ *     layers 8, 10 and 12, NULL for the others.
+ *   PCT_NET_DATA_GRAD (l = 1..14): out[vox_in][Cin] = bf16((conv^T(dy) + add)
+ *     * [mask > 0]); dy: [vox_out][Cout] gradient of layer l's pre-activation;
+ *     mask: layer l-1's stored activation; add: the skip gradient into layer
+ *     l-1's output (may be NULL; must be NULL for the up-convolutions 8, 10, 12).
+ *   PCT_NET_WEIGHT_GRAD (l = 0..14): out = float[27*Cin*Cout + Cout], dW
+ *     [tap][ci][co] then db, from the layer's input `in` and `dy` (zeroed
+ *     first).
+ * Asynchronous on `stream` (NULL = the network's own stream). */
+/* Channels (padded) and grid levels of layer l's input and output. */
+PCT_API pct_status pct_net_layer_shape(const pct_net *net, int32_t layer, int32_t *cin, int32_t *cout,
+                                       int32_t *in_level, int32_t *out_level);
+#define PCT_NET_FORWARD 0
+#define PCT_NET_DATA_GRAD 1
+#define PCT_NET_WEIGHT_GRAD 2
+PCT_API pct_status pct_net_layer(pct_net *net, int32_t layer, int32_t op, const void *in, const void *skip,
+                                 const void *dy, const void *mask, const void *add, void *out, void *stream);
+
 /* One DROP block update that allocates no device or host memory, for callers
  * that cannot allocate once they run (services that reserve all GPU memory
  * at start-up for a fixed plan, plugins whose host application owns every

@@ -289,6 +289,67 @@ def loss_and_grads(p: np.ndarray, x1: np.ndarray, target: np.ndarray, bf16: bool
     return loss, pack(grads), pack(core), pack(rel)
 
 
+def _layer_conv(kind, h, W, b):
+    if kind == "s1":
+        return conv(h, W, b, 1)
+    if kind == "s2":
+        return conv(h, W, b, 2)
+    return conv(up2(h), W, b, 1)
+
+
+def layer_forward(p: np.ndarray, li: int, h: np.ndarray, skip=None):
+    """Hidden layer li (0..13) on its stored input h (channels last): the
+    stored output bf16(relu(conv(h) + b + skip)) with BF16 weights, and the
+    magnitude sum |b| + sum |W| |h| (+ skip) of every pre-activation."""
+    W, b = unpack(p)[li]
+    W = to_bf16(W)
+    kind = SPEC[li][2]
+    pre = _layer_conv(kind, h, W, b)
+    mag = _layer_conv(kind, np.abs(h), np.abs(W), np.abs(b))
+    if skip is not None:
+        pre = pre + skip
+        mag = mag + np.abs(skip)
+    return to_bf16(np.maximum(pre, 0.0)), mag
+
+
+def layer_data_grad(p: np.ndarray, li: int, dy: np.ndarray, mask: np.ndarray, add=None):
+    """Layer li's (1..14) gradient into layer li-1's output: bf16((conv^T(dy)
+    + add) * [mask > 0]) with BF16 weights, dy the gradient of li's
+    pre-activation and mask li-1's stored activation; and the magnitude sum
+    of every element (before the mask)."""
+    W, _ = unpack(p)[li]
+    W = to_bf16(W)
+    kind = SPEC[li][2]
+    shape = mask.shape
+    if kind == "s1":
+        dh = conv_adjoint(shape, dy, W, 1)
+        mag = conv_adjoint(shape, np.abs(dy), np.abs(W), 1)
+    elif kind == "s2":
+        dh = conv_adjoint(shape, dy, W, 2)
+        mag = conv_adjoint(shape, np.abs(dy), np.abs(W), 2)
+    else:
+        up_shape = (2 * shape[0], 2 * shape[1], 2 * shape[2], shape[3])
+        dh = down2_sum(conv_adjoint(up_shape, dy, W, 1))
+        mag = down2_sum(conv_adjoint(up_shape, np.abs(dy), np.abs(W), 1))
+    if add is not None:
+        dh = dh + add
+        mag = mag + np.abs(add)
+    return to_bf16(dh * (mask > 0)), mag
+
+
+def layer_weight_grad(li: int, h: np.ndarray, dy: np.ndarray):
+    """Layer li's parameter gradient from its input h and the gradient dy of
+    its pre-activation: flat [dW (tap, ci, co), db] and the magnitude sum of
+    every element."""
+    kind = SPEC[li][2]
+    hh = up2(h) if kind == "up" else h
+    stride = 2 if kind == "s2" else 1
+    co = dy.shape[-1]
+    g = np.concatenate([conv_wgrad(hh, dy, stride).ravel(), dy.reshape(-1, co).sum(axis=0)])
+    m = np.concatenate([conv_wgrad(np.abs(hh), np.abs(dy), stride).ravel(), np.abs(dy).reshape(-1, co).sum(axis=0)])
+    return g, m
+
+
 def init_params(seed: int = 0) -> np.ndarray:
     """He-normal weights on the real channels, zero biases (test inputs)."""
     rng = np.random.Generator(np.random.Philox(seed))

@@ -32,7 +32,8 @@ __device__ __forceinline__ float ld_weak(const float* p) {
 // weak loads instead of the read-only path (which assumes data that never
 // changes during the launch).
 // cnt (kCount): also add every run to the block's run counts s_j (the first
-// sweep after a load forms the DROP weights this way).
+// sweep after a load forms the DROP weights this way), in the gather's replay
+// of the row rather than inside the walk.
 template <bool kCoherent, bool kPlain, bool kCount, class Walk>
 __device__ __forceinline__ void drop_history_core(const RecV& v, Walk&& walk, const float* __restrict__ x,
                                                   float* __restrict__ delta, float lambda,
@@ -41,7 +42,6 @@ __device__ __forceinline__ void drop_history_core(const RecV& v, Walk&& walk, co
   uint2 row[kRowCap];
   int nrow = 0;
   walk([&](int j, float l) {
-    if (kCount) atomicAdd(cnt + j, 1u);
     if (nrow < kRowCap) row[nrow] = make_uint2((unsigned)j, __float_as_uint(l));
     ++nrow;
   });
@@ -62,10 +62,14 @@ __device__ __forceinline__ void drop_history_core(const RecV& v, Walk&& walk, co
   if (nrow <= kRowCap) {
     for (int q = 0; q < nrow; ++q) {
       const uint2 e = row[q];
+      if (kCount) atomicAdd(cnt + e.x, 1u);
       gather((int)e.x, __uint_as_float(e.y));
     }
   } else {
-    walk(gather);
+    walk([&](int j, float l) {
+      if (kCount) atomicAdd(cnt + j, 1u);
+      gather(j, l);
+    });
   }
   if (!(nn > 0.f)) return;
   const float res = __fadd_rn(__fsub_rn(v.wepl, y), c);

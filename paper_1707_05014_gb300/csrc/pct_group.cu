@@ -35,11 +35,6 @@
 namespace pct {
 namespace {
 
-// fadd_rd(q, kFloorBias) = floor(q) + kFloorBias exactly for |q| < 2^22: the
-// sum lies in [2^23, 2^24), where floats are the integers, and rounding down
-// is the floor. Its bit pattern minus kFloorBiasBits is floor(q).
-constexpr float kFloorBias = 12582912.0f;  // 1.5 * 2^23
-constexpr int kFloorBiasBits = 0x4B400000;
 
 template <int T>
 struct Group {
@@ -65,8 +60,6 @@ struct Group {
 
 __device__ __forceinline__ int hibit(unsigned m) { return 31 - __clz(m); }  // m != 0
 
-// Voxel index along one axis of an offset grid coordinate: floor(q) - kQOff.
-__device__ __forceinline__ int vox_of(float bq) { return __float_as_int(bq) - kFloorBiasBits - kQOff; }
 
 // Lane-local analysis of one segment P -> Q (history_fast: each axis crosses
 // at most one face). The events are the distinct crossing times in order
@@ -337,7 +330,6 @@ __global__ void __launch_bounds__(kGroupThreads, 4) drop_group_kernel(Geo g, Rec
     // walk: the row goes to the group's buffer (no global loads in the walk,
     // so no lane waits on memory between steps)
     auto record = [&](int j, float l, int pos) {
-      if (kCount) atomicAdd(cnt + j, 1u);
       if (pos < rowcap) rows[pos] = make_uint2((unsigned)j, __float_as_uint(l));
     };
     const int nrow = group_walk<T>(G, g, tab, v, record);
@@ -359,10 +351,14 @@ __global__ void __launch_bounds__(kGroupThreads, 4) drop_group_kernel(Geo g, Rec
       // a_i.x and |a_i|^2: every lane takes every T-th run of the row
       for (int q = G.ln; q < nrow; q += T) {
         const uint2 e = rows[q];
+        if (kCount) atomicAdd(cnt + e.x, 1u);
         gather((int)e.x, __uint_as_float(e.y));
       }
     } else {
-      auto gather_walk = [&](int j, float l, int) { gather(j, l); };
+      auto gather_walk = [&](int j, float l, int) {
+        if (kCount) atomicAdd(cnt + j, 1u);
+        gather(j, l);
+      };
       group_walk<T>(G, g, tab, v, gather_walk);
     }
     const float yy = kPlain ? group_sum<T>(G, y) : group_sum_comp<T>(G, y, c);

@@ -714,6 +714,85 @@ pct_status pct_net_gradients(pct_net* nt, const float* x1, const float* target, 
   return PCT_OK;
 }
 
+pct_status pct_net_layer_shape(const pct_net* nt, int32_t layer, int32_t* cin, int32_t* cout, int32_t* in_level,
+                               int32_t* out_level) {
+  if (!nt || !cin || !cout || !in_level || !out_level) return nfail(PCT_ERR_INVALID_ARG, "NULL argument");
+  if (layer < 0 || layer >= (int)nt->layers.size()) return nfail(PCT_ERR_INVALID_ARG, "layer out of range");
+  const Layer& ly = nt->layers[layer];
+  *cin = ly.Cin;
+  *cout = ly.Cout;
+  *in_level = ly.in_level;
+  *out_level = ly.out_level;
+  return PCT_OK;
+}
+
+pct_status pct_net_layer(pct_net* nt, int32_t layer, int32_t op, const void* in, const void* skip, const void* dy,
+                         const void* mask, const void* add, void* out, void* stream) {
+  if (!nt || !out) return nfail(PCT_ERR_INVALID_ARG, "net or out is NULL");
+  const int nl = (int)nt->layers.size();
+  if (layer < 0 || layer >= nl) return nfail(PCT_ERR_INVALID_ARG, "layer out of range");
+  const Layer& ly = nt->layers[layer];
+  const Dims din = nt->lv[ly.in_level], dout = nt->lv[ly.out_level];
+  const bool has_skip = layer == 8 || layer == 10 || layer == 12;
+  pct::DeviceGuard device_guard_;
+  NET_CK(cudaSetDevice(nt->device));
+  cudaStream_t s = stream ? (cudaStream_t)stream : nt->own_stream;
+  cudaError_t e = cudaSuccess;
+  if (op == PCT_NET_FORWARD) {
+    if (layer == nl - 1) return nfail(PCT_ERR_INVALID_ARG, "the output layer's forward is pct_net_forward");
+    if (!in || has_skip != (skip != nullptr)) return nfail(PCT_ERR_INVALID_ARG, "in, or skip (layers 8, 10, 12 only)");
+    EpiAct ep{(bf16*)out, nt->params + ly.b_off, (const bf16*)skip, ly.Cout, 1};
+    const bf16* w = nt->wf + ly.w_off;
+    const int bn = bn_for(ly.Cout);
+    if (ly.kind == kS1)
+      e = launch_conv<kS1>(bn, (const bf16*)in, din, ly.Cin, dout, w, ly.Cout, ep, s);
+    else if (ly.kind == kS2)
+      e = launch_conv<kS2>(bn, (const bf16*)in, din, ly.Cin, dout, w, ly.Cout, ep, s);
+    else
+      e = launch_conv<kUp>(bn, (const bf16*)in, din, ly.Cin, dout, w, ly.Cout, ep, s);
+  } else if (op == PCT_NET_DATA_GRAD) {
+    if (layer == 0) return nfail(PCT_ERR_INVALID_ARG, "layer 0 has no data gradient");
+    if (!dy || !mask) return nfail(PCT_ERR_INVALID_ARG, "dy or mask is NULL");
+    if (ly.kind == kS1) {
+      EpiGrad ep{(bf16*)out, nullptr, (const bf16*)add, (const bf16*)mask, ly.Cin};
+      e = launch_conv<kS1>(bn_for(ly.Cin), (const bf16*)dy, dout, ly.Cout, din, nt->wflip + ly.w_off, ly.Cin, ep, s);
+    } else if (ly.kind == kS2) {
+      EpiGrad ep{(bf16*)out, nullptr, (const bf16*)add, (const bf16*)mask, ly.Cin};
+      e = launch_conv<kBwdS2>(bn_for(ly.Cin), (const bf16*)dy, dout, ly.Cout, din, nt->wtr + ly.w_off, ly.Cin, ep, s);
+    } else {
+      if (add) return nfail(PCT_ERR_INVALID_ARG, "an up-convolution's input has no skip gradient");
+      const Dims dhi{2 * din.D, 2 * din.H, 2 * din.W};
+      EpiGrad ep{nullptr, nt->hi, nullptr, nullptr, ly.Cin};
+      e = launch_conv<kS1>(bn_for(ly.Cin), (const bf16*)dy, dout, ly.Cout, dhi, nt->wflip + ly.w_off, ly.Cin, ep, s);
+      if (e == cudaSuccess) {
+        pool_grad_kernel<<<blocks_for(din.n() * ly.Cin, 256), 256, 0, s>>>(nt->hi, din, ly.Cin, (const bf16*)mask,
+                                                                             (bf16*)out);
+        e = cudaGetLastError();
+      }
+    }
+  } else if (op == PCT_NET_WEIGHT_GRAD) {
+    if (!in || !dy) return nfail(PCT_ERR_INVALID_ARG, "in or dy is NULL");
+    float* dw = (float*)out;
+    float* db = dw + 27LL * ly.Cin * ly.Cout;
+    NET_CK(cudaMemsetAsync(dw, 0, (27LL * ly.Cin * ly.Cout + ly.Cout) * sizeof(float), s));
+    if (ly.kind == kS1)
+      e = launch_wgrad<kS1>((const bf16*)in, din, ly.Cin, dout, (const bf16*)dy, ly.Cout, dw, s);
+    else if (ly.kind == kS2)
+      e = launch_wgrad<kS2>((const bf16*)in, din, ly.Cin, dout, (const bf16*)dy, ly.Cout, dw, s);
+    else
+      e = launch_wgrad<kUp>((const bf16*)in, din, ly.Cin, dout, (const bf16*)dy, ly.Cout, dw, s);
+    if (e == cudaSuccess) {
+      const int N = ly.Cout, threads = 256 - 256 % N;
+      bias_grad_kernel<<<304, threads, 0, s>>>((const bf16*)dy, dout.n(), N, db);
+      e = cudaGetLastError();
+    }
+  } else {
+    return nfail(PCT_ERR_INVALID_ARG, "op must be PCT_NET_FORWARD, PCT_NET_DATA_GRAD or PCT_NET_WEIGHT_GRAD");
+  }
+  if (e != cudaSuccess) return nfail(PCT_ERR_CUDA, "layer launch", cudaGetErrorString(e));
+  return PCT_OK;
+}
+
 pct_status pct_net_train_step(pct_net* nt, const float* x1, const float* target, float* x0_scratch, float lr,
                               double* loss, void* stream) {
   if (!nt || !x1 || !target || !x0_scratch) return nfail(PCT_ERR_INVALID_ARG, "NULL argument");

@@ -304,7 +304,8 @@ __device__ __forceinline__ void walk_segment(const Geo& g, WalkState& s, const f
   s.qP = q;
 }
 
-// Calls f(q) with the float grid coordinates of nodes klo+1 .. khi in order.
+// Calls f(q, t, v) with the float grid coordinates and the lateral and
+// vertical positions (mm) of nodes klo+1 .. khi in order.
 // The node loop runs in three phases (entry extension, MLP nodes, exit
 // extension) so that no per-node branch selects the node formula.
 template <class F>
@@ -316,7 +317,7 @@ __device__ __forceinline__ void for_each_node(const Geo& g, const float4* __rest
     const float kf = (float)k;
     const float dk = __fmul_rn(kf, g.du);
     const float t = __fmaf_rn(r.st0, dk, r.t0), v = __fmaf_rn(r.sv0, dk, r.v0);
-    f(node_grid(g, r, __fmaf_rn(kf, g.du, g.u0), t, v));
+    f(node_grid(g, r, __fmaf_rn(kf, g.du, g.u0), t, v), t, v);
   }
   // MLP nodes between the measurement planes (kf counts k exactly in float)
   const int kmid = min(khi, g.K);
@@ -325,13 +326,13 @@ __device__ __forceinline__ void for_each_node(const Geo& g, const float4* __rest
     const float4 c = tab[k];
     const float t = __fmaf_rn(c.w, r.st2, __fmaf_rn(c.z, r.t2, __fmaf_rn(c.y, r.st0, __fmul_rn(c.x, r.t0))));
     const float v = __fmaf_rn(c.w, r.sv2, __fmaf_rn(c.z, r.v2, __fmaf_rn(c.y, r.sv0, __fmul_rn(c.x, r.v0))));
-    f(node_grid(g, r, __fmaf_rn(kf, g.du, g.u0), t, v));
+    f(node_grid(g, r, __fmaf_rn(kf, g.du, g.u0), t, v), t, v);
   }
   // exit extension: straight along the exit slope
   for (; k <= khi; ++k) {
     const float dk = __fmul_rn((float)(k - g.K), g.du);
     const float t = __fmaf_rn(r.st2, dk, r.t2), v = __fmaf_rn(r.sv2, dk, r.v2);
-    f(node_grid(g, r, __fmaf_rn((float)k, g.du, g.u0), t, v));
+    f(node_grid(g, r, __fmaf_rn((float)k, g.du, g.u0), t, v), t, v);
   }
 }
 
@@ -345,9 +346,11 @@ __device__ __forceinline__ void for_each_node(const Geo& g, const float4* __rest
 // and two crossing fractions n1/d1, n2/d2 are ordered exactly by comparing
 // n1*d2 with n2*d1 as an FMA two-product (cmp_prod). That is the integer
 // walk's cross-multiplication on the same numbers, so the runs are the same.
-// A voxel change is detected by comparing each coordinate with the faces of
-// the current voxel, kept as floats: no rounding to Q20 and no conversion in
-// the node loop.
+// Crossing fractions that lie further apart than twice the division's error
+// order the same way as the exact ones, so the exact comparison runs only
+// for near ties. A voxel change is detected by comparing the floor of each
+// coordinate (a round-down addition) with the current voxel's: no rounding to
+// Q20 and no conversion in the node loop.
 
 // Sign of a*b - c*d, exactly: p = a*b rounded, a*b = p + fma(a, b, -p) exactly
 // (no underflow for the magnitudes here), and rounding is monotonic, so
@@ -380,9 +383,18 @@ __device__ __forceinline__ bool history_fast(const Geo& g, const RecV& r) {
   return fmaxf(bx, fmaxf(by, bz)) < 0.999f;
 }
 
+// fadd_rd(q, kFloorBias) = floor(q) + kFloorBias exactly for |q| < 2^22: the
+// sum lies in [2^23, 2^24), where floats are the integers, and rounding down
+// is the floor. Its bit pattern minus kFloorBiasBits is floor(q).
+constexpr float kFloorBias = 12582912.0f;  // 1.5 * 2^23
+constexpr int kFloorBiasBits = 0x4B400000;
+
+// Voxel index along one axis of a biased floor: floor(q) - kQOff.
+__device__ __forceinline__ int vox_of(float bq) { return __float_as_int(bq) - kFloorBiasBits - kQOff; }
+
 struct FastState {
   float3 qP;          // previous node, offset grid coordinates
-  float lx, ly, lz;   // lower faces of the current voxel, offset grid coordinates
+  float bx, by, bz;   // floor of the previous node (the current voxel) + kFloorBias
   int cx, cy, cz;     // current voxel, grid indices
   float run;          // length of the current run so far (mm)
   bool pos;           // the current run has positive exact extent
@@ -402,8 +414,8 @@ __device__ __forceinline__ void emit_fast(const Geo& g, FastState& s, Visit& vis
 // length of the segment.
 template <class Visit>
 __device__ __forceinline__ void seg_fast_exact(const Geo& g, FastState& s, float L, bool rx, bool ry, bool rz, bool xa,
-                                            bool ya, bool za, float ndx, float ndy, float ndz, float ddx, float ddy,
-                                            float ddz, Visit& visit) {
+                                               bool ya, bool za, float ndx, float ndy, float ndz, float ddx, float ddy,
+                                               float ddz, Visit& visit) {
   // exact pairwise order of the crossings (< 0: the first axis crosses first)
   const int oxy = rx && ry ? cmp_prod(ndx, ddy, ndy, ddx) : 0;
   const int oxz = rx && rz ? cmp_prod(ndx, ddz, ndz, ddx) : 0;
@@ -422,17 +434,14 @@ __device__ __forceinline__ void seg_fast_exact(const Geo& g, FastState& s, float
     emit_fast(g, s, visit);
     if (mx) {
       s.cx += xa ? 1 : -1;
-      s.lx += xa ? 1.f : -1.f;
       rx = false;
     }
     if (my) {
       s.cy += ya ? 1 : -1;
-      s.ly += ya ? 1.f : -1.f;
       ry = false;
     }
     if (mz) {
       s.cz += za ? 1 : -1;
-      s.lz += za ? 1.f : -1.f;
       rz = false;
     }
     tl = t;
@@ -449,30 +458,35 @@ __device__ __forceinline__ void seg_fast_exact(const Geo& g, FastState& s, float
 // (< 1.2e-7 on [0, 1]), so fractions further apart order as the exact ones.
 constexpr float kTieWindow = 4e-7f;
 
-// Advance the fast walk from s.qP to the next node q.
+// Advance the fast walk from the previous node to the next one, q (offset
+// grid coordinates).
 template <class Visit>
 __device__ __forceinline__ void seg_fast(const Geo& g, FastState& s, const float3 q, Visit& visit) {
-  const float dx = __fsub_rn(q.x, s.qP.x), dy = __fsub_rn(q.y, s.qP.y), dz = __fsub_rn(q.z, s.qP.z);
-  const float fx = __fmul_rn(dx, g.hx), fy = __fmul_rn(dy, g.hy), fz = __fmul_rn(dz, g.hz);
-  // The nodes of a validated record are at least du / sqrt(2) apart in x or
-  // y (du >= 2R/2047), far above the float spacing, so L2 > 0.
+  // Segment length from the grid coordinates, the polyline the crossings are
+  // taken on (near the grid the differences are exact). The nodes of a
+  // validated record are at least du / sqrt(2) apart in x or y (du >= 2R/2047),
+  // far above the float spacing, so L2 > 0.
+  const float ddx = fabsf(__fsub_rn(q.x, s.qP.x)), ddy = fabsf(__fsub_rn(q.y, s.qP.y)),
+              ddz = fabsf(__fsub_rn(q.z, s.qP.z));
+  const float fx = __fmul_rn(ddx, g.hx), fy = __fmul_rn(ddy, g.hy), fz = __fmul_rn(ddz, g.hz);
   const float L2 = __fmaf_rn(fx, fx, __fmaf_rn(fy, fy, __fmul_rn(fz, fz)));
   const float L = L2 * rsqrtf(L2);
-  const float ux = s.lx + 1.f, uy = s.ly + 1.f, uz = s.lz + 1.f;  // upper faces
-  const bool xa = q.x >= ux, xb = q.x < s.lx;  // half-open voxels: a face reached moving up is crossed
-  const bool ya = q.y >= uy, yb = q.y < s.ly;
-  const bool za = q.z >= uz, zb = q.z < s.lz;
-  if (!(xa | xb | ya | yb | za | zb)) {
+  // the voxel of q against the current one (half-open voxels: a face reached
+  // moving up is crossed, one reached moving down is not)
+  const float bqx = __fadd_rd(q.x, kFloorBias), bqy = __fadd_rd(q.y, kFloorBias), bqz = __fadd_rd(q.z, kFloorBias);
+  const bool rx = bqx != s.bx, ry = bqy != s.by, rz = bqz != s.bz;  // crossings to take
+  if (!(rx | ry | rz)) {
     s.run += L;  // the segment moves, so the run's extent is positive
     s.pos = true;
     s.qP = q;
     return;
   }
-  const bool rx = xa | xb, ry = ya | yb, rz = za | zb;  // crossings to take
+  const bool xa = bqx > s.bx, ya = bqy > s.by, za = bqz > s.bz;  // crossing upwards
   // exact distance to the crossed face and exact axis length of the segment
-  const float ndx = xa ? __fsub_rn(ux, s.qP.x) : __fsub_rn(s.qP.x, s.lx), ddx = fabsf(dx);
-  const float ndy = ya ? __fsub_rn(uy, s.qP.y) : __fsub_rn(s.qP.y, s.ly), ddy = fabsf(dy);
-  const float ndz = za ? __fsub_rn(uz, s.qP.z) : __fsub_rn(s.qP.z, s.lz), ddz = fabsf(dz);
+  const float lx = __fsub_rn(s.bx, kFloorBias), ly = __fsub_rn(s.by, kFloorBias), lz = __fsub_rn(s.bz, kFloorBias);
+  const float ndx = xa ? __fsub_rn(__fadd_rn(lx, 1.f), s.qP.x) : __fsub_rn(s.qP.x, lx);
+  const float ndy = ya ? __fsub_rn(__fadd_rn(ly, 1.f), s.qP.y) : __fsub_rn(s.qP.y, ly);
+  const float ndz = za ? __fsub_rn(__fadd_rn(lz, 1.f), s.qP.z) : __fsub_rn(s.qP.z, lz);
   float tx = rx ? __fdividef(ndx, ddx) : INFINITY;
   float ty = ry ? __fdividef(ndy, ddy) : INFINITY;
   float tz = rz ? __fdividef(ndz, ddz) : INFINITY;
@@ -482,39 +496,39 @@ __device__ __forceinline__ void seg_fast(const Geo& g, FastState& s, const float
                     tmax > 1.f - kTieWindow;
   if (near) {
     seg_fast_exact(g, s, L, rx, ry, rz, xa, ya, za, ndx, ndy, ndz, ddx, ddy, ddz, visit);
-    s.qP = q;
-    return;
+  } else {
+    // distinct fractions: the float order is the exact order, one axis per event
+    float tl = 0.f;
+    bool first = true;
+    for (;;) {
+      const float m = fminf(tx, fminf(ty, tz));
+      if (m == INFINITY) break;
+      s.run += (m - tl) * L;
+      s.pos |= !first || m > 0.f;  // m > 0 exactly when the distance to the face is
+      emit_fast(g, s, visit);
+      const bool mx = tx == m, my = !mx && ty == m, mz = !mx && !my;
+      if (mx) {
+        s.cx += xa ? 1 : -1;
+        tx = INFINITY;
+      }
+      if (my) {
+        s.cy += ya ? 1 : -1;
+        ty = INFINITY;
+      }
+      if (mz) {
+        s.cz += za ? 1 : -1;
+        tz = INFINITY;
+      }
+      tl = m;
+      first = false;
+    }
+    s.run += (1.f - tl) * L;
+    s.pos = true;  // the last crossing lies more than the tie window before the node
   }
-  // distinct fractions: the float order is the exact order, one axis per event
-  float tl = 0.f;
-  bool first = true;
-  for (;;) {
-    const float m = fminf(tx, fminf(ty, tz));
-    if (m == INFINITY) break;
-    s.run += (m - tl) * L;
-    s.pos |= !first || m > 0.f;  // m > 0 exactly when the distance to the face is
-    emit_fast(g, s, visit);
-    const bool mx = tx == m, my = !mx && ty == m, mz = !mx && !my;
-    if (mx) {
-      s.cx += xa ? 1 : -1;
-      s.lx += xa ? 1.f : -1.f;
-      tx = INFINITY;
-    }
-    if (my) {
-      s.cy += ya ? 1 : -1;
-      s.ly += ya ? 1.f : -1.f;
-      ty = INFINITY;
-    }
-    if (mz) {
-      s.cz += za ? 1 : -1;
-      s.lz += za ? 1.f : -1.f;
-      tz = INFINITY;
-    }
-    tl = m;
-    first = false;
-  }
-  s.run += (1.f - tl) * L;
-  s.pos = true;  // the last crossing lies more than the tie window before the node
+  // each axis crossed at most one face: the voxel is now the floor of q
+  s.bx = bqx;
+  s.by = bqy;
+  s.bz = bqz;
   s.qP = q;
 }
 
@@ -526,15 +540,15 @@ __device__ __forceinline__ void walk_fast(const Geo& g, const float4* __restrict
     const float2 tv = node_tv(g, tab, r, klo);
     s.qP = node_grid(g, r, __fmaf_rn((float)klo, g.du, g.u0), tv.x, tv.y);
   }
-  s.lx = floorf(s.qP.x);
-  s.ly = floorf(s.qP.y);
-  s.lz = floorf(s.qP.z);
-  s.cx = (int)s.lx - kQOff;
-  s.cy = (int)s.ly - kQOff;
-  s.cz = (int)s.lz - kQOff;
+  s.bx = __fadd_rd(s.qP.x, kFloorBias);
+  s.by = __fadd_rd(s.qP.y, kFloorBias);
+  s.bz = __fadd_rd(s.qP.z, kFloorBias);
+  s.cx = vox_of(s.bx);
+  s.cy = vox_of(s.by);
+  s.cz = vox_of(s.bz);
   s.run = 0.f;
   s.pos = false;
-  for_each_node(g, tab, r, klo, khi, [&](const float3 q) { seg_fast(g, s, q, visit); });
+  for_each_node(g, tab, r, klo, khi, [&](const float3 q, float, float) { seg_fast(g, s, q, visit); });
   emit_fast(g, s, visit);
 }
 
@@ -568,7 +582,7 @@ __device__ __forceinline__ void walk_proton(const Geo& g, const float4* __restri
   s.cz = floor_q(s.P.z);
   s.run = 0.f;
   s.pos = false;
-  for_each_node(g, tab, r, klo, khi, [&](const float3 q) { walk_segment(g, s, q, visit); });
+  for_each_node(g, tab, r, klo, khi, [&](const float3 q, float, float) { walk_segment(g, s, q, visit); });
   emit_run(g, s, visit);
 }
 

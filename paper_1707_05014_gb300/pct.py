@@ -106,6 +106,8 @@ _SIGS = {
                           ctypes.POINTER(ctypes.c_double)],
     "pct_net_train_step": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_float,
                            ctypes.POINTER(ctypes.c_double), ctypes.c_void_p],
+    "pct_net_layer_shape": [ctypes.c_void_p, ctypes.c_int32] + [ctypes.POINTER(ctypes.c_int32)] * 4,
+    "pct_net_layer": [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32] + [ctypes.c_void_p] * 7,
 }
 
 
@@ -505,6 +507,9 @@ class Batch:
         return int(self._L.pct_batch_launch_count(self._h))
 
 
+NET_FORWARD, NET_DATA_GRAD, NET_WEIGHT_GRAD = 0, 1, 2
+
+
 class Net:
     """Warm-start network (pct_net_*): x0 = x1 + f(x1) for nz x ny x nx volumes
     (CUDA float tensors in the reconstruction's voxel order)."""
@@ -552,6 +557,47 @@ class Net:
             n = self.shape[0] * self.shape[1] * self.shape[2]
             self._scratch = torch.empty(n, dtype=torch.float32, device=torch.device("cuda", self.device))
         return self._scratch
+
+    def layer_shape(self, layer: int):
+        """(Cin, Cout, input level, output level) of a layer."""
+        v = [ctypes.c_int32() for _ in range(4)]
+        _check(self._L.pct_net_layer_shape(self._h, int(layer), *[ctypes.byref(x) for x in v]))
+        return tuple(int(x.value) for x in v)
+
+    def layer(self, layer: int, op: int, inp=None, skip=None, dy=None, mask=None, add=None):
+        """One layer through pct_net_layer. BF16 operands are int16 CUDA
+        tensors of bit patterns, channels last; returns the output as an int16
+        (BF16 bits) tensor, or float32 for NET_WEIGHT_GRAD (dW then db).
+        Synchronises."""
+        torch = _torch()
+        cin, cout, lin, lout = self.layer_shape(layer)
+        nz, ny, nx = self.shape
+        vox = lambda lv: (nz >> lv) * (ny >> lv) * (nx >> lv)  # noqa: E731
+        dev = torch.device("cuda", self.device)
+        want = {"inp": (inp, vox(lin) * cin), "skip": (skip, vox(lout) * cout), "dy": (dy, vox(lout) * cout),
+                "mask": (mask, vox(lin) * cin), "add": (add, vox(lin) * cin)}
+        ptr = {}
+        keep = []
+        for name, (t, n) in want.items():
+            if t is None:
+                ptr[name] = None
+                continue
+            if not (_is_tensor(t) and t.is_cuda and t.dtype == torch.int16):
+                raise ValueError(f"{name}: expected an int16 CUDA tensor of BF16 bit patterns")
+            _check_vector(t.reshape(-1), n, name, self.device)
+            t = t.contiguous()
+            keep.append(t)
+            ptr[name] = ctypes.c_void_p(t.data_ptr())
+        if op == NET_FORWARD:
+            out = torch.empty(vox(lout) * cout, dtype=torch.int16, device=dev)
+        elif op == NET_DATA_GRAD:
+            out = torch.empty(vox(lin) * cin, dtype=torch.int16, device=dev)
+        else:
+            out = torch.empty(27 * cin * cout + cout, dtype=torch.float32, device=dev)
+        _check(self._L.pct_net_layer(self._h, int(layer), int(op), ptr["inp"], ptr["skip"], ptr["dy"], ptr["mask"],
+                                     ptr["add"], ctypes.c_void_p(out.data_ptr()), _stream_ptr()))
+        torch.cuda.synchronize(dev)
+        return out
 
     def get_params(self) -> np.ndarray:
         out = np.empty(self.n_params, dtype=np.float32)

@@ -149,3 +149,65 @@ def test_training_lowers_the_loss(P):
             net.train_step(dx1, dt, lr=2e-3, want_loss=False)
         l1 = net.train_step(dx1, dt, lr=2e-3)
     assert l1 < 0.5 * l0
+
+
+def _bf16_bits(a):
+    """float64 values already on the BF16 grid -> int16 CUDA tensor of bits."""
+    import torch
+
+    u = (np.asarray(a, dtype=np.float32).view(np.uint32) >> 16).astype(np.uint16)
+    return torch.from_numpy(u.view(np.int16).ravel().copy()).cuda()
+
+
+def _from_bf16_bits(t, shape):
+    u = t.cpu().numpy().view(np.uint16).astype(np.uint32) << 16
+    return u.view(np.float32).astype(np.float64).reshape(shape)
+
+
+@pytest.mark.parametrize("seed", [4])
+def test_every_layer_matches_reference_element_wise(P, seed):
+    """Each layer's forward, data gradient and weight gradient on the same
+    seeded BF16 inputs on both sides (oracle/unet.py layer_*): the stored
+    results differ by the FP32 summation order (at most K 2^-24 of the
+    magnitude sum for K summed terms) plus one BF16 ulp (2^-7) of the value
+    where that difference crosses a rounding boundary; the FP32 weight
+    gradients by the summation order alone. A wrong halo row, tap, stride or
+    skip changes elements by O(1) of their magnitude."""
+    rng = np.random.Generator(np.random.Philox(200 + seed))
+    _, _, p = _data(seed)
+    D, H, W = SHAPE
+    nl = len(U.SPEC)
+    worst = {}
+    with P.Net(*SHAPE) as net:
+        net.set_params(p)
+        for li, (ci, co, kind, skip) in enumerate(U.SPEC):
+            _, _, lin, lout = net.layer_shape(li)
+            din = (D >> lin, H >> lin, W >> lin, ci)
+            dout = (D >> lout, H >> lout, W >> lout, co)
+            h = U.to_bf16(np.maximum(rng.standard_normal(din), 0.0))
+            dy = U.to_bf16(1e-3 * rng.standard_normal(dout))
+            taps = 27 * ci
+            if li < nl - 1:
+                sk = U.to_bf16(np.maximum(rng.standard_normal(dout), 0.0)) if skip >= 0 else None
+                ref, mag = U.layer_forward(p, li, h, sk)
+                got = _from_bf16_bits(net.layer(li, P.NET_FORWARD, inp=_bf16_bits(h),
+                                                skip=None if sk is None else _bf16_bits(sk)), dout)
+                bound = 2.0**-7 * np.abs(ref) * 1.01 + 2 * (taps + 2) * 2.0**-24 * mag + 1e-30
+                worst[(li, "fwd")] = float((np.abs(got - ref) / bound).max())
+            if li > 0:
+                mask = U.to_bf16(np.maximum(rng.standard_normal(din), 0.0))
+                adds = [u for u, s in enumerate(U.SPEC) if s[3] == li - 1]
+                ad = U.to_bf16(1e-3 * rng.standard_normal(din)) if adds and kind != "up" else None
+                ref, mag = U.layer_data_grad(p, li, dy, mask, ad)
+                got = _from_bf16_bits(net.layer(li, P.NET_DATA_GRAD, dy=_bf16_bits(dy), mask=_bf16_bits(mask),
+                                                add=None if ad is None else _bf16_bits(ad)), din)
+                terms = 27 * co * (8 if kind == "up" else 1) + 2
+                bound = 2.0**-7 * np.abs(ref) * 1.01 + 2 * terms * 2.0**-24 * mag + 1e-30
+                worst[(li, "dgrad")] = float((np.abs(got - ref) / bound).max())
+            ref, mag = U.layer_weight_grad(li, h, dy)
+            got = net.layer(li, P.NET_WEIGHT_GRAD, inp=_bf16_bits(h), dy=_bf16_bits(dy)).cpu().numpy()
+            vox = dout[0] * dout[1] * dout[2]
+            bound = 2 * (vox + 32) * 2.0**-24 * mag + 1e-30
+            worst[(li, "wgrad")] = float((np.abs(got.astype(np.float64) - ref) / bound).max())
+    bad = {k: v for k, v in worst.items() if v > 1.0}
+    assert not bad, bad

@@ -104,3 +104,41 @@ def test_gradient_bound_scales_bound_the_gradient():
         _, g0, core0, rel0 = U.loss_and_grads(p, x1, target, bf16=bf16, scales=True, relu_margin=0.0)
         assert np.array_equal(g0, g)
         assert np.allclose(core0, rel0, rtol=1e-12, atol=0)
+
+
+def test_layer_functions_chain_to_the_network():
+    """The per-layer functions (the GPU's per-layer check uses them) chained
+    over the topology give the whole network's forward output and every
+    parameter gradient exactly (BF16 storage on)."""
+    rng = np.random.Generator(np.random.Philox(13))
+    p = U.init_params(6)
+    off = 0
+    for ci, co, _, _ in U.SPEC:
+        off += 27 * ci * co
+        p[off:off + co] = 0.05 * rng.standard_normal(co)
+        off += co
+    x1 = rng.random((8, 8, 16))
+    target = x1 + 0.3 * rng.standard_normal(x1.shape)
+    x0, c = U.forward(p, x1, bf16=True)
+    h = c["inp"]
+    acts = []
+    for li, (_, _, _, skip) in enumerate(U.SPEC[:-1]):
+        h, mag = U.layer_forward(p, li, h, acts[skip] if skip >= 0 else None)
+        assert np.array_equal(h, c["acts"][li]) and np.all(mag >= 0)
+        acts.append(h)
+    _, g = U.loss_and_grads(p, x1, target, bf16=True)
+    nl = len(U.SPEC)
+    df = np.zeros(x0.shape + (16,))
+    df[..., 0] = np.sign(x0 - target) / x0.size
+    gpre = [None] * nl
+    gpre[nl - 1] = U.to_bf16(df)
+    offs = np.cumsum([0] + [27 * ci * co + co for ci, co, _, _ in U.SPEC])
+    for li in range(nl - 1, -1, -1):
+        hin = c["inp"] if li == 0 else acts[li - 1]
+        gw, mw = U.layer_weight_grad(li, hin, gpre[li])
+        assert np.array_equal(gw, g[offs[li]:offs[li + 1]]) and np.all(np.abs(gw) <= mw + 1e-300)
+        if li == 0:
+            break
+        adds = [gpre[u] for u, (_, _, _, skip) in enumerate(U.SPEC) if skip == li - 1]
+        gpre[li - 1], md = U.layer_data_grad(p, li, gpre[li], acts[li - 1], adds[0] if adds else None)
+        assert np.all(md >= 0)
