@@ -127,7 +127,7 @@ def ncu_counters():
     """DRAM bytes per history of the fused kernel from the committed ncu summary,
     if it was taken on the current kernel sources."""
     try:
-        with open(os.path.join(ROOT, "profiles", "drop_fused_head_counters.json")) as f:
+        with open(os.path.join(ROOT, "profiles", "drop_fused_head200_counters.json")) as f:
             c = json.load(f)
     except OSError:
         return None
@@ -628,7 +628,8 @@ def run_ours(args):
     alu_peak = ALU_LANES_PER_SM * N_SMS * sm_mhz * 1e6 / 1e12  # Tops/s
     achieved = ops_per_history * per_block / avg_fused_s / 1e12
     cnt = ncu_counters()
-    traffic = cnt["dram_bytes_per_history"] * per_block if cnt else None
+    # the counters were taken on the one-lane kernel without a hull
+    traffic = cnt["dram_bytes_per_history"] * per_block if cnt and args.lanes <= 1 and not args.hull else None
     hbm_achieved = 44.0 * per_block / avg_fused_s / 1e9
     # the library's own roof microbenchmarks: L2 atomics, L2 gathers, ALU issue
     mr = P.measure_roofs(local)

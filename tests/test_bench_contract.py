@@ -70,7 +70,7 @@ def test_traffic_counters_are_used_only_for_the_sources_they_were_taken_on(monke
     sys.path.insert(0, ROOT)
     import bench
 
-    with open(os.path.join(ROOT, "profiles", "drop_fused_head_counters.json")) as f:
+    with open(os.path.join(ROOT, "profiles", "drop_fused_head200_counters.json")) as f:
         rec = json.load(f)
     assert rec["sources"] == list(bench.FUSED_SOURCES) and rec["dram_bytes_per_history"] > 44
     monkeypatch.setattr(bench, "kernel_source_hash", lambda: rec["source_hash"])
