@@ -112,17 +112,27 @@ def solve_to_target(ctx: P.Context, x_true: np.ndarray, grid: S.Grid, target: fl
     def err():
         return S.mean_rsp_error(ctx.get_rsp().astype(np.float64), x_true, grid)
 
+    ms_at = []  # GPU time spent when each error was reached
     sweeps = 0
     timed(lambda: ctx.iterate(1))
     sweeps = 1
     if net is not None:
         used_net = timed(lambda: warm_start(ctx, net, check_stride))
     errs.append(err())
+    ms_at.append(t_ms)
     while errs[-1] > target and sweeps < max_sweeps:
         timed(lambda: ctx.iterate(1))
         sweeps += 1
         errs.append(err())
-    return {"reached": errs[-1] <= target, "sweeps": sweeps, "ms": t_ms, "errors": errs, "net_used": used_net}
+        ms_at.append(t_ms)
+    return {"reached": errs[-1] <= target, "sweeps": sweeps, "ms": t_ms, "errors": errs, "ms_at": ms_at,
+            "net_used": used_net}
+
+
+def ms_to_target(result: Dict, target: float) -> Optional[float]:
+    """GPU time (ms) at which a solve_to_target result first reached `target`
+    (None if it never did)."""
+    return next((ms for e, ms in zip(result["errors"], result["ms_at"]) if e <= target), None)
 
 
 def warm_start(ctx: P.Context, net: P.Net, check_stride: int = 64) -> bool:
@@ -177,13 +187,16 @@ def solve_batch_to_target(batch: P.Batch, ctxs: Sequence[P.Context], x_trues: Se
     if net is not None:
         used = timed(lambda: [warm_start(c, net, check_stride) for c in ctxs])
     errs = [errs_now()]
+    ms_at = [t_ms]
     while max(errs[-1]) > target and sweeps < max_sweeps:
         timed(sweep)
         sweeps += 1
         errs.append(errs_now())
+        ms_at.append(t_ms)
     per = [next((k + 1 for k, e in enumerate(errs) if e[r] <= target), None) for r in range(len(ctxs))]
     return {"reached": max(errs[-1]) <= target, "sweeps": sweeps, "ms": t_ms, "sweeps_to_target": per,
-            "errors": [[e[r] for e in errs] for r in range(len(ctxs))], "net_used": used}
+            "errors": [[e[r] for e in errs] for r in range(len(ctxs))], "ms_at": ms_at,
+            "worst_errors": [max(e) for e in errs], "net_used": used}
 
 
 def pick_blocks(trial: Callable[[int, Optional[float]], Optional[float]], candidates: Sequence[int]) -> Tuple[int, Dict]:
@@ -214,7 +227,7 @@ def pick_blocks(trial: Callable[[int, Optional[float]], Optional[float]], candid
 
 
 def tune_blocks(grid: S.Grid, n: int, seed: int, target: float, max_sweeps: int,
-                candidates: Sequence[int] = (10, 20, 50, 100), device: int = 0, lanes: int = 1) -> Tuple[int, Dict]:
+                candidates: Sequence[int] = (20, 50, 100, 200), device: int = 0, lanes: int = 1) -> Tuple[int, Dict]:
     """pick_blocks on one seeded training head: for each B, a plain
     reconstruction from x = 0 timed to the target mean RSP error (the known
     phantom of a training case decides; held-out cases are never used)."""
