@@ -393,10 +393,11 @@ def time_to_image(args, local: int, log) -> dict:
     the network; on held-out heads with 1e9 histories, the time to each target
     mean RSP error of the warm-started solve and of the plain solver (CUDA
     events on the GPU work; the error check against the known phantom is
-    outside the timed region). The block count is first tuned for the plain
-    solver's time to the first target, and both solvers use it. Each timed
-    solve starts from a fresh load, so both pay the first sweep's forming of
-    the block weights. Every step runs in the library's kernels."""
+    outside the timed region). Both solvers use the same block count (--ws-blocks,
+    or tuned for the plain solver with --ws-tune-blocks); a study of the plain
+    solver over several block counts is reported beside it. Each timed solve
+    starts from a fresh load, so both pay the first sweep's forming of the
+    block weights. Every step runs in the library's kernels."""
     import numpy as np
     import torch
 
@@ -407,6 +408,13 @@ def time_to_image(args, local: int, log) -> dict:
     g = W.training_grid()
     targets = sorted({args.ws_target, *([args.ws_target2] if args.ws_target2 > 0 else [])}, reverse=True)
     tight = targets[-1]
+    study = None
+    if args.ws_blocks_study:  # the plain solver's error per sweep for several block counts (training head 999)
+        t0 = time.time()
+        cands = [int(v) for v in args.ws_blocks_study.split(",") if v.strip()]
+        study = {"per_blocks": W.blocks_study(g, args.ws_test_n, 999, targets, args.ws_study_sweeps, cands,
+                                              device=local, lanes=args.lanes), "study_s": time.time() - t0}
+        log(f"blocks study: {study}")
     tuning = None
     if args.ws_tune_blocks:  # blocks per update picked on a training head (seed 999), then used throughout
         t0 = time.time()
@@ -498,7 +506,7 @@ def time_to_image(args, local: int, log) -> dict:
                    "training_target": f"plain solver after {args.ws_train_sweeps} sweeps", "epochs": args.ws_epochs,
                    "lanes_per_history": args.lanes},
         "tests": results, "train_loss": hist, "training_data_s": t_data, "training_s": t_train,
-        "blocks_tuning": tuning,
+        "blocks_tuning": tuning, "blocks_study": study,
     }
 
 
@@ -517,7 +525,7 @@ def run_warmstart(args):
             "higher_is_better": False, "data": "synthetic", "dtype": "f32", "config": tti["config"],
             "plain_seconds": tti["plain_seconds"], "speedup": tti["speedup"],
             **{k: tti[k] for k in ("by_target", "tests", "train_loss", "training_data_s", "training_s",
-                                   "blocks_tuning", "batched")}}
+                                   "blocks_tuning", "blocks_study", "batched")}}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -713,7 +721,8 @@ def run_ours(args):
         log = lambda m: print(m, file=sys.stderr, flush=True)  # noqa: E731
         full = time_to_image(args, local, log)
         tti = {k: full[k] for k in ("metric", "unit", "higher_is_better", "warm_seconds", "plain_seconds", "speedup",
-                                    "by_target", "config", "training_data_s", "training_s", "blocks_tuning")}
+                                    "by_target", "config", "training_data_s", "training_s", "blocks_tuning",
+                                    "blocks_study")}
         tti["tests"] = [{"seed": r["seed"], **{m: {"seconds_to": r[m]["seconds_to"], "sweeps": r[m]["sweeps"],
                                                    "errors": r[m]["errors"],
                                                    **({"net_used": r[m]["net_used"]} if m == "warm" else {})}
@@ -789,14 +798,18 @@ def main():
     ap.add_argument("--ws-train-n", type=int, default=50_000_000)
     ap.add_argument("--ws-train-sweeps", type=int, default=3)
     ap.add_argument("--ws-blocks", type=int, default=50)
-    ap.add_argument("--ws-fixed-blocks", dest="ws_tune_blocks", action="store_false",
-                    help="time to image: keep --ws-blocks instead of tuning the block count on a training head")
+    ap.add_argument("--ws-tune-blocks", action="store_true",
+                    help="time to image: tune the block count for the plain solver's time to --ws-target on a "
+                         "training head and use it for both solvers (default: --ws-blocks)")
+    ap.add_argument("--ws-blocks-study", default="20,50,100,200",
+                    help="block counts of the plain-solver study reported beside the time to image ('' to skip)")
+    ap.add_argument("--ws-study-sweeps", type=int, default=4)
     ap.add_argument("--ws-epochs", type=int, default=10)
     ap.add_argument("--ws-tests", type=int, default=2)
     ap.add_argument("--ws-test-n", type=int, default=1_000_000_000)
     ap.add_argument("--ws-target", type=float, default=0.01)
-    ap.add_argument("--ws-target2", type=float, default=0.005, help="a tighter second target (<= 0: none)")
-    ap.add_argument("--ws-max-sweeps", type=int, default=10)
+    ap.add_argument("--ws-target2", type=float, default=0.006, help="a tighter second target (<= 0: none)")
+    ap.add_argument("--ws-max-sweeps", type=int, default=6)
     ap.add_argument("--ws-batch", default="1e9,5e8,2.5e8",
                     help="histories of the held-out heads solved together as one batch ('' to skip)")
     ap.add_argument("--n-recon", type=int, default=32, help="reconstructions of the batched workload")

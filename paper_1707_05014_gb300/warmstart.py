@@ -226,6 +226,32 @@ def pick_blocks(trial: Callable[[int, Optional[float]], Optional[float]], candid
     return best_b, results
 
 
+def blocks_study(grid: S.Grid, n: int, seed: int, targets: Sequence[float], sweeps: int,
+                 candidates: Sequence[int] = (20, 50, 100, 200), device: int = 0, lanes: int = 1) -> Dict:
+    """The plain solver on one seeded training head for every block count B:
+    the mean RSP error after each of `sweeps` sweeps and the GPU time at which
+    each target was first reached (None if not within the sweeps). Shows the
+    trade-off the block count sets: more blocks converge faster per sweep, and
+    with noisy data stall higher (the error can grow again over later
+    sweeps)."""
+    import torch
+
+    out = {}
+    for b in candidates:
+        wl = head_workload(grid, n, seed, n_blocks=b)
+        x_true = S.voxelize(wl.phantom(), grid, ss=2)
+        rec = S.make_histories_device(wl, device=f"cuda:{device}")
+        with P.Context(grid, n_blocks=b, device=device, lanes=lanes) as ctx:
+            ctx.load(rec)
+            del rec
+            torch.cuda.empty_cache()
+            r = solve_to_target(ctx, x_true, grid, -1.0, sweeps)  # every sweep (no target stops it)
+        out[str(b)] = {"errors": r["errors"], "ms_at": r["ms_at"],
+                       "seconds_to": {str(t): (lambda ms: None if ms is None else ms / 1e3)(ms_to_target(r, t))
+                                      for t in targets}}
+    return out
+
+
 def tune_blocks(grid: S.Grid, n: int, seed: int, target: float, max_sweeps: int,
                 candidates: Sequence[int] = (20, 50, 100, 200), device: int = 0, lanes: int = 1) -> Tuple[int, Dict]:
     """pick_blocks on one seeded training head: for each B, a plain
