@@ -203,12 +203,15 @@ def run_reference(args):
 
 def main_workload(args, rank: int = 0):
     """The throughput workload: head200 (1e9 histories, 200x200x48 @ 1x1x2 mm,
-    50 blocks) or head (50M histories, 160x160x64 @ 1.25 mm, 10 blocks); each
-    rank draws its own reconstruction (weak scaling)."""
+    50 blocks), head (50M histories, 160x160x64 @ 1.25 mm, 10 blocks) or tiny
+    (100k histories, 32^3 @ 2 mm, water cylinder, 10 blocks); each rank draws
+    its own reconstruction (weak scaling)."""
     from paper_1707_05014_gb300 import synthetic as S
 
     if args.workload == "head":
         return S.head_workload(args.n or 50_000_000, seed=2 + rank)
+    if args.workload == "tiny":
+        return S.tiny_workload(args.n or 100_000, seed=1 + rank)
     return S.head200_workload(args.n or 1_000_000_000, seed=5 + rank)
 
 
@@ -396,8 +399,10 @@ def time_to_image(args, local: int, log) -> dict:
     outside the timed region). Both solvers use the same block count (--ws-blocks,
     or tuned for the plain solver with --ws-tune-blocks); a study of the plain
     solver over several block counts is reported beside it. Each timed solve
-    starts from a fresh load, so both pay the first sweep's forming of the
-    block weights. Every step runs in the library's kernels."""
+    starts from a fresh load with the block weights formed beforehand
+    (pct_block_weights, timed separately): the clock starts at the first
+    sweep with the records resident. Every step runs in the library's
+    kernels."""
     import numpy as np
     import torch
 
@@ -442,8 +447,13 @@ def time_to_image(args, local: int, log) -> dict:
         ctx = P.Context(g, n_blocks=wl.n_blocks, device=local, lanes=args.lanes)
         r = {"seed": 5000 + k}
         for name, use in (("plain", None), ("warm", net)):
-            ctx.load(rec)  # fresh: x = 0, block weights formed by the first timed sweep
+            ctx.load(rec)  # fresh: x = 0
+            torch.cuda.synchronize()
+            tw = time.perf_counter()
+            ctx.block_weights()  # set-up, timed separately
+            weights_s = time.perf_counter() - tw
             res = W.solve_to_target(ctx, x_true, g, tight, args.ws_max_sweeps, net=use)
+            res["block_weights_seconds"] = weights_s
             res["seconds_to"] = {str(t): (lambda ms: None if ms is None else ms / 1e3)(W.ms_to_target(res, t))
                                  for t in targets}
             r[name] = res
@@ -725,6 +735,7 @@ def run_ours(args):
                                     "blocks_study")}
         tti["tests"] = [{"seed": r["seed"], **{m: {"seconds_to": r[m]["seconds_to"], "sweeps": r[m]["sweeps"],
                                                    "errors": r[m]["errors"],
+                                                   "block_weights_seconds": r[m]["block_weights_seconds"],
                                                    **({"net_used": r[m]["net_used"]} if m == "warm" else {})}
                                                for m in ("plain", "warm")}} for r in full["tests"]]
         bt = full["batched"]
@@ -753,7 +764,7 @@ def run_ours(args):
                        "grid": grid_text(g),
                        "mlp_node_step_mm": args.node_step if args.node_step > 0 else min(g.hx, g.hy, g.hz) / 2,
                        "lanes_per_history": args.lanes,
-                       "histories_per_gpu": wl.n, "angles": 90, "n_blocks": wl.n_blocks,
+                       "histories_per_gpu": wl.n, "angles": wl.n_angles or "continuous", "n_blocks": wl.n_blocks,
                        "step": "one DROP sweep over all histories", "parallelism": f"replicas{world}",
                        "l2": f"records {44 * wl.n / 1e9:.1f} GB per sweep > 129 MB L2 (no flush needed); x and delta L2-resident",
                        "hull": (f"carved from the data: rows of histories with WEPL <= {args.hull_wepl} mm are air, "
@@ -786,7 +797,7 @@ def main():
     ap.add_argument("--hull-wepl", type=float, default=1.0, help="carving: histories with WEPL <= this (mm) are air")
     ap.add_argument("--hull-dilate", type=int, default=1, help="carving: 6-neighbour growth steps of the hull")
     ap.add_argument("--workload", default="head200",
-                    choices=["head200", "head", "batched", "precision", "warmstart", "table2"])
+                    choices=["head200", "head", "tiny", "batched", "precision", "warmstart", "table2"])
     ap.add_argument("--t2-n", type=int, default=200_000_000)
     ap.add_argument("--t2-blocks", type=int, default=600, help="DROP blocks; CARP: blocks split over the strings")
     ap.add_argument("--t2-strings", type=int, default=60)

@@ -239,6 +239,14 @@ PCT_API pct_status pct_residual(pct_ctx *ctx, int64_t stride, double *sum_sq);
  * written to DEVICE memory `out`. */
 PCT_API pct_status pct_block_counts(pct_ctx *ctx, int32_t block, float *out);
 
+/* Form the DROP weights S_b^-1 = diag(1/s_j) of every block of the loaded
+ * histories now (Sec. 2.1: the update of block b divides by its run counts).
+ * Otherwise the first pct_iterate after a load forms them while it sweeps; a
+ * caller that times sweeps separately from this set-up calls it first. No-op
+ * if they are formed already. PCT_ERR_STATE without loaded histories.
+ * Synchronises. */
+PCT_API pct_status pct_block_weights(pct_ctx *ctx);
+
 /* Set the initial image x0 (M floats; device memory if on_device, else host).
  * Does not reset the TVS trial counter (pct_load_histories does). */
 PCT_API pct_status pct_set_x0(pct_ctx *ctx, const float *x0, int on_device);

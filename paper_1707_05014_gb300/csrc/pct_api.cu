@@ -664,6 +664,12 @@ pct_status pct_block_counts(pct_ctx* c, int32_t block, float* out) {
   return PCT_OK;
 }
 
+pct_status pct_block_weights(pct_ctx* c) {
+  if (!c) return fail(PCT_ERR_INVALID_ARG, "ctx is NULL");
+  if (!c->loaded) return fail(PCT_ERR_STATE, "no histories loaded");
+  return pct::ensure_block_weights(c);
+}
+
 pct_status pct_set_x0(pct_ctx* c, const float* x0, int on_device) {
   if (!c || !x0) return fail(PCT_ERR_INVALID_ARG, "ctx or x0 is NULL");
   pct::DeviceGuard device_guard_;

@@ -75,6 +75,7 @@ _SIGS = {
     "pct_mlp_rows": [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
                      ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)],
     "pct_block_counts": [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p],
+    "pct_block_weights": [ctypes.c_void_p],
     "pct_set_hull": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int],
     "pct_measure_roofs": [ctypes.c_int, ctypes.c_int64, ctypes.c_void_p],
     "pct_carve_hull": [ctypes.c_void_p, ctypes.c_float, ctypes.c_int32],
@@ -377,6 +378,11 @@ class Context:
         self._bind_stream()
         _check(self._L.pct_block_counts(self._h, int(block), ctypes.c_void_p(out.data_ptr())))
         return out
+
+    def block_weights(self) -> None:
+        """Form every block's DROP weights now (else the first sweep does)."""
+        self._bind_stream()
+        _check(self._L.pct_block_weights(self._h))
 
     def set_x0(self, x0) -> None:
         _check_vector(x0.reshape(-1) if hasattr(x0, "reshape") else x0, self.M, "x0", self.device)

@@ -312,3 +312,24 @@ def test_sweeps_on_a_side_stream_are_ordered_before_later_calls(pct):
             ctx.iterate(3)
         b = ctx.get_rsp()
     assert np.abs(a - b).max() <= 1e-4 * max(1.0, np.abs(a).max())
+
+
+def test_block_weights_formed_ahead_give_the_same_image(pct, oracle):
+    # pct_block_weights forms every block's s_j before the first sweep (the
+    # sweep then runs without counting); the image is the oracle's either way
+    wl = S.tiny_workload(30_000, seed=34)
+    rec = S.make_histories(wl)
+    with pct.Context(wl.grid, n_blocks=4) as ctx:
+        with pytest.raises(pct.PctError):
+            ctx.block_weights()  # nothing loaded yet
+        ctx.load(rec)
+        ctx.block_weights()
+        ctx.block_weights()  # formed already: no-op
+        for b in range(4):
+            got = ctx.block_counts(b).cpu().numpy().astype(np.float64)
+            assert np.array_equal(got, oracle.block_counts(wl.grid, rec, 4, b, mode=oracle.MODE_FP32))
+        ctx.iterate(3)
+        x = ctx.get_rsp().astype(np.float64)
+    xo = oracle.drop(wl.grid, rec, 4, 3, mode=oracle.MODE_FP32)
+    err = np.abs(x - xo) / np.maximum(np.abs(xo), 1.0)
+    assert err.max() <= 1e-3, err.max()
