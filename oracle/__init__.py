@@ -95,6 +95,8 @@ def lib():
         L.or_gauss_legendre.argtypes = [ctypes.c_int, dp, dp]
         L.or_moment.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int]
         L.or_moment.restype = ctypes.c_double
+        L.or_scatter_cov.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int, dp]
+        L.or_scatter_cov.restype = None
         L.or_mlp_table.argtypes = [gp, ctypes.c_int, dp]
         L.or_mlp_table_n.argtypes = [gp, ctypes.c_int, ctypes.c_int, dp]
         L.or_hull_ranges.argtypes = [gp, dp, rp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, i32p]
@@ -162,6 +164,16 @@ def geom_info(g, node_step: float = 0.0) -> Tuple[float, float, int, int]:
 
 def inv_beta2p2(w_cm: float, flags: int = 0) -> float:
     return lib().or_inv_beta2p2(float(w_cm), int(flags))
+
+
+def scatter_cov(a_cm: float, b_cm: float, flags: int = 0) -> np.ndarray:
+    """Scattering covariance (position-position, position-slope, slope-slope)
+    of the water slab between depths a and b (cm), the building block of the
+    MLP matrices."""
+    out = np.zeros(3)
+    lib().or_scatter_cov(ctypes.c_double(a_cm), ctypes.c_double(b_cm), ctypes.c_int(flags),
+                         out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    return out
 
 
 def gauss_legendre(n: int) -> Tuple[np.ndarray, np.ndarray]:

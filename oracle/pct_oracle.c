@@ -187,6 +187,19 @@ double or_moment(double a, double b, double c, int m, int flags) {
   return s * half;
 }
 
+/* Scattering covariance of the (position, slope) state over the water slab
+ * from depth a to depth b (cm): E0^2 (1 + 0.038 ln((b-a)/X0))^2 / X0 times
+ * [int (b-w)^2 f, int (b-w) f, int f] over [a, b], f = 1/(beta^2 p^2)
+ * (the cited MLP formalism; the log term takes the slab's own thickness).
+ * out: position-position, position-slope, slope-slope (rad^2 for the last;
+ * lengths in cm). */
+void or_scatter_cov(double a, double b, int flags, double *out) {
+  const double k = or_highland(b - a, flags);
+  out[0] = k * or_moment(a, b, b, 2, flags);
+  out[1] = k * or_moment(a, b, b, 1, flags);
+  out[2] = k * or_moment(a, b, b, 0, flags);
+}
+
 static void inv2(const double a[2][2], double o[2][2]) {
   double det = a[0][0] * a[1][1] - a[0][1] * a[1][0];
   o[0][0] = a[1][1] / det;
@@ -220,11 +233,11 @@ static void or_table_fill(double W, double du, int n, int flags, double *out) {
       continue;
     }
     double w1 = k * du / 10.0; /* node depth, cm */
-    double k1 = or_highland(w1, flags), k2 = or_highland(W - w1, flags);
-    double S1[2][2] = {{k1 * or_moment(0, w1, w1, 2, flags), k1 * or_moment(0, w1, w1, 1, flags)},
-                       {k1 * or_moment(0, w1, w1, 1, flags), k1 * or_moment(0, w1, w1, 0, flags)}};
-    double S2[2][2] = {{k2 * or_moment(w1, W, W, 2, flags), k2 * or_moment(w1, W, W, 1, flags)},
-                       {k2 * or_moment(w1, W, W, 1, flags), k2 * or_moment(w1, W, W, 0, flags)}};
+    double c1[3], c2[3];
+    or_scatter_cov(0.0, w1, flags, c1); /* entry plane -> node */
+    or_scatter_cov(w1, W, flags, c2);   /* node -> exit plane */
+    double S1[2][2] = {{c1[0], c1[1]}, {c1[1], c1[2]}};
+    double S2[2][2] = {{c2[0], c2[1]}, {c2[1], c2[2]}};
     double R0[2][2] = {{1.0, w1}, {0.0, 1.0}};
     double R1[2][2] = {{1.0, W - w1}, {0.0, 1.0}};
     double R1T[2][2] = {{1.0, 0.0}, {W - w1, 1.0}};

@@ -254,3 +254,30 @@ def test_table_is_the_conditional_mean_of_a_simulated_scattering_walk(oracle, la
         assert np.all(np.abs(c - tab[k]) <= 5.0 * se), (k, c, tab[k], se)
         worst_flat = max(worst_flat, float(np.max(np.abs(c - flat[k]) / se)))
     assert worst_flat > 30.0
+
+
+def test_scattering_covariance_follows_the_highland_width(oracle):
+    """The slope variance the oracle gives a water slab is the published
+    Highland width theta0 = 13.6 MeV / (beta c p) sqrt(L/X0) (1 + 0.038 ln(L/X0)),
+    X0 = 36.08 cm: for thin slabs at the 200 MeV entry, with beta and p from the
+    relativistic kinematics here (within 2 %: the energy polynomial's entry value
+    and the loss across the slab), so the log term's sign and size are pinned;
+    and wherever a slab sits, the factor on its 1/(beta p)^2 integral is that of
+    its own thickness (the log's argument is the sub-path length, not the depth)."""
+    mp, T, X0 = 938.272, 200.0, 36.08
+    E = T + mp
+    pc = math.sqrt(E * E - mp * mp)
+    bcp = pc * pc / E
+    for L in (0.05, 0.1, 0.2):
+        theta0 = 13.6 / bcp * math.sqrt(L / X0) * (1.0 + 0.038 * math.log(L / X0))
+        cov = oracle.scatter_cov(0.0, L)
+        assert abs(cov[2] / theta0**2 - 1.0) < 0.02, (L, cov[2], theta0**2)
+        # without the log term the variance moves by far more than that
+        assert abs(oracle.scatter_cov(0.0, L, flags=oracle.F_NO_LOG)[2] / theta0**2 - 1.0) > 0.5
+    for a, L in ((0.0, 1.0), (8.0, 1.0), (15.0, 1.0), (3.0, 5.0)):
+        cov = oracle.scatter_cov(a, a + L)
+        factor = cov[2] / oracle.moment(a, a + L, a + L, 0)
+        want = 13.6**2 * (1.0 + 0.038 * math.log(L / X0)) ** 2 / X0
+        assert abs(factor / want - 1.0) < 1e-12, (a, L)
+        # the position terms are the first and second moments about the exit
+        assert abs(cov[1] / cov[2] - oracle.moment(a, a + L, a + L, 1) / oracle.moment(a, a + L, a + L, 0)) < 1e-12
