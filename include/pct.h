@@ -241,8 +241,10 @@ PCT_API pct_status pct_block_counts(pct_ctx *ctx, int32_t block, float *out);
 
 /* Form the DROP weights S_b^-1 = diag(1/s_j) of every block of the loaded
  * histories now (Sec. 2.1: the update of block b divides by its run counts).
- * Otherwise the first pct_iterate after a load forms them while it sweeps; a
- * caller that times sweeps separately from this set-up calls it first. No-op
+ * Otherwise the first pct_iterate after a load forms them while it sweeps
+ * (cheaper: the counting rides on the sweep's own walk, where this call walks
+ * every history once more); a caller that times sweeps separately from this
+ * set-up calls it first. No-op
  * if they are formed already. PCT_ERR_STATE without loaded histories.
  * Synchronises. */
 PCT_API pct_status pct_block_weights(pct_ctx *ctx);
