@@ -432,24 +432,34 @@ __global__ void __launch_bounds__(kGroupThreads) row_fill_group_kernel(Geo g, Re
   }
 }
 
-int g_sms = 0;
+// Per-device state below is kept for devices 0 .. kMaxDevices - 1 (the
+// current device when a context works on it).
+constexpr int kMaxDevices = 64;
+
+inline int current_device() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) dev = 0;
+  return dev;
+}
 
 inline unsigned group_grid(int64_t count, int T, int per_sm) {
-  if (!g_sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (g_sms <= 0) g_sms = 1;
+  static int sms[kMaxDevices];
+  const int dev = current_device();
+  if (!sms[dev]) {
+    int n = 0;
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    sms[dev] = n > 0 ? n : 1;
   }
   const int64_t need = (count + kGroupThreads / T - 1) / (kGroupThreads / T);
-  const int64_t cap = (int64_t)g_sms * per_sm;
+  const int64_t cap = (int64_t)sms[dev] * per_sm;
   return (unsigned)(need < 1 ? 1 : (need < cap ? need : cap));
 }
 
 // Dynamic shared memory and resident blocks per SM of one drop_group_kernel
-// instantiation. The attribute is raised (and the occupancy taken) once per
-// size, outside stream capture: launch_drop_group is first reached from
-// prepare_drop_group when a context is created.
+// instantiation on one device (the attribute is a device's). The attribute
+// is raised (and the occupancy taken) once per size, outside stream capture:
+// launch_drop_group is first reached from prepare_drop_group when a context
+// is created.
 struct GroupLaunchInfo {
   size_t smem_set = 0;   // largest dynamic shared memory allowed so far
   size_t smem_occ = 0;   // size the occupancy below was taken for
@@ -458,8 +468,8 @@ struct GroupLaunchInfo {
 
 template <int T, bool kPlain, bool kCount>
 GroupLaunchInfo& launch_info() {
-  static GroupLaunchInfo info;
-  return info;
+  static GroupLaunchInfo info[kMaxDevices];
+  return info[current_device()];
 }
 
 inline size_t drop_group_smem(int T, int K) {
