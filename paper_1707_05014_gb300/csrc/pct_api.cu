@@ -323,6 +323,7 @@ pct_status pct_destroy(pct_ctx* c) {
   cudaSetDevice(c->device);
   if (c->own_stream) cudaStreamSynchronize(c->own_stream);
   if (c->stream && c->stream != c->own_stream) cudaStreamSynchronize(c->stream);
+  if (c->copy_stream) cudaStreamSynchronize(c->copy_stream);
   free_records(c);
   cudaFree(c->tab64);
   cudaFree(c->tab32);
@@ -344,6 +345,9 @@ pct_status pct_destroy(pct_ctx* c) {
     for (int i = 0; i < 3 * c->cfg.n_blocks; ++i) cudaEventDestroy(c->ev[i]);
     delete[] c->ev;
   }
+  for (int i = 0; i < 4; ++i)
+    if (c->load_ev[i]) cudaEventDestroy(c->load_ev[i]);
+  if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
   if (c->own_stream) cudaStreamDestroy(c->own_stream);
   delete c;
   return PCT_OK;
@@ -415,6 +419,7 @@ pct_status pct_load_histories(pct_ctx* c, const pct_histories* h, int flags, int
   pct::DeviceGuard device_guard_;
   PCT_CK(cudaSetDevice(c->device));
   PCT_CK(cudaStreamSynchronize(c->stream));
+  if (c->copy_stream) PCT_CK(cudaStreamSynchronize(c->copy_stream));  // copies left by a failed load
   reset_records(c);
   ++c->generation;
   const int64_t n = h->n;
@@ -438,18 +443,30 @@ pct_status pct_load_histories(pct_ctx* c, const pct_histories* h, int flags, int
     PCT_GROW(c->sort_order, c->order_cap, max_blk);
     PCT_GROW(c->sort_hist, c->hist_cap, pct::kSortHistEntries);
   }
-  if (flags == PCT_LOAD_HOST) PCT_GROW(c->staging, c->staging_cap, max_blk * 11);
+  if (flags == PCT_LOAD_HOST) {
+    PCT_GROW(c->staging, c->staging_cap, 2 * max_blk * 11);
+    if (!c->copy_stream) PCT_CK(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+    for (int i = 0; i < 4; ++i)
+      if (!c->load_ev[i]) PCT_CK(cudaEventCreateWithFlags(&c->load_ev[i], cudaEventDisableTiming));
+  }
 
-  // per block: bring the records to the device, validate, order (or copy)
+  // per block: bring the records to the device, validate, order (or copy).
+  // Host records go through two staging slots: block b + 1 is copied on the
+  // copy stream while block b is validated and ordered on the context's stream.
   PCT_CK(cudaMemsetAsync(c->first_bad, 0xff, sizeof(unsigned long long), c->stream));
   for (int b = 0; b < B; ++b) {
     const int64_t lo = block_lo(c, b), cnt = block_lo(c, b + 1) - lo;
     Rec blk;
     if (flags == PCT_LOAD_HOST) {
+      const int slot = b & 1;
+      float* dst = c->staging + (size_t)slot * 11 * max_blk;
+      if (b >= 2) PCT_CK(cudaStreamWaitEvent(c->copy_stream, c->load_ev[2 + slot], 0));  // block b - 2 consumed
       for (int f = 0; f < 11; ++f)
-        PCT_CK(cudaMemcpyAsync(c->staging + (size_t)f * max_blk, src[f] + lo, (size_t)cnt * sizeof(float),
-                               cudaMemcpyHostToDevice, c->stream));
-      blk = rec_at(c->staging, max_blk);
+        PCT_CK(cudaMemcpyAsync(dst + (size_t)f * max_blk, src[f] + lo, (size_t)cnt * sizeof(float),
+                               cudaMemcpyHostToDevice, c->copy_stream));
+      PCT_CK(cudaEventRecord(c->load_ev[slot], c->copy_stream));
+      PCT_CK(cudaStreamWaitEvent(c->stream, c->load_ev[slot], 0));
+      blk = rec_at(dst, max_blk);
     } else {
       blk = rec_offset(src, lo);
     }
@@ -460,9 +477,10 @@ pct_status pct_load_histories(pct_ctx* c, const pct_histories* h, int flags, int
                                     c->stream));
       c->launches += 5;
     } else if (!in_place) {
-      PCT_CK(pct::launch_copy_block(blk, cnt, lo, c->rec, nullptr, c->stream));
+      PCT_CK(pct::launch_copy_block(blk, cnt, lo, c->rec, c->stream));
       c->launches += 1;
     }
+    if (flags == PCT_LOAD_HOST) PCT_CK(cudaEventRecord(c->load_ev[2 + (b & 1)], c->stream));
   }
   unsigned long long fb = 0;
   PCT_CK(cudaMemcpyAsync(&fb, c->first_bad, sizeof fb, cudaMemcpyDeviceToHost, c->stream));

@@ -29,7 +29,12 @@ struct pct_ctx {
   // and the load's scratch (host staging, sort keys, order, bins).
   int64_t rec_cap = 0, where_cap = 0, range_cap = 0, staging_cap = 0, key_cap = 0, order_cap = 0, hist_cap = 0;
   int64_t* where_buf = nullptr;
-  float* staging = nullptr;
+  float* staging = nullptr;   // two slots of the largest block's 11 arrays (host loads)
+  // Host loads: the next block's copy (copy_stream) overlaps the current
+  // block's validation and ordering (stream). load_ev[s]: slot s copied;
+  // load_ev[2 + s]: slot s consumed. Created by the first host load.
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t load_ev[4] = {};
   unsigned* sort_key = nullptr;
   unsigned* sort_order = nullptr;
   unsigned* sort_hist = nullptr;

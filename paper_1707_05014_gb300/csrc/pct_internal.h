@@ -131,12 +131,12 @@ cudaError_t launch_validate(const Rec& r, int64_t n, int64_t base, float pos_lim
                             cudaStream_t s);
 // Order n records of one block by (angle bin, entry lateral bin) into
 // dst_rec[base .. base+n); where[base + i] receives the stored position of
-// input record i (where may be null). key/order: n entries; hist:
+// input record i (where must not be null). key/order: n entries; hist:
 // kSortHistEntries (the bins and the scan's tile sums).
 cudaError_t launch_sort_block(const Rec& src, int64_t n, int64_t base, float lat_lim, Rec dst_rec, int64_t* where,
                               unsigned* key, unsigned* hist, unsigned* order, cudaStream_t s);
-// Copy n records into dst_rec[base ..) in input order (where as above).
-cudaError_t launch_copy_block(const Rec& src, int64_t n, int64_t base, Rec dst_rec, int64_t* where, cudaStream_t s);
+// Copy n records into dst_rec[base ..) in input order.
+cudaError_t launch_copy_block(const Rec& src, int64_t n, int64_t base, Rec dst_rec, cudaStream_t s);
 cudaError_t launch_count(const Geo& g, const Rec& r, const float4* tab, const Hull& hull, int64_t first, int64_t count,
                          unsigned int* cnt, int threads, cudaStream_t s);
 cudaError_t launch_inv_counts(const unsigned int* cnt, float* inv_s, int64_t M, cudaStream_t s);

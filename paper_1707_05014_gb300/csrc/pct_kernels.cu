@@ -494,37 +494,45 @@ __global__ void __launch_bounds__(kScanThreads) scan_tiles_kernel(unsigned* __re
     if (base + q < nb) hist[base + q] = tile[q];
 }
 
-__global__ void scatter_kernel(const unsigned* __restrict__ key, int64_t n, unsigned* __restrict__ offs,
-                               unsigned* __restrict__ order) {
+// Counting-sort placement of record i: its stored position p (the next slot
+// of its bin), order[p] = i, and where[base + i] = base + p (written here, in
+// load order, so that the map is stored with coalesced writes).
+__global__ void scatter_kernel(const unsigned* __restrict__ key, int64_t n, int64_t base, unsigned* __restrict__ offs,
+                               unsigned* __restrict__ order, int64_t* __restrict__ where) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const unsigned p = atomicAdd(offs + key[i], 1u);
   order[p] = (unsigned)i;
+  where[base + i] = base + p;
 }
 
-struct RecOut {
-  float *t0, *v0, *st0, *sv0, *t2, *v2, *st2, *sv2, *wepl, *cphi, *sphi;
-};
+__device__ __forceinline__ const float* field_of(const Rec& r, int f) {
+  switch (f) {
+    case 0: return r.t0;
+    case 1: return r.v0;
+    case 2: return r.st0;
+    case 3: return r.sv0;
+    case 4: return r.t2;
+    case 5: return r.v2;
+    case 6: return r.st2;
+    case 7: return r.sv2;
+    case 8: return r.wepl;
+    case 9: return r.cphi;
+    default: return r.sphi;
+  }
+}
 
-// dst[base + p] = src[order[p]] for every field; where[base + order[p]] = base + p
-__global__ void gather_kernel(Rec src, RecOut dst, const unsigned* __restrict__ order, int64_t n, int64_t base,
-                              int64_t* __restrict__ where) {
-  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+// dst.f[base + p] = src.f[order[p]] (order null: src.f[p]) for record field
+// f = blockIdx.y. The CTAs of one field are dispatched before those of the
+// next, so the random reads of a block's reordering stay within one field
+// (4 B per record: 80 MB for 20M records), which the L2 holds, instead of
+// spreading over all eleven.
+__global__ void gather_kernel(Rec src, Rec dst, const unsigned* __restrict__ order, int64_t n, int64_t base) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n) return;
+  const int f = blockIdx.y;
   const int64_t i = order ? (int64_t)order[p] : p;
-  const int64_t o = base + p;
-  dst.t0[o] = src.t0[i];
-  dst.v0[o] = src.v0[i];
-  dst.st0[o] = src.st0[i];
-  dst.sv0[o] = src.sv0[i];
-  dst.t2[o] = src.t2[i];
-  dst.v2[o] = src.v2[i];
-  dst.st2[o] = src.st2[i];
-  dst.sv2[o] = src.sv2[i];
-  dst.wepl[o] = src.wepl[i];
-  dst.cphi[o] = src.cphi[i];
-  dst.sphi[o] = src.sphi[i];
-  if (where) where[base + i] = o;
+  const_cast<float*>(field_of(dst, f))[base + p] = field_of(src, f)[i];
 }
 
 inline unsigned grid_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
@@ -548,22 +556,14 @@ cudaError_t launch_sort_block(const Rec& src, int64_t n, int64_t base, float lat
     scan_tile_offsets_kernel<<<1, kScanMaxTiles, 0, s>>>(tile_sum, nt);
     scan_tiles_kernel<<<nt, kScanThreads, 0, s>>>(hist, nb, tile_sum);
   }
-  scatter_kernel<<<grid_for(n, 256), 256, 0, s>>>(key, n, hist, order);
-  RecOut d{const_cast<float*>(dst_rec.t0), const_cast<float*>(dst_rec.v0), const_cast<float*>(dst_rec.st0),
-           const_cast<float*>(dst_rec.sv0), const_cast<float*>(dst_rec.t2), const_cast<float*>(dst_rec.v2),
-           const_cast<float*>(dst_rec.st2), const_cast<float*>(dst_rec.sv2), const_cast<float*>(dst_rec.wepl),
-           const_cast<float*>(dst_rec.cphi), const_cast<float*>(dst_rec.sphi)};
-  gather_kernel<<<grid_for(n, 256), 256, 0, s>>>(src, d, order, n, base, where);
+  scatter_kernel<<<grid_for(n, 256), 256, 0, s>>>(key, n, base, hist, order, where);
+  gather_kernel<<<dim3(grid_for(n, 256), 11), 256, 0, s>>>(src, dst_rec, order, n, base);
   return cudaGetLastError();
 }
 
-cudaError_t launch_copy_block(const Rec& src, int64_t n, int64_t base, Rec dst_rec, int64_t* where, cudaStream_t s) {
+cudaError_t launch_copy_block(const Rec& src, int64_t n, int64_t base, Rec dst_rec, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  RecOut d{const_cast<float*>(dst_rec.t0), const_cast<float*>(dst_rec.v0), const_cast<float*>(dst_rec.st0),
-           const_cast<float*>(dst_rec.sv0), const_cast<float*>(dst_rec.t2), const_cast<float*>(dst_rec.v2),
-           const_cast<float*>(dst_rec.st2), const_cast<float*>(dst_rec.sv2), const_cast<float*>(dst_rec.wepl),
-           const_cast<float*>(dst_rec.cphi), const_cast<float*>(dst_rec.sphi)};
-  gather_kernel<<<grid_for(n, 256), 256, 0, s>>>(src, d, nullptr, n, base, where);
+  gather_kernel<<<dim3(grid_for(n, 256), 11), 256, 0, s>>>(src, dst_rec, nullptr, n, base);
   return cudaGetLastError();
 }
 

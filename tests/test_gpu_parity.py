@@ -238,6 +238,40 @@ def test_tvs_parity(pct, oracle, carp):
     assert oracle.tv_value(wl.grid, x) < oracle.tv_value(wl.grid, plain)
 
 
+def test_host_load_through_two_staging_slots_matches_a_device_copy(pct, oracle):
+    # Host records pass through two staging slots (block b + 1 copied while
+    # block b is validated and ordered). Seven ragged blocks reuse each slot
+    # three times: the rows in load order and the run counts equal those of a
+    # device-copy load and the oracle's, and a bad record in the last block is
+    # found.
+    import torch
+
+    wl = S.tiny_workload(7003, seed=16)
+    g = wl.grid
+    rec = S.make_histories(wl)
+    hmin = min(g.hx, g.hy, g.hz)
+    with pct.Context(g, n_blocks=7) as host, pct.Context(g, n_blocks=7) as dev:
+        host.load(rec)
+        dev.load({k: torch.from_numpy(v).cuda() for k, v in rec.items()})
+        a = _cmp_rows(oracle, g, rec, host, 0, wl.n, hmin)
+        b = [t.cpu().numpy() for t in dev.rows(0, wl.n)]
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
+        host.iterate(2)
+        dev.iterate(2)
+        x, y = host.get_rsp(), dev.get_rsp()
+        assert np.abs(x - y).max() <= 1e-4 * max(1.0, np.abs(y).max())
+        bad = {k: v.copy() for k, v in rec.items()}
+        bad["sv2"][wl.n - 2] = np.inf
+        with pytest.raises(pct.PctError) as ei:
+            host.load(bad)
+        assert ei.value.code == -2 and host.first_bad == wl.n - 2
+        host.load(rec)
+        host.iterate(2)
+        z = host.get_rsp()
+    xo = oracle.drop(g, rec, 7, 2, mode=oracle.MODE_FP32)
+    assert np.max(np.abs(z - xo) / np.maximum(np.abs(xo), 1.0)) <= 1e-3
+
+
 def test_empty_load_is_rejected(pct):
     wl = S.tiny_workload(10, seed=12)
     rec = {k: v[:0] for k, v in S.make_histories(wl).items()}
