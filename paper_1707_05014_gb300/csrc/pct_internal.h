@@ -18,8 +18,11 @@ constexpr int kQOff = 16;
 constexpr float kQClamp = 1000.0f;       // |q| clamp in voxels (never reached for valid records)
 constexpr int kMaxNodes = 2048;          // K + 1 limit (shared-memory MLP table)
 constexpr int kMaxDim = 512;             // per-axis voxel limit
-constexpr int kSortAngles = 256;         // load-time ordering: gantry-angle bins
-constexpr int kSortLateral = 4096;       // load-time ordering: mid-path lateral-position bins
+constexpr int kSortAngles = 128;         // load-time ordering: gantry-angle bins (49 mrad; the 90 angles of the head workloads each have their own)
+constexpr int kSortMid = 1024;           // load-time ordering: mid-path lateral-position bins
+constexpr int kSortDiff = 32;            // load-time ordering: exit-minus-entry lateral bins
+constexpr float kSortDiffLim = 16.f;     // |t2 - t0| range of the exit-minus-entry bins (mm)
+constexpr int kSortLateral = kSortMid * kSortDiff;
 // entries of the ordering's bin array: the bins, then one sum per scan tile
 constexpr int64_t kSortHistEntries = (int64_t)kSortAngles * kSortLateral + 1024;
 constexpr int kRowCap = 512;             // runs kept per history between the fused kernel's two passes
