@@ -473,7 +473,7 @@ pct_status pct_load_histories(pct_ctx* c, const pct_histories* h, int flags, int
     PCT_CK(pct::launch_validate(blk, cnt, lo, c->pos_limit, c->first_bad, c->stream));
     c->launches += 1;
     if (sort) {
-      PCT_CK(pct::launch_sort_block(blk, cnt, lo, c->pos_limit, c->rec, c->where, c->sort_key, c->sort_hist, c->sort_order,
+      PCT_CK(pct::launch_sort_block(blk, cnt, lo, c->pos_limit, c->tab32, c->K, c->rec, c->where, c->sort_key, c->sort_hist, c->sort_order,
                                     c->stream));
       c->launches += 5;
     } else if (!in_place) {

@@ -19,9 +19,9 @@ constexpr float kQClamp = 1000.0f;       // |q| clamp in voxels (never reached f
 constexpr int kMaxNodes = 2048;          // K + 1 limit (shared-memory MLP table)
 constexpr int kMaxDim = 512;             // per-axis voxel limit
 constexpr int kSortAngles = 128;         // load-time ordering: gantry-angle bins (49 mrad; the 90 angles of the head workloads each have their own)
-constexpr int kSortMid = 1024;           // load-time ordering: mid-path lateral-position bins
-constexpr int kSortDiff = 32;            // load-time ordering: exit-minus-entry lateral bins
-constexpr float kSortDiffLim = 16.f;     // |t2 - t0| range of the exit-minus-entry bins (mm)
+constexpr int kSortMid = 1024;           // load-time ordering: bins of the MLP's lateral midpoint between the quarter points
+constexpr int kSortDiff = 32;            // load-time ordering: bins of the MLP's lateral change between the quarter points
+constexpr float kSortDiffLim = 8.f;      // range +-kSortDiffLim (mm) of that change
 constexpr int kSortLateral = kSortMid * kSortDiff;
 // entries of the ordering's bin array: the bins, then one sum per scan tile
 constexpr int64_t kSortHistEntries = (int64_t)kSortAngles * kSortLateral + 1024;
@@ -132,12 +132,14 @@ cudaError_t launch_carve_hull(const Geo& g, const Rec& r, const float4* tab, int
                               uint8_t* out, uint8_t* tmp, cudaStream_t s);
 cudaError_t launch_validate(const Rec& r, int64_t n, int64_t base, float pos_limit, unsigned long long* first_bad,
                             cudaStream_t s);
-// Order n records of one block by (angle bin, entry lateral bin) into
+// Order n records of one block by (angle bin, lateral bins of the MLP at the
+// quarter points; tab: the FP32 MLP table of K + 1 nodes) into
 // dst_rec[base .. base+n); where[base + i] receives the stored position of
 // input record i (where must not be null). key/order: n entries; hist:
 // kSortHistEntries (the bins and the scan's tile sums).
-cudaError_t launch_sort_block(const Rec& src, int64_t n, int64_t base, float lat_lim, Rec dst_rec, int64_t* where,
-                              unsigned* key, unsigned* hist, unsigned* order, cudaStream_t s);
+cudaError_t launch_sort_block(const Rec& src, int64_t n, int64_t base, float lat_lim, const float4* tab, int K,
+                              Rec dst_rec, int64_t* where, unsigned* key, unsigned* hist, unsigned* order,
+                              cudaStream_t s);
 // Copy n records into dst_rec[base ..) in input order.
 cudaError_t launch_copy_block(const Rec& src, int64_t n, int64_t base, Rec dst_rec, cudaStream_t s);
 cudaError_t launch_count(const Geo& g, const Rec& r, const float4* tab, const Hull& hull, int64_t first, int64_t count,

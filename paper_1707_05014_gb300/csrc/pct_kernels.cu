@@ -386,33 +386,35 @@ __global__ void row_fill_kernel(Geo g, Rec r, const float4* __restrict__ tab_g, 
 }
 
 
-// ---- load-time ordering of each block: (gantry-angle bin, mid-path lateral
-// bin, exit-minus-entry lateral bin), so that the 32 lanes of a warp trace
-// nearly the same path and cross the same faces at the same node steps.
+// ---- load-time ordering of each block: (gantry-angle bin, lateral bin of the
+// path's midpoint, bin of its lateral change), so that the 32 lanes of a warp
+// trace nearly the same path and cross the same faces at the same node steps.
 // Counting sort: key -> histogram -> exclusive scan -> scatter.
 //
-// Two paths of one angle whose lateral positions differ by dm halfway between
-// the planes and by dd in exit minus entry are apart by at most |dm| + |dd|/2
-// along the slab, so the lateral bins are twice as wide in t2 - t0 as in the
-// midpoint (1024 midpoint bins over the validated range, 32 bins over +-16 mm
-// of t2 - t0, which holds the multiple-scattering displacement of a head-sized
-// object many times over). On the 1e9-history head workload (90 angles,
-// 2.2e5 histories per angle and block) a central bin holds about a warp's
-// worth of histories, and a warp's paths stay within about a millimetre of
-// each other; ordering by the midpoint alone left the entry and exit ends of
-// a warp's paths millimetres apart.
-__global__ void sort_key_kernel(Rec r, int64_t n, int n_ang, int n_lat, float lat_lim, unsigned* __restrict__ key) {
+// The key samples each history's own MLP (Sec. 2) at the quarter points of the
+// slab, nodes k1 = K/4 and k3 = K - K/4 (lateral positions ta, tc, from the
+// FP32 table). Two paths of one angle whose (ta + tc)/2 differ by dm and whose
+// tc - ta differ by dd are about |dm| + |dd| u/R apart at depth u, the scattering
+// slopes included; the bins are 1024 over the validated lateral range for the
+// midpoint (0.47 mm on the 200x200x48 grid) and 32 over +-8 mm for the change
+// (0.5 mm). On the 1e9-history head workload (90 angles, 2.2e5 histories per
+// angle and block) a central bin holds about a warp's worth of histories.
+__global__ void sort_key_kernel(Rec r, int64_t n, int n_ang, int n_lat, float lat_lim, const float4* __restrict__ tab,
+                                int k1, int k3, unsigned* __restrict__ key) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const float two_pi = 6.283185307f;
   float a = atan2f(r.sphi[i], r.cphi[i]);
   if (a < 0.f) a += two_pi;
   int ab = min(n_ang - 1, max(0, (int)(a * (n_ang / two_pi) + 0.5f) % n_ang));
-  const float t0 = r.t0[i], t2 = r.t2[i];
-  const float tmid = 0.5f * (t0 + t2);
+  const float t0 = r.t0[i], t2 = r.t2[i], st0 = r.st0[i], st2 = r.st2[i];
+  const float4 c1 = __ldg(tab + k1), c3 = __ldg(tab + k3);
+  const float ta = fmaf(c1.w, st2, fmaf(c1.z, t2, fmaf(c1.y, st0, c1.x * t0)));
+  const float tc = fmaf(c3.w, st2, fmaf(c3.z, t2, fmaf(c3.y, st0, c3.x * t0)));
+  const float tmid = 0.5f * (ta + tc);
   int tb = (int)floorf((tmid + lat_lim) * (kSortMid / (2.f * lat_lim)));
   tb = min(kSortMid - 1, max(0, tb));
-  int db = (int)floorf((t2 - t0 + kSortDiffLim) * (kSortDiff / (2.f * kSortDiffLim)));
+  int db = (int)floorf((tc - ta + kSortDiffLim) * (kSortDiff / (2.f * kSortDiffLim)));
   db = min(kSortDiff - 1, max(0, db));
   key[i] = (unsigned)(ab * n_lat + tb * kSortDiff + db);
 }
@@ -551,13 +553,14 @@ inline unsigned grid_for(int64_t n, int threads) { return (unsigned)((n + thread
 
 }  // namespace
 
-cudaError_t launch_sort_block(const Rec& src, int64_t n, int64_t base, float lat_lim, Rec dst_rec,
-                              int64_t* where, unsigned* key, unsigned* hist, unsigned* order, cudaStream_t s) {
+cudaError_t launch_sort_block(const Rec& src, int64_t n, int64_t base, float lat_lim, const float4* tab, int K,
+                              Rec dst_rec, int64_t* where, unsigned* key, unsigned* hist, unsigned* order,
+                              cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   const int n_ang = kSortAngles, n_lat = kSortLateral;
   cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(unsigned) * n_ang * n_lat, s);
   if (e != cudaSuccess) return e;
-  sort_key_kernel<<<grid_for(n, 256), 256, 0, s>>>(src, n, n_ang, n_lat, lat_lim, key);
+  sort_key_kernel<<<grid_for(n, 256), 256, 0, s>>>(src, n, n_ang, n_lat, lat_lim, tab, K / 4, K - K / 4, key);
   histogram_kernel<<<grid_for(n, 256), 256, 0, s>>>(key, n, hist);
   {
     const int nb = n_ang * n_lat, nt = (nb + kScanTile - 1) / kScanTile;
