@@ -24,6 +24,7 @@ workload on the host cores.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import math
 import os
@@ -213,10 +214,12 @@ def main_workload(args, rank: int = 0):
     from paper_1707_05014_gb300 import synthetic as S
 
     if args.workload == "head":
-        return S.head_workload(args.n or 50_000_000, seed=2 + rank)
-    if args.workload == "tiny":
-        return S.tiny_workload(args.n or 100_000, seed=1 + rank)
-    return S.head200_workload(args.n or 1_000_000_000, seed=5 + rank)
+        wl = S.head_workload(args.n or 50_000_000, seed=2 + rank)
+    elif args.workload == "tiny":
+        wl = S.tiny_workload(args.n or 100_000, seed=1 + rank)
+    else:
+        wl = S.head200_workload(args.n or 1_000_000_000, seed=5 + rank)
+    return dataclasses.replace(wl, n_blocks=args.blocks) if args.blocks else wl
 
 
 def grid_text(g) -> str:
@@ -795,6 +798,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=None, help="histories per GPU (default: the workload's own)")
+    ap.add_argument("--blocks", type=int, default=0,
+                    help="DROP blocks of the throughput workload (default: the workload's own; a profile of one "
+                         "full-size launch uses --n 20000000 --blocks 1)")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--e2e-sweeps", type=int, default=10)
     ap.add_argument("--cpu-sample", type=int, default=1_000_000)
