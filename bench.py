@@ -668,8 +668,10 @@ def run_ours(args):
     alu_peak = ALU_LANES_PER_SM * N_SMS * sm_mhz * 1e6 / 1e12  # Tops/s
     achieved = ops_per_history * per_block / avg_fused_s / 1e12
     cnt = ncu_counters()
-    # the counters were taken on the one-lane kernel without a hull
-    traffic = cnt["dram_bytes_per_history"] * per_block if cnt and args.lanes <= 1 and not args.hull else None
+    # the counters were taken on the one-lane kernel without a hull, on one launch of the 200x200x48 workload
+    same = (cnt and args.lanes <= 1 and not args.hull and args.workload == cnt.get("workload")
+            and per_block == cnt.get("histories"))
+    traffic = cnt["dram_bytes_per_history"] * per_block if same else None
     hbm_achieved = 44.0 * per_block / avg_fused_s / 1e9
     # the library's own roof microbenchmarks: L2 atomics, L2 gathers, ALU issue
     mr = P.measure_roofs(local)
