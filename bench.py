@@ -128,6 +128,15 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
+def traffic_per_launch(cnt, args, per_block):
+    """DRAM bytes of one fused launch from the committed counters, or None
+    unless they were taken on this configuration: the one-lane kernel without
+    a hull, the same workload and the same histories per launch."""
+    same = (cnt is not None and args.lanes <= 1 and not args.hull and args.workload == cnt.get("workload")
+            and per_block == cnt.get("histories"))
+    return cnt["dram_bytes_per_history"] * per_block if same else None
+
+
 def ncu_counters():
     """DRAM bytes per history of the fused kernel from the committed ncu summary,
     if it was taken on the current kernel sources."""
@@ -667,11 +676,7 @@ def run_ours(args):
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
     alu_peak = ALU_LANES_PER_SM * N_SMS * sm_mhz * 1e6 / 1e12  # Tops/s
     achieved = ops_per_history * per_block / avg_fused_s / 1e12
-    cnt = ncu_counters()
-    # the counters were taken on the one-lane kernel without a hull, on one launch of the 200x200x48 workload
-    same = (cnt and args.lanes <= 1 and not args.hull and args.workload == cnt.get("workload")
-            and per_block == cnt.get("histories"))
-    traffic = cnt["dram_bytes_per_history"] * per_block if same else None
+    traffic = traffic_per_launch(ncu_counters(), args, per_block)
     hbm_achieved = 44.0 * per_block / avg_fused_s / 1e9
     # the library's own roof microbenchmarks: L2 atomics, L2 gathers, ALU issue
     mr = P.measure_roofs(local)

@@ -79,6 +79,22 @@ def test_traffic_counters_are_used_only_for_the_sources_they_were_taken_on(monke
     assert bench.ncu_counters() is None
 
 
+def test_traffic_is_reported_only_for_the_captured_configuration():
+    sys.path.insert(0, ROOT)
+    import argparse
+    import bench
+
+    with open(os.path.join(ROOT, "profiles", "drop_fused_head200_counters.json")) as f:
+        rec = json.load(f)
+    ok = argparse.Namespace(lanes=1, hull=False, workload=rec["workload"])
+    n = rec["histories"]
+    assert bench.traffic_per_launch(rec, ok, n) == rec["dram_bytes_per_history"] * n
+    assert bench.traffic_per_launch(None, ok, n) is None
+    assert bench.traffic_per_launch(rec, ok, n // 2) is None  # another launch size
+    for bad in (dict(lanes=32), dict(hull=True), dict(workload="head")):
+        assert bench.traffic_per_launch(rec, argparse.Namespace(**{**vars(ok), **bad}), n) is None
+
+
 def test_oracle_is_loaded_only_by_tests_smoke_and_the_cpu_legs():
     # The oracle is test infrastructure: the package never imports it, and
     # bench.py loads it in one function only, the timing of the CPU baseline and
