@@ -100,11 +100,12 @@ typedef struct pct_config {
                                results over the strings touching each voxel.
                                Not accepted by pct_batch_create.             */
 #define PCT_FLAG_NO_SORT 8  /* keep each block in load order (default: each
-                               block is stored ordered by gantry angle and
-                               entry lateral position, which keeps the lanes
-                               of a warp on near-parallel paths; membership
-                               of the blocks, and so the result, is unchanged
-                               up to floating-point summation order)          */
+                               block is stored ordered by gantry angle and by
+                               the lateral position of the history's MLP at the
+                               quarter points of the slab, which keeps the
+                               lanes of a warp on nearly the same path;
+                               membership of the blocks, and so the result, is
+                               unchanged up to floating-point summation order) */
 
 /* One history per index: entry state at u = -R, exit state at u = +R, the
  * WEPL b_i (mm) and the gantry angle as cos/sin (Sec. 2: each proton is
@@ -257,7 +258,13 @@ PCT_API pct_status pct_set_x0(pct_ctx *ctx, const float *x0, int on_device);
  * order, every history i of b contributes lambda (b_i - a_i.x)/|a_i|^2 a_i
  * (a_i recomputed from the MLP, a_i.x compensated), then
  * x_j += delta_j / s_j. Asynchronous on the context stream; one CUDA graph
- * per sweep. */
+ * per sweep. The first sweep after a load also forms the block weights
+ * unless pct_block_weights did: with one lane per history and no hull, CARP
+ * or TVS it adds each run's update and count as one float pair; it then waits
+ * for that sweep, and if a voxel collected 2^24 or more runs of one block
+ * (where a float count is no longer exact) it undoes the sweep, forms the
+ * weights with integer counts and sweeps again. It allocates 12 bytes per
+ * voxel for this on its first use. */
 PCT_API pct_status pct_iterate(pct_ctx *ctx, int32_t n_sweeps);
 
 /* ---- A DROP block shared by several processes (Sec. 1 and Sec. 3.1: the

@@ -330,6 +330,9 @@ pct_status pct_destroy(pct_ctx* c) {
   cudaFree(c->x);
   cudaFree(c->delta);
   cudaFree(c->cnt);
+  cudaFree(c->pair);
+  cudaFree(c->pair_overflow);
+  cudaFree(c->x_save);
   cudaFree(c->first_bad);
   cudaFree(c->acc);
   cudaFree(c->carp_sum);
@@ -698,6 +701,14 @@ pct_status pct_set_x0(pct_ctx* c, const float* x0, int on_device) {
   return PCT_OK;
 }
 
+// The first sweep after a load adds each run's update and count by one vector
+// reduction (pct::launch_drop_fused_pair) for one lane per history without a
+// hull, CARP or TVS; the others count with integer atomics beside the update.
+static bool paired_counting(const pct_ctx* c) {
+  return c->cfg.threads_per_proton <= 1 && !c->hull_mask && !(c->cfg.flags & PCT_FLAG_CARP) &&
+         !(c->cfg.tvs_beta0 > 0.f);
+}
+
 // One sweep as a CUDA graph. counting: the first sweep after a load also
 // counts each block's runs (cnt) and forms its weights inv_s just before the
 // block's update, in place of a separate counting pass.
@@ -716,6 +727,14 @@ static pct_status build_sweep_graph(pct_ctx* c, bool counting, cudaGraphExec_t* 
   if (tvs && carp)
     err = pct::launch_tvs(c->x, c->grid.nx, c->grid.ny, c->grid.nz, tp, c->tv_g, c->tv_xp, c->tv_acc, c->tv_state, s);
   if (carp && err == cudaSuccess) err = cudaMemcpyAsync(c->carp_x0, c->x, xbytes, cudaMemcpyDeviceToDevice, s);
+  const bool pair = counting && paired_counting(c);
+  if (pair) {
+    // the image before the sweep (kept to redo it with integer counts), a clean
+    // update-and-count array and overflow flag
+    err = cudaMemcpyAsync(c->x_save, c->x, xbytes, cudaMemcpyDeviceToDevice, s);
+    if (err == cudaSuccess) err = cudaMemsetAsync(c->pair, 0, (size_t)c->M * sizeof(float2), s);
+    if (err == cudaSuccess) err = cudaMemsetAsync(c->pair_overflow, 0, sizeof(int), s);
+  }
   const int S = carp ? c->cfg.carp_strings : 1;
   for (int st = 0; st < S && err == cudaSuccess; ++st) {
     // CARP: string st sweeps blocks [st B/S, (st+1) B/S) on a copy of the
@@ -727,6 +746,18 @@ static pct_status build_sweep_graph(pct_ctx* c, bool counting, cudaGraphExec_t* 
       if (tvs && !carp)
         err = pct::launch_tvs(c->x, c->grid.nx, c->grid.ny, c->grid.nz, tp, c->tv_g, c->tv_xp, c->tv_acc,
                               c->tv_state, s);
+      if (pair) {
+        if (err == cudaSuccess && c->ev) err = cudaEventRecordWithFlags(c->ev[3 * b], s, cudaEventRecordExternal);
+        if (err == cudaSuccess)
+          err = pct::launch_drop_fused_pair(c->geo, c->rec, c->tab32, lo, hi - lo, c->x, c->pair, c->cfg.lambda,
+                                            c->cfg.flags, s);
+        if (err == cudaSuccess && c->ev) err = cudaEventRecordWithFlags(c->ev[3 * b + 1], s, cudaEventRecordExternal);
+        if (err == cudaSuccess)
+          err = pct::launch_drop_apply_pair(c->x, c->pair, c->inv_s + (size_t)b * c->M, c->M, clamp, c->cfg.clamp_min,
+                                            c->pair_overflow, s);
+        if (err == cudaSuccess && c->ev) err = cudaEventRecordWithFlags(c->ev[3 * b + 2], s, cudaEventRecordExternal);
+        continue;
+      }
       if (err == cudaSuccess && counting) err = cudaMemsetAsync(c->cnt, 0, (size_t)c->M * sizeof(unsigned int), s);
       if (err == cudaSuccess && c->ev) err = cudaEventRecordWithFlags(c->ev[3 * b], s, cudaEventRecordExternal);
       if (err == cudaSuccess)
@@ -774,15 +805,35 @@ pct_status pct_iterate(pct_ctx* c, int32_t n_sweeps) {
   const int64_t per_sweep = 2 * c->cfg.n_blocks + ((c->cfg.flags & PCT_FLAG_CARP) ? c->cfg.carp_strings + 1 : 0);
   if (!c->weights_ready) {
     // first sweep after a load: counts the block weights as it goes
+    const bool pair = paired_counting(c);
+    if (pair) {
+      if (!c->pair) PCT_ALLOC(c->pair, (size_t)c->M * sizeof(float2));
+      if (!c->pair_overflow) PCT_ALLOC(c->pair_overflow, sizeof(int));
+      if (!c->x_save) PCT_ALLOC(c->x_save, (size_t)c->M * sizeof(float));
+    }
     if (!c->sweep_count) {
       pct_status st = build_sweep_graph(c, true, &c->sweep_count);
       if (st != PCT_OK) return st;
     }
     PCT_CK(cudaGraphLaunch(c->sweep_count, c->stream));
+    c->launches += pair ? per_sweep : per_sweep + c->cfg.n_blocks;
+    bool redo = false;
+    if (pair) {
+      // a float count that reached 2^24 may have lost runs: undo the sweep,
+      // form the weights with integer counts and sweep again
+      int overflow = 0;
+      PCT_CK(cudaMemcpyAsync(&overflow, c->pair_overflow, sizeof overflow, cudaMemcpyDeviceToHost, c->stream));
+      PCT_CK(cudaStreamSynchronize(c->stream));
+      if (overflow) {
+        PCT_CK(cudaMemcpyAsync(c->x, c->x_save, (size_t)c->M * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
+        pct_status st = block_weights(c);
+        if (st != PCT_OK) return st;
+        redo = true;
+      }
+    }
     c->weights_ready = true;
-    c->launches += per_sweep + c->cfg.n_blocks;
     c->swept = true;
-    --n_sweeps;
+    if (!redo) --n_sweeps;
   }
   if (n_sweeps > 0 && !c->sweep) {
     pct_status st = build_sweep_graph(c, false, &c->sweep);

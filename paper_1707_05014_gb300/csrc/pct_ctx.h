@@ -42,6 +42,13 @@ struct pct_ctx {
   float* delta = nullptr;
   float* inv_s = nullptr;  // B x M
   unsigned int* cnt = nullptr;
+  // The first sweep after a load without a hull, CARP or TVS: the block's
+  // update and run counts side by side (M float2), a flag set where a float
+  // count reached 2^24, and the image before that sweep (to redo it with exact
+  // integer counts if the flag is set). Allocated by the first such sweep.
+  float2* pair = nullptr;
+  int* pair_overflow = nullptr;
+  float* x_save = nullptr;
   unsigned long long* first_bad = nullptr;
   double* acc = nullptr;  // residual accumulator
   float* carp_sum = nullptr;    // CARP: sum of string estimates per voxel

@@ -18,6 +18,11 @@ __device__ __forceinline__ float ld_weak(const float* p) {
   return v;
 }
 
+// pair[0] += u, pair[1] += 1 in one vector reduction (sm_90 and later).
+__device__ __forceinline__ void red_add_pair(float2* p, float u) {
+  asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(u), "f"(1.0f) : "memory");
+}
+
 // MLP nodes -> walk -> compensated a_i.x and |a_i|^2 -> relaxed residual ->
 // scatter-add into delta. The walk only records the row (voxel, chord) in
 // thread-local memory; the gather of x for a_i.x and the scatter replay the
@@ -34,10 +39,17 @@ __device__ __forceinline__ float ld_weak(const float* p) {
 // cnt (kCount): also add every run to the block's run counts s_j (the first
 // sweep after a load forms the DROP weights this way), in the gather's replay
 // of the row rather than inside the walk.
-template <bool kCoherent, bool kPlain, bool kCount, class Walk>
+//
+// pair (kPair, instead of delta and cnt): the update and the run count of
+// voxel j side by side, (delta_j, s_j) = pair[j], both added by one vector
+// reduction per run; the count is a float, exact while below 2^24 (the block
+// update checks that). A history without runs of positive length adds zero
+// updates but still counts its runs.
+template <bool kCoherent, bool kPlain, bool kCount, class Walk, bool kPair = false>
 __device__ __forceinline__ void drop_history_core(const RecV& v, Walk&& walk, const float* __restrict__ x,
                                                   float* __restrict__ delta, float lambda,
-                                                  unsigned int* __restrict__ cnt = nullptr) {
+                                                  unsigned int* __restrict__ cnt = nullptr,
+                                                  float2* __restrict__ pair = nullptr) {
   auto xload = [&](int j) { return kCoherent ? ld_weak(x + j) : __ldg(x + j); };
   uint2 row[kRowCap];
   int nrow = 0;
@@ -70,6 +82,19 @@ __device__ __forceinline__ void drop_history_core(const RecV& v, Walk&& walk, co
       if (kCount) atomicAdd(cnt + j, 1u);
       gather(j, l);
     });
+  }
+  if (kPair) {
+    const float res = __fadd_rn(__fsub_rn(v.wepl, y), c);
+    const float ri = nn > 0.f ? lambda * res / nn : 0.f;
+    if (nrow <= kRowCap) {
+      for (int q = 0; q < nrow; ++q) {
+        const uint2 e = row[q];
+        red_add_pair(pair + e.x, __uint_as_float(e.y) * ri);
+      }
+    } else {
+      walk([&](int j, float l) { red_add_pair(pair + j, l * ri); });
+    }
+    return;
   }
   if (!(nn > 0.f)) return;
   const float res = __fadd_rn(__fsub_rn(v.wepl, y), c);
@@ -110,6 +135,16 @@ __device__ __forceinline__ void drop_history_count(const Geo& g, const float4* _
   const RecV v = load_rec(r, i);
   drop_history_core<false, kPlain, true>(v, [&](auto&& visit) { walk_proton(g, tab, v, visit); }, x, delta, lambda,
                                          cnt);
+}
+
+// drop_history that adds (a_ij r_i, 1) to pair[j] for every run (the block's
+// update and run counts side by side).
+template <bool kPlain = false>
+__device__ __forceinline__ void drop_history_pair(const Geo& g, const float4* __restrict__ tab, const Rec& r, int64_t i,
+                                                  const float* __restrict__ x, float lambda, float2* __restrict__ pair) {
+  const RecV v = load_rec(r, i);
+  auto walk = [&](auto&& visit) { walk_proton(g, tab, v, visit); };
+  drop_history_core<false, kPlain, false, decltype(walk)&, true>(v, walk, x, nullptr, lambda, nullptr, pair);
 }
 
 template <bool kPlain = false>

@@ -144,6 +144,15 @@ cudaError_t launch_sort_block(const Rec& src, int64_t n, int64_t base, float lat
 cudaError_t launch_copy_block(const Rec& src, int64_t n, int64_t base, Rec dst_rec, cudaStream_t s);
 cudaError_t launch_count(const Geo& g, const Rec& r, const float4* tab, const Hull& hull, int64_t first, int64_t count,
                          unsigned int* cnt, int threads, cudaStream_t s);
+// The first sweep's block pass without a hull, one lane per history: the
+// update and the run counts of the block added to pair (M float2, zero on
+// entry) by one vector reduction per run; then the block update from pair
+// (1/s_j into inv_s, x += delta/s, pair zeroed; *overflow set where a float
+// count reached 2^24).
+cudaError_t launch_drop_fused_pair(const Geo& g, const Rec& r, const float4* tab, int64_t first, int64_t count,
+                                   const float* x, float2* pair, float lambda, int flags, cudaStream_t s);
+cudaError_t launch_drop_apply_pair(float* x, float2* pair, float* inv_s, int64_t M, int clamp, float clamp_min,
+                                   int* overflow, cudaStream_t s);
 cudaError_t launch_inv_counts(const unsigned int* cnt, float* inv_s, int64_t M, cudaStream_t s);
 cudaError_t launch_counts_to_float(const unsigned int* cnt, float* out, int64_t M, cudaStream_t s);
 // cnt non-null: also count the block's runs per voxel into cnt (zeroed by the

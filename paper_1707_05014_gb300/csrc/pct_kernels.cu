@@ -84,6 +84,38 @@ __global__ void __launch_bounds__(128, 9) drop_fused_count_kernel(Geo g, Rec r, 
   drop_history_count<kPlain>(g, tab, r, first + p, x, delta, lambda, cnt);
 }
 
+// The counting sweep's kernel without a hull: the block's update and run
+// counts go to pair, (a_ij r_i, 1) per run in one vector reduction.
+template <bool kPlain>
+__global__ void __launch_bounds__(128, 9) drop_fused_pair_kernel(Geo g, Rec r, const float4* __restrict__ tab_g,
+                                                               int64_t first, int64_t count,
+                                                               const float* __restrict__ x, float lambda,
+                                                               float2* __restrict__ pair) {
+  extern __shared__ float4 tab[];
+  load_table(tab_g, tab, g.K + 1);
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= count) return;
+  drop_history_pair<kPlain>(g, tab, r, first + p, x, lambda, pair);
+}
+
+// The counting sweep's block update: (delta_j, s_j) = pair[j]; 1/s_j into
+// inv_s (0 where no run counted), x_j += delta_j / s_j (optionally clamped),
+// pair[j] = 0. A float count is exact below 2^24; a count that reached 2^24
+// may have lost runs, which sets *overflow.
+__global__ void drop_apply_pair_kernel(float* __restrict__ x, float2* __restrict__ pair, float* __restrict__ inv_s,
+                                       int64_t M, int clamp, float clamp_min, int* __restrict__ overflow) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= M) return;
+  const float2 dc = pair[j];
+  if (dc.y >= 16777216.f) atomicOr(overflow, 1);
+  const float inv = dc.y > 0.f ? 1.0f / dc.y : 0.0f;
+  inv_s[j] = inv;
+  float xv = __fmaf_rn(dc.x, inv, x[j]);
+  if (clamp) xv = fmaxf(xv, clamp_min);
+  x[j] = xv;
+  pair[j] = make_float2(0.f, 0.f);
+}
+
 // The same with an object hull (see walk_proton_hull). PCT_HULL_MIN_CTAS:
 // resident 128-thread CTAs per SM its register allocation must allow.
 #ifndef PCT_HULL_MIN_CTAS
@@ -641,6 +673,25 @@ cudaError_t launch_drop_fused(const Geo& g, const Rec& r, const float4* tab, con
     else
       drop_fused_kernel<false><<<blocks, threads, smem, s>>>(g, r, tab, first, count, x, delta, lambda);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_drop_fused_pair(const Geo& g, const Rec& r, const float4* tab, int64_t first, int64_t count,
+                                   const float* x, float2* pair, float lambda, int flags, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  const int threads = 128;
+  const unsigned blocks = grid_for(count, threads);
+  const size_t smem = (g.K + 1) * sizeof(float4);
+  if (flags & 2)
+    drop_fused_pair_kernel<true><<<blocks, threads, smem, s>>>(g, r, tab, first, count, x, lambda, pair);
+  else
+    drop_fused_pair_kernel<false><<<blocks, threads, smem, s>>>(g, r, tab, first, count, x, lambda, pair);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_drop_apply_pair(float* x, float2* pair, float* inv_s, int64_t M, int clamp, float clamp_min,
+                                   int* overflow, cudaStream_t s) {
+  drop_apply_pair_kernel<<<grid_for(M, 256), 256, 0, s>>>(x, pair, inv_s, M, clamp, clamp_min, overflow);
   return cudaGetLastError();
 }
 
