@@ -249,8 +249,9 @@ def max_over_ranks(ms: float, device=None) -> float:
 
 
 def run_batched(args):
-    """Batched variant: 32 independent reconstructions of uneven size advanced by
-    one persistent launch per sweep (pct_batch_*), autotuned; the same sweep
+    """Batched variant: 32 independent reconstructions of uneven size advanced
+    together (pct_batch_*) in the mode the autotuner picks (graph branches of
+    the per-block kernels, or one persistent launch per sweep); the same sweep
     done one context at a time (pct_iterate) is timed beside it."""
     import torch
 
@@ -337,9 +338,13 @@ def run_batched(args):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"batched{len(wls)}", "reconstructions": len(wls), "histories": total,
                        "grids": "64x64x32 .. 160x160x64 over 200 mm", "histories_each": "2M-40M log-uniform",
-                       "n_blocks": 10, "step": "one DROP sweep of every reconstruction (one persistent launch)",
+                       "n_blocks": 10,
+                       "step": "one DROP sweep of every reconstruction (" + (
+                           "one persistent launch" if tune.get("mode") == "persistent" else
+                           f"graph of {tune.get('branches')} branches of per-block launches") + ")",
                        "parallelism": f"replicas{world}"},
-            "roofline": {"kernel": "batch_kernel", "bound": "alu", "achieved": achieved, "peak": alu_peak,
+            "roofline": {"kernel": "batch_kernel" if tune.get("mode") == "persistent" else (
+                             "drop_group_kernel" if tune.get("lanes", 1) > 1 else "drop_fused_kernel"), "bound": "alu", "achieved": achieved, "peak": alu_peak,
                          "unit": "Tops/s", "frac": achieved / alu_peak, "traffic": None},
             "autotune": tune, "modes_ms_per_sweep": modes, "sequential_contexts_value": total / (seq_ms / 1e3),
             "gpu_launches": launches, "clocks": clk,
