@@ -817,7 +817,7 @@ def main():
     ap.add_argument("--e2e-sweeps", type=int, default=10)
     ap.add_argument("--cpu-sample", type=int, default=1_000_000)
     ap.add_argument("--ref-sample", type=int, default=1_000_000)
-    ap.add_argument("--lanes", type=int, default=1, help="lanes per history in the fused kernel (1, 8, 16, 32)")
+    ap.add_argument("--lanes", type=int, default=1, help="lanes per history in the fused kernel (1, 2, 4, 8, 16, 32)")
     ap.add_argument("--no-sort", action="store_true", help="keep each block in load order (A/B of the ordering)")
     ap.add_argument("--hull", action="store_true", help="head / table2: MLP inside a hull carved from the data")
     ap.add_argument("--node-step", type=float, default=0.0, help="head: MLP node spacing in mm (default min(h)/2)")

@@ -66,7 +66,7 @@ typedef struct pct_config {
   int32_t flags;            /* PCT_FLAG_*                                      */
   float clamp_min;          /* lower clamp of x after each block (with flag)   */
   int32_t threads_per_proton; /* lanes per history in the fused kernel and the
-                               row export: 1 (0 = 1) or 8, 16, 32 (the group
+                               row export: 1 (0 = 1) or 2, 4, 8, 16, 32 (the group
                                walk: the lanes split the history's MLP
                                segments; same runs, in the same order). With an
                                object hull the one-lane kernels run.          */
@@ -347,7 +347,7 @@ typedef struct pct_batch_config {
                                      unreachable, so the bound runs out and the call
                                      reports PCT_ERR_TIMEOUT (the GPU stays usable)        */
   int32_t lanes;                  /* graph-branch mode: lanes per history of the fused
-                                     kernels (1, 8, 16 or 32, as threads_per_proton);
+                                     kernels (1, 2, 4, 8, 16 or 32, as threads_per_proton);
                                      <= 0: each context's own threads_per_proton. The
                                      persistent kernel always takes one lane per history  */
 } pct_batch_config;

@@ -179,7 +179,7 @@ pct_status pct_create(pct_ctx** out, const pct_grid* grid, const pct_config* cfg
   if (cfg->n_blocks < 1) return fail(PCT_ERR_INVALID_ARG, "n_blocks must be >= 1");
   if (!(cfg->lambda > 0.f && cfg->lambda < 2.f)) return fail(PCT_ERR_INVALID_ARG, "lambda must be in (0, 2)");
   if (cfg->threads_per_proton != 0 && cfg->threads_per_proton != 1 && !pct::group_lanes_supported(cfg->threads_per_proton))
-    return fail(PCT_ERR_INVALID_ARG, "threads_per_proton must be 1, 8, 16 or 32");
+    return fail(PCT_ERR_INVALID_ARG, "threads_per_proton must be 1, 2, 4, 8, 16 or 32");
 
   pct_ctx* c = new pct_ctx();
   c->device = device;

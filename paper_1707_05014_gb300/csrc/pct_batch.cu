@@ -402,7 +402,7 @@ pct_status pct_batch_create(pct_batch** out, pct_ctx* const* ctxs, int32_t n, co
     if (b->cfg.ctas_per_sm <= 0 || b->cfg.ctas_per_sm > b->max_ctas_per_sm) b->cfg.ctas_per_sm = b->max_ctas_per_sm;
     if (b->cfg.lanes < 0) b->cfg.lanes = 0;
     if (b->cfg.lanes > 1 && !pct::group_lanes_supported(b->cfg.lanes)) {
-      st = bfail(PCT_ERR_INVALID_ARG, "lanes must be 1, 8, 16 or 32");
+      st = bfail(PCT_ERR_INVALID_ARG, "lanes must be 1, 2, 4, 8, 16 or 32");
       break;
     }
     std::vector<ReconDesc> rd(n);

@@ -1,4 +1,4 @@
-// Group walk: T lanes (T = 8, 16 or 32) share one history, each lane taking
+// Group walk: T lanes (T = 2, 4, 8, 16 or 32) share one history, each lane taking
 // one segment of the polyline per step (arXiv 1707.05014 Sec. 2: the row a_i
 // of a proton is the length of its most-likely path in every voxel it
 // touches; Sec. 2.1, Fig. 1: DROP projects each row once per sweep).
@@ -307,13 +307,20 @@ __device__ __forceinline__ void load_tab(const float4* __restrict__ src, float4*
   __syncthreads();
 }
 
-constexpr int kGroupThreads = 256;
+// Threads per CTA of the group kernels: 256, or 32 groups for T < 8 (each
+// group holds a kGroupRowCap-run row in shared memory, 3 KB, so 128 groups of
+// two lanes would not fit). kGroupMinCtas: the register budget (64 per thread).
+template <int T>
+constexpr int kGroupThreads = T >= 8 ? 256 : 32 * T;
+template <int T>
+constexpr int kGroupMinCtas = 1024 / kGroupThreads<T>;
+inline int group_threads(int T) { return T >= 8 ? 256 : 32 * T; }
 
 // Fused MLP + DROP projection, T lanes per history; persistent over the
 // block's histories (group q takes histories q, q + groups, ...). kCount:
 // also count every run into cnt (the block's s_j).
 template <int T, bool kPlain, bool kCount>
-__global__ void __launch_bounds__(kGroupThreads, 4) drop_group_kernel(Geo g, Rec r, const float4* __restrict__ tab_g,
+__global__ void __launch_bounds__(kGroupThreads<T>, kGroupMinCtas<T>) drop_group_kernel(Geo g, Rec r, const float4* __restrict__ tab_g,
                                                                   int64_t first, int64_t count,
                                                                   const float* __restrict__ x,
                                                                   float* __restrict__ delta, float lambda,
@@ -324,8 +331,8 @@ __global__ void __launch_bounds__(kGroupThreads, 4) drop_group_kernel(Geo g, Rec
   const Group<T> G;
   const int gib = threadIdx.x / T;
   uint2* rows = reinterpret_cast<uint2*>(smem + (g.K + 1)) + (size_t)gib * rowcap;
-  const int64_t groups = (int64_t)gridDim.x * (kGroupThreads / T);
-  for (int64_t p = (int64_t)blockIdx.x * (kGroupThreads / T) + gib; p < count; p += groups) {
+  const int64_t groups = (int64_t)gridDim.x * (kGroupThreads<T> / T);
+  for (int64_t p = (int64_t)blockIdx.x * (kGroupThreads<T> / T) + gib; p < count; p += groups) {
     const RecV v = load_rec(r, first + p);
     // walk: the row goes to the group's buffer (no global loads in the walk,
     // so no lane waits on memory between steps)
@@ -382,15 +389,15 @@ __global__ void __launch_bounds__(kGroupThreads, 4) drop_group_kernel(Geo g, Rec
 // Row export through the group walk: counts, then (voxel, chord) in path
 // order and, optionally, the Q20 nodes k = 0..K.
 template <int T>
-__global__ void __launch_bounds__(kGroupThreads) row_count_group_kernel(Geo g, Rec r, const float4* __restrict__ tab_g,
+__global__ void __launch_bounds__(kGroupThreads<T>) row_count_group_kernel(Geo g, Rec r, const float4* __restrict__ tab_g,
                                                                        int64_t first, int64_t count,
                                                                        const int64_t* __restrict__ where,
                                                                        int64_t* __restrict__ row_ptr) {
   extern __shared__ float4 smem[];
   load_tab(tab_g, smem, g.K + 1);
   const Group<T> G;
-  const int64_t groups = (int64_t)gridDim.x * (kGroupThreads / T);
-  for (int64_t p = (int64_t)blockIdx.x * (kGroupThreads / T) + threadIdx.x / T; p < count; p += groups) {
+  const int64_t groups = (int64_t)gridDim.x * (kGroupThreads<T> / T);
+  for (int64_t p = (int64_t)blockIdx.x * (kGroupThreads<T> / T) + threadIdx.x / T; p < count; p += groups) {
     const int64_t i = where ? where[first + p] : first + p;
     const RecV v = load_rec(r, i);
     auto none = [](int, float, int) {};
@@ -400,7 +407,7 @@ __global__ void __launch_bounds__(kGroupThreads) row_count_group_kernel(Geo g, R
 }
 
 template <int T>
-__global__ void __launch_bounds__(kGroupThreads) row_fill_group_kernel(Geo g, Rec r, const float4* __restrict__ tab_g,
+__global__ void __launch_bounds__(kGroupThreads<T>) row_fill_group_kernel(Geo g, Rec r, const float4* __restrict__ tab_g,
                                                                       int64_t first, int64_t count,
                                                                       const int64_t* __restrict__ where,
                                                                       const int64_t* __restrict__ row_ptr,
@@ -410,8 +417,8 @@ __global__ void __launch_bounds__(kGroupThreads) row_fill_group_kernel(Geo g, Re
   extern __shared__ float4 smem[];
   load_tab(tab_g, smem, g.K + 1);
   const Group<T> G;
-  const int64_t groups = (int64_t)gridDim.x * (kGroupThreads / T);
-  for (int64_t p = (int64_t)blockIdx.x * (kGroupThreads / T) + threadIdx.x / T; p < count; p += groups) {
+  const int64_t groups = (int64_t)gridDim.x * (kGroupThreads<T> / T);
+  for (int64_t p = (int64_t)blockIdx.x * (kGroupThreads<T> / T) + threadIdx.x / T; p < count; p += groups) {
     const int64_t i = where ? where[first + p] : first + p;
     const RecV v = load_rec(r, i);
     const int64_t o = row_ptr[p];
@@ -450,7 +457,8 @@ inline unsigned group_grid(int64_t count, int T, int per_sm) {
     cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
     sms[dev] = n > 0 ? n : 1;
   }
-  const int64_t need = (count + kGroupThreads / T - 1) / (kGroupThreads / T);
+  const int per_cta = group_threads(T) / T;
+  const int64_t need = (count + per_cta - 1) / per_cta;
   const int64_t cap = (int64_t)sms[dev] * per_sm;
   return (unsigned)(need < 1 ? 1 : (need < cap ? need : cap));
 }
@@ -473,7 +481,7 @@ GroupLaunchInfo& launch_info() {
 }
 
 inline size_t drop_group_smem(int T, int K) {
-  return (size_t)(K + 1) * sizeof(float4) + (size_t)(kGroupThreads / T) * kGroupRowCap * sizeof(uint2);
+  return (size_t)(K + 1) * sizeof(float4) + (size_t)(group_threads(T) / T) * kGroupRowCap * sizeof(uint2);
 }
 
 template <int T, bool kPlain, bool kCount>
@@ -488,7 +496,7 @@ cudaError_t prepare_drop_group_t(int K) {
   }
   if (info.smem_occ != smem) {
     int per_sm = 0;
-    const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kGroupThreads, smem);
+    const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kGroupThreads<T>, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     info.per_sm = per_sm;
@@ -503,7 +511,7 @@ cudaError_t launch_drop_group_t(const Geo& g, const Rec& r, const float4* tab, i
   cudaError_t e = prepare_drop_group_t<T, kPlain, kCount>(g.K);
   if (e != cudaSuccess) return e;
   const GroupLaunchInfo& info = launch_info<T, kPlain, kCount>();
-  drop_group_kernel<T, kPlain, kCount><<<group_grid(count, T, info.per_sm), kGroupThreads, info.smem_occ, s>>>(
+  drop_group_kernel<T, kPlain, kCount><<<group_grid(count, T, info.per_sm), kGroupThreads<T>, info.smem_occ, s>>>(
       g, r, tab, first, count, x, delta, lambda, cnt, kGroupRowCap);
   return cudaGetLastError();
 }
@@ -534,20 +542,22 @@ cudaError_t launch_rows_group_t(const Geo& g, const Rec& r, const float4* tab, i
                                 bool fill, cudaStream_t s) {
   const size_t smem = (size_t)(g.K + 1) * sizeof(float4);  // <= 32 KB (K + 1 <= 2048)
   if (fill)
-    row_fill_group_kernel<T><<<group_grid(count, T, 4), kGroupThreads, smem, s>>>(g, r, tab, first, count, where,
+    row_fill_group_kernel<T><<<group_grid(count, T, 4), kGroupThreads<T>, smem, s>>>(g, r, tab, first, count, where,
                                                                                  row_ptr, vox, len, nodes);
   else
-    row_count_group_kernel<T><<<group_grid(count, T, 4), kGroupThreads, smem, s>>>(g, r, tab, first, count, where,
+    row_count_group_kernel<T><<<group_grid(count, T, 4), kGroupThreads<T>, smem, s>>>(g, r, tab, first, count, where,
                                                                                   row_ptr);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-bool group_lanes_supported(int T) { return T == 8 || T == 16 || T == 32; }
+bool group_lanes_supported(int T) { return T == 2 || T == 4 || T == 8 || T == 16 || T == 32; }
 
 cudaError_t prepare_drop_group(int T, int K) {
   switch (T) {
+    case 2: return prepare_drop_group_all<2>(K);
+    case 4: return prepare_drop_group_all<4>(K);
     case 8: return prepare_drop_group_all<8>(K);
     case 16: return prepare_drop_group_all<16>(K);
     case 32: return prepare_drop_group_all<32>(K);
@@ -561,6 +571,8 @@ cudaError_t launch_drop_group(int T, const Geo& g, const Rec& r, const float4* t
   if (count <= 0) return cudaSuccess;
   const bool plain = (flags & 2) != 0;
   switch (T) {
+    case 2: return launch_drop_group_any<2>(g, r, tab, first, count, x, delta, lambda, plain, cnt, s);
+    case 4: return launch_drop_group_any<4>(g, r, tab, first, count, x, delta, lambda, plain, cnt, s);
     case 8: return launch_drop_group_any<8>(g, r, tab, first, count, x, delta, lambda, plain, cnt, s);
     case 16: return launch_drop_group_any<16>(g, r, tab, first, count, x, delta, lambda, plain, cnt, s);
     case 32: return launch_drop_group_any<32>(g, r, tab, first, count, x, delta, lambda, plain, cnt, s);
@@ -573,6 +585,8 @@ cudaError_t launch_rows_group(int T, const Geo& g, const Rec& r, const float4* t
                               bool fill, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
   switch (T) {
+    case 2: return launch_rows_group_t<2>(g, r, tab, first, count, where, row_ptr, vox, len, nodes, fill, s);
+    case 4: return launch_rows_group_t<4>(g, r, tab, first, count, where, row_ptr, vox, len, nodes, fill, s);
     case 8: return launch_rows_group_t<8>(g, r, tab, first, count, where, row_ptr, vox, len, nodes, fill, s);
     case 16: return launch_rows_group_t<16>(g, r, tab, first, count, where, row_ptr, vox, len, nodes, fill, s);
     case 32: return launch_rows_group_t<32>(g, r, tab, first, count, where, row_ptr, vox, len, nodes, fill, s);

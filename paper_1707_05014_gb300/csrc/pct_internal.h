@@ -157,11 +157,11 @@ cudaError_t launch_inv_counts(const unsigned int* cnt, float* inv_s, int64_t M, 
 cudaError_t launch_counts_to_float(const unsigned int* cnt, float* out, int64_t M, cudaStream_t s);
 // cnt non-null: also count the block's runs per voxel into cnt (zeroed by the
 // caller). lanes: lanes per history, 1 (one thread per history) or, without
-// a hull, 8, 16 or 32 (the group walk).
+// a hull, 2, 4, 8, 16 or 32 (the group walk).
 cudaError_t launch_drop_fused(const Geo& g, const Rec& r, const float4* tab, const Hull& hull, int64_t first, int64_t count,
                               const float* x, float* delta, float lambda, int flags, int lanes, cudaStream_t s,
                               unsigned int* cnt = nullptr);
-// The group walk (T lanes per history, T in {8, 16, 32}; no hull): the fused
+// The group walk (T lanes per history, T in {2, 4, 8, 16, 32}; no hull): the fused
 // kernel and the row export. prepare_drop_group sets the fused kernels'
 // shared-memory limit for K + 1 table nodes; call it outside stream capture
 // before the first launch for that K.

@@ -75,7 +75,8 @@ def _cfg(pct, **kw):
     ((32, 32, 32, 2.0, float("nan"), 2.0), {}, "voxel sizes"),
     ((32, 32, 32, 2.0, 2.0, 2.0), {"n_blocks": 0}, "n_blocks"),
     ((32, 32, 32, 2.0, 2.0, 2.0), {"lam": 2.0}, "lambda"),
-    ((32, 32, 32, 2.0, 2.0, 2.0), {"threads_per_proton": 4}, "threads_per_proton"),
+    ((32, 32, 32, 2.0, 2.0, 2.0), {"threads_per_proton": 3}, "threads_per_proton"),
+    ((32, 32, 32, 2.0, 2.0, 2.0), {"threads_per_proton": 64}, "threads_per_proton"),
     ((32, 32, 32, 2.0, 2.0, 2.0), {"node_step_mm": 1e-3}, "node count"),
     ((512, 512, 512, 1.0, 1.0, 1.0), {"node_step_mm": 100.0}, "fixed-point node range"),
 ])

@@ -1,4 +1,4 @@
-"""GPU parity of the group walk (8, 16 or 32 lanes per history, the
+"""GPU parity of the group walk (2, 4, 8, 16 or 32 lanes per history, the
 threads_per_proton setting) against the FP64 oracle, through the C ABI.
 
 The group walk splits a history's MLP segments over the lanes and merges the
@@ -17,7 +17,7 @@ pytestmark = pytest.mark.gpu
 
 RSP_TOL = 1e-3
 CHORD_TOL = 1e-5
-LANES = [8, 16, 32]
+LANES = [2, 4, 8, 16, 32]
 
 
 @pytest.fixture(scope="module")
@@ -161,6 +161,6 @@ def test_group_with_hull_runs_the_one_lane_kernels(pct):
 
 def test_lane_counts_outside_the_supported_set_are_rejected(pct):
     g = S.Grid(8, 8, 8, 2.0, 2.0, 2.0)
-    for lanes in (2, 4, 7, 64):
+    for lanes in (3, 7, 64):
         with pytest.raises(pct.PctError):
             pct.Context(g, n_blocks=1, lanes=lanes)
