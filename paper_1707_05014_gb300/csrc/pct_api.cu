@@ -405,6 +405,40 @@ Rec rec_offset(const float* const* src, int64_t lo) {
 
 
 
+// Bring block b's records to the device, validate them and store them ordered
+// (or copied) into the context's record arrays, all queued on the context's
+// stream; host records go through staging slot b & 1 on the copy stream.
+pct_status load_block(pct_ctx* c, const float* const src[11], int flags, int b, int64_t max_blk, bool sort,
+                      bool in_place) {
+  const int64_t lo = block_lo(c, b), cnt = block_lo(c, b + 1) - lo;
+  Rec blk;
+  if (flags == PCT_LOAD_HOST) {
+    const int slot = b & 1;
+    float* dst = c->staging + (size_t)slot * 11 * max_blk;
+    if (b >= 2) PCT_CK(cudaStreamWaitEvent(c->copy_stream, c->load_ev[2 + slot], 0));  // block b - 2 consumed
+    for (int f = 0; f < 11; ++f)
+      PCT_CK(cudaMemcpyAsync(dst + (size_t)f * max_blk, src[f] + lo, (size_t)cnt * sizeof(float),
+                             cudaMemcpyHostToDevice, c->copy_stream));
+    PCT_CK(cudaEventRecord(c->load_ev[slot], c->copy_stream));
+    PCT_CK(cudaStreamWaitEvent(c->stream, c->load_ev[slot], 0));
+    blk = rec_at(dst, max_blk);
+  } else {
+    blk = rec_offset(src, lo);
+  }
+  PCT_CK(pct::launch_validate(blk, cnt, lo, c->pos_limit, c->first_bad, c->stream));
+  c->launches += 1;
+  if (sort) {
+    PCT_CK(pct::launch_sort_block(blk, cnt, lo, c->pos_limit, c->tab32, c->K, c->rec, c->where, c->sort_key, c->sort_hist, c->sort_order,
+                                  c->stream));
+    c->launches += 5;
+  } else if (!in_place) {
+    PCT_CK(pct::launch_copy_block(blk, cnt, lo, c->rec, c->stream));
+    c->launches += 1;
+  }
+  if (flags == PCT_LOAD_HOST) PCT_CK(cudaEventRecord(c->load_ev[2 + (b & 1)], c->stream));
+  return PCT_OK;
+}
+
 }  // namespace
 
 pct_status pct_load_histories(pct_ctx* c, const pct_histories* h, int flags, int64_t* first_bad) {
@@ -457,33 +491,15 @@ pct_status pct_load_histories(pct_ctx* c, const pct_histories* h, int flags, int
   // Host records go through two staging slots: block b + 1 is copied on the
   // copy stream while block b is validated and ordered on the context's stream.
   PCT_CK(cudaMemsetAsync(c->first_bad, 0xff, sizeof(unsigned long long), c->stream));
-  for (int b = 0; b < B; ++b) {
-    const int64_t lo = block_lo(c, b), cnt = block_lo(c, b + 1) - lo;
-    Rec blk;
+  {
+    pct_status lst = PCT_OK;
+    for (int b = 0; b < B && lst == PCT_OK; ++b) lst = load_block(c, src, flags, b, max_blk, sort, in_place);
     if (flags == PCT_LOAD_HOST) {
-      const int slot = b & 1;
-      float* dst = c->staging + (size_t)slot * 11 * max_blk;
-      if (b >= 2) PCT_CK(cudaStreamWaitEvent(c->copy_stream, c->load_ev[2 + slot], 0));  // block b - 2 consumed
-      for (int f = 0; f < 11; ++f)
-        PCT_CK(cudaMemcpyAsync(dst + (size_t)f * max_blk, src[f] + lo, (size_t)cnt * sizeof(float),
-                               cudaMemcpyHostToDevice, c->copy_stream));
-      PCT_CK(cudaEventRecord(c->load_ev[slot], c->copy_stream));
-      PCT_CK(cudaStreamWaitEvent(c->stream, c->load_ev[slot], 0));
-      blk = rec_at(dst, max_blk);
-    } else {
-      blk = rec_offset(src, lo);
+      // no copy outlives the call: the caller may free its host arrays on return
+      const cudaError_t e = cudaStreamSynchronize(c->copy_stream);
+      if (lst == PCT_OK && e != cudaSuccess) lst = fail(PCT_ERR_CUDA, "host copies: %s", cudaGetErrorString(e));
     }
-    PCT_CK(pct::launch_validate(blk, cnt, lo, c->pos_limit, c->first_bad, c->stream));
-    c->launches += 1;
-    if (sort) {
-      PCT_CK(pct::launch_sort_block(blk, cnt, lo, c->pos_limit, c->tab32, c->K, c->rec, c->where, c->sort_key, c->sort_hist, c->sort_order,
-                                    c->stream));
-      c->launches += 5;
-    } else if (!in_place) {
-      PCT_CK(pct::launch_copy_block(blk, cnt, lo, c->rec, c->stream));
-      c->launches += 1;
-    }
-    if (flags == PCT_LOAD_HOST) PCT_CK(cudaEventRecord(c->load_ev[2 + (b & 1)], c->stream));
+    if (lst != PCT_OK) return lst;
   }
   unsigned long long fb = 0;
   PCT_CK(cudaMemcpyAsync(&fb, c->first_bad, sizeof fb, cudaMemcpyDeviceToHost, c->stream));
