@@ -114,17 +114,46 @@ OPS_PER_RUN = 11  # crossing fraction 3, accumulation 2, index 3, load/atomic 3
 FUSED_SOURCES = ("pct_internal.h", "pct_walk.cuh", "pct_drop.cuh", "pct_kernels.cu")
 
 
-def kernel_source_hash() -> str:
-    """Hash of the fused kernel's CUDA sources: counters taken for another
-    version are stale."""
+def strip_c_comments(text: str) -> str:
+    """C/C++/CUDA source without its comments and with runs of white space
+    collapsed to one blank (string and character literals kept as written)."""
+    out, i, n = [], 0, len(text)
+    while i < n:
+        ch = text[i]
+        if ch in "\"'":
+            j = i + 1
+            while j < n and text[j] != ch:
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        elif text.startswith("//", i):
+            j = text.find("\n", i)
+            i = n if j < 0 else j
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            out.append(" ")
+            i = n if j < 0 else j + 2
+        else:
+            out.append(ch)
+            i += 1
+    return " ".join("".join(out).split())
+
+
+def kernel_source_hash(read=None) -> str:
+    """Hash of the fused kernel's CUDA sources, comments and layout aside:
+    counters taken on other code are stale. read(name) returns a file's text
+    (default: the working tree)."""
     import hashlib
 
     d = os.path.join(ROOT, "paper_1707_05014_gb300", "csrc")
+    if read is None:
+        def read(name):
+            with open(os.path.join(d, name), encoding="utf-8") as fh:
+                return fh.read()
     h = hashlib.sha256()
     for f in FUSED_SOURCES:
         h.update(f.encode())
-        with open(os.path.join(d, f), "rb") as fh:
-            h.update(fh.read())
+        h.update(strip_c_comments(read(f)).encode())
     return h.hexdigest()[:16]
 
 

@@ -428,7 +428,7 @@ __global__ void row_fill_kernel(Geo g, Rec r, const float4* __restrict__ tab_g, 
 // FP32 table). Two paths of one angle whose (ta + tc)/2 differ by dm and whose
 // tc - ta differ by dd are about |dm| + |dd| u/R apart at depth u, the scattering
 // slopes included; the bins are 1024 over the validated lateral range for the
-// midpoint (0.47 mm on the 200x200x48 grid) and 32 over +-8 mm for the change
+// midpoint (0.49 mm on the 200x200x48 grid) and 32 over +-8 mm for the change
 // (0.5 mm). On the 1e9-history head workload (90 angles, 2.2e5 histories per
 // angle and block) a central bin holds about a warp's worth of histories.
 __global__ void sort_key_kernel(Rec r, int64_t n, int n_ang, int n_lat, float lat_lim, const float4* __restrict__ tab,

@@ -79,6 +79,19 @@ def test_traffic_counters_are_used_only_for_the_sources_they_were_taken_on(monke
     assert bench.ncu_counters() is None
 
 
+def test_source_hash_ignores_comments_and_layout_but_not_code():
+    sys.path.insert(0, ROOT)
+    import bench
+
+    src = {f: "int f(int a) { return a + 1; }  // x\n" for f in bench.FUSED_SOURCES}
+    h0 = bench.kernel_source_hash(src.__getitem__)
+    commented = {f: "/* note */ int f(int a)\n{\n  return a + 1;  // y\n}\n" for f in bench.FUSED_SOURCES}
+    assert bench.kernel_source_hash(commented.__getitem__) == h0
+    changed = dict(src, **{bench.FUSED_SOURCES[0]: "int f(int a) { return a + 2; }"})
+    assert bench.kernel_source_hash(changed.__getitem__) != h0
+    assert bench.strip_c_comments('s = "//not a comment"; /* c */ t = 1; // c') == 's = "//not a comment"; t = 1;'
+
+
 def test_traffic_is_reported_only_for_the_captured_configuration():
     sys.path.insert(0, ROOT)
     import argparse
