@@ -165,7 +165,11 @@ PCT_API pct_status pct_mlp_table(pct_ctx *ctx, double *out, int to_device);
  * pct_iterate sweep after the load, which counts each block's runs as it
  * updates it (pct_batch_create counts them itself if no sweep has). The
  * context keeps its record buffers across loads and grows them when a load
- * needs more. Each block must hold fewer than 2^32 histories. Synchronises. */
+ * needs more. Host records (PCT_LOAD_HOST) pass through two staging slots of
+ * the largest block's 44 bytes per history, the next block's copy overlapping
+ * the current block's ordering; every copy has finished when the call
+ * returns, also on error, so the caller may free the host arrays then. Each
+ * block must hold fewer than 2^32 histories. Synchronises. */
 PCT_API pct_status pct_load_histories(pct_ctx *ctx, const pct_histories *h, int flags, int64_t *first_bad);
 
 /* Rows a_i of histories [first, first+count) of the loaded set (indices in
