@@ -11,6 +11,7 @@
 
 #include "../../include/pct.h"
 #include "pct_ctx.h"
+#include "pct_trace.h"
 
 using pct::Geo;
 using pct::Rec;
@@ -442,6 +443,7 @@ pct_status load_block(pct_ctx* c, const float* const src[11], int flags, int b, 
 }  // namespace
 
 pct_status pct_load_histories(pct_ctx* c, const pct_histories* h, int flags, int64_t* first_bad) {
+  pct::TraceRange trace_("pct_load_histories");
   if (first_bad) *first_bad = -1;
   if (!c || !h) return fail(PCT_ERR_INVALID_ARG, "ctx or histories is NULL");
   if (h->n < 1) return fail(PCT_ERR_INVALID_ARG, "n must be >= 1");
@@ -702,6 +704,7 @@ pct_status pct_block_counts(pct_ctx* c, int32_t block, float* out) {
 }
 
 pct_status pct_block_weights(pct_ctx* c) {
+  pct::TraceRange trace_("pct_block_weights");
   if (!c) return fail(PCT_ERR_INVALID_ARG, "ctx is NULL");
   if (!c->loaded) return fail(PCT_ERR_STATE, "no histories loaded");
   return pct::ensure_block_weights(c);
@@ -810,6 +813,7 @@ static pct_status build_sweep_graph(pct_ctx* c, bool counting, cudaGraphExec_t* 
 }
 
 pct_status pct_iterate(pct_ctx* c, int32_t n_sweeps) {
+  pct::TraceRange trace_("pct_iterate");
   if (!c) return fail(PCT_ERR_INVALID_ARG, "ctx is NULL");
   if (!c->loaded) return fail(PCT_ERR_STATE, "no histories loaded");
   if (n_sweeps < 0) return fail(PCT_ERR_INVALID_ARG, "n_sweeps < 0");

@@ -23,6 +23,7 @@
 
 #include "pct_ctx.h"
 #include "pct_drop.cuh"
+#include "pct_trace.h"
 
 namespace {
 
@@ -455,6 +456,7 @@ pct_status pct_batch_destroy(pct_batch* b) {
 }
 
 pct_status pct_batch_iterate(pct_batch* b, int32_t n_sweeps, void* stream) {
+  pct::TraceRange trace_("pct_batch_iterate");
   if (!b) return bfail(PCT_ERR_INVALID_ARG, "batch is NULL");
   if (n_sweeps < 0) return bfail(PCT_ERR_INVALID_ARG, "n_sweeps < 0");
   pct_status cs = check_contexts(b);
@@ -512,6 +514,7 @@ pct_status pct_batch_sync(pct_batch* b, void* stream) {
 }
 
 pct_status pct_batch_autotune(pct_batch* b, pct_batch_config* chosen, float* best_ms) {
+  pct::TraceRange trace_("pct_batch_autotune");
   if (!b) return bfail(PCT_ERR_INVALID_ARG, "batch is NULL");
   pct_status cs = check_contexts(b);
   if (cs != PCT_OK) return cs;

@@ -32,6 +32,7 @@
 
 #include "../../include/pct.h"
 #include "pct_internal.h"
+#include "pct_trace.h"
 
 namespace {
 
@@ -693,6 +694,7 @@ pct_status pct_net_set_params(pct_net* nt, const float* in) {
 }
 
 pct_status pct_net_forward(pct_net* nt, const float* x1, float* x0, void* stream) {
+  pct::TraceRange trace_("pct_net_forward");
   if (!nt || !x1 || !x0) return nfail(PCT_ERR_INVALID_ARG, "NULL argument");
   pct::DeviceGuard device_guard_;
   NET_CK(cudaSetDevice(nt->device));
@@ -795,6 +797,7 @@ pct_status pct_net_layer(pct_net* nt, int32_t layer, int32_t op, const void* in,
 
 pct_status pct_net_train_step(pct_net* nt, const float* x1, const float* target, float* x0_scratch, float lr,
                               double* loss, void* stream) {
+  pct::TraceRange trace_("pct_net_train_step");
   if (!nt || !x1 || !target || !x0_scratch) return nfail(PCT_ERR_INVALID_ARG, "NULL argument");
   if (!(lr > 0.f)) return nfail(PCT_ERR_INVALID_ARG, "lr must be > 0");
   pct::DeviceGuard device_guard_;
